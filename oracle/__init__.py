@@ -1,0 +1,275 @@
+"""FP64 CPU oracle of the coupled guiding-center / Boris pusher (Bacchini et al. 2020).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It wraps the plain C
+implementation in ``gcb_oracle.c`` (compiled here with gcc, no CUDA) and shares
+no code with the CUDA library.
+
+Arrays use the oracle's own plain layout: positions ``x`` and displacements
+``dxp`` of shape (ndim, n), momenta ``u`` of shape (3, n), all float64,
+``flags`` uint8 of shape (n,); field components as separate float64 node
+arrays of shape (nz, ny, nx) (2D: (ny, nx)).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gcb_oracle.c")
+_HDR = os.path.join(_HERE, "gcb_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+
+FIELD_GRID, FIELD_UNIFORM, FIELD_HARRIS, FIELD_BOTTLE, FIELD_ROTOR = 0, 1, 2, 3, 4
+GRAD_DW, GRAD_GRID = 0, 1
+FORCE_NONE, FORCE_BORIS, FORCE_GCA = 0, 1, 2
+MU_CONSERVE, UPERP_CONSERVE = 0, 1
+FLAG_S, FLAG_SPREV, FLAG_NONCONV, FLAG_GCAFAIL, FLAG_NONFINITE = 1, 2, 4, 8, 16
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (OpenMP); returns its path.
+
+    ``GCB_ORACLE_LIB`` names a prebuilt library to load instead; the mutation
+    test uses it to run the pins against an oracle with a planted mistake."""
+    alt = os.environ.get("GCB_ORACLE_LIB")
+    if alt:
+        return alt
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = force or not os.path.exists(_LIB) or max(
+        os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(_LIB)
+    if stale:
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Field(C.Structure):
+    _fields_ = [("kind", C.c_int), ("ndim", C.c_int), ("n", C.c_long * 3),
+                ("dx", C.c_double * 3), ("E", C.c_void_p * 3), ("B", C.c_void_p * 3),
+                ("dB", C.c_void_p * 9), ("par", C.c_double * 16)]
+
+
+class Params(C.Structure):
+    _fields_ = [("c", C.c_double), ("dt", C.c_double), ("f_rho", C.c_double),
+                ("f_E", C.c_double), ("dl", C.c_double), ("qm", C.c_double * 4),
+                ("curvature", C.c_int), ("mu_mode", C.c_int), ("grad_mode", C.c_int),
+                ("force", C.c_int), ("max_iter", C.c_int), ("fixed_iters", C.c_int),
+                ("tol", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_boris", C.c_long), ("n_gca", C.c_long), ("n_to_gca", C.c_long),
+                ("n_to_boris", C.c_long), ("n_nonconv", C.c_long), ("n_gcafail", C.c_long),
+                ("n_nonfinite", C.c_long), ("sum_iter", C.c_long), ("max_iter", C.c_long),
+                ("sum_ekin", C.c_double)]
+
+
+class Detail(C.Structure):
+    _fields_ = [("S", C.c_int), ("margin", C.c_double), ("branch", C.c_int),
+                ("gcafail", C.c_int), ("nonconv", C.c_int), ("iters", C.c_int),
+                ("resid", C.c_double), ("H", C.c_double), ("upar_old", C.c_double),
+                ("upar_new", C.c_double), ("mu", C.c_double), ("uperp", C.c_double),
+                ("Gamma_full", C.c_double), ("Gamma1", C.c_double), ("k1", C.c_double),
+                ("k2", C.c_double), ("k3", C.c_double), ("Rn", C.c_double * 3),
+                ("Rnp1", C.c_double * 3), ("bpg", C.c_double * 3)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P, D3 = C.POINTER, C.c_double * 3
+            lib.orc_eval_field.argtypes = [P(Field), P(Params), D3, C.c_double * 15]
+            lib.orc_switch.argtypes = [D3, D3, C.c_double, C.c_double, P(Params),
+                                       P(C.c_double)]
+            lib.orc_switch.restype = C.c_int
+            lib.orc_step_one.argtypes = [P(Field), P(Params), D3, D3, D3,
+                                         P(C.c_ubyte), P(Detail)]
+            lib.orc_decompose.argtypes = [P(Field), P(Params), C.c_double, D3, D3,
+                                          P(C.c_double), P(C.c_double), P(C.c_double), D3]
+            lib.orc_decompose.restype = C.c_int
+            lib.orc_reconstruct.argtypes = [P(Field), P(Params), C.c_double, D3,
+                                            C.c_double, C.c_double, C.c_double, D3, D3]
+            lib.orc_reconstruct.restype = C.c_int
+            lib.orc_push_sr.argtypes = [C.c_long, C.c_void_p * 3, C.c_void_p * 3,
+                                        C.c_void_p * 3, C.c_void_p, P(Field), P(Params),
+                                        C.c_int, C.c_int, P(Stats)]
+            lib.orc_push_sr.restype = C.c_int
+            lib.orc_push_resolved.argtypes = [C.c_long, C.c_void_p * 3, C.c_void_p * 3,
+                                              C.c_void_p, P(Field), P(Params), C.c_double,
+                                              C.c_double, C.c_int]
+            lib.orc_push_resolved.restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def make_params(*, c=1.0, dt, f_rho=0.4, f_E=1.0, dl=1.0, qm=(-1.0, 1.0, 0.0, 0.0),
+                curvature=1, mu_mode=MU_CONSERVE, grad_mode=GRAD_DW, force=FORCE_NONE,
+                max_iter=16, fixed_iters=0, tol=1e-7) -> Params:
+    q = list(qm) + [0.0] * (4 - len(qm))
+    return Params(c, dt, f_rho, f_E, dl, (C.c_double * 4)(*q), curvature, mu_mode,
+                  grad_mode, force, max_iter, fixed_iters, tol)
+
+
+class OracleField:
+    """A field the oracle can evaluate; keeps its numpy arrays alive."""
+
+    def __init__(self, kind, ndim, n=(1, 1, 1), dx=(1.0, 1.0, 1.0), E=None, B=None,
+                 dB=None, par=()):
+        self._keep = []
+        s = Field()
+        s.kind, s.ndim = kind, ndim
+        n = tuple(n) + (1,) * (3 - len(n))
+        dx = tuple(dx) + (1.0,) * (3 - len(dx))
+        for k in range(3):
+            s.n[k] = int(n[k])
+            s.dx[k] = float(dx[k])
+        if kind == FIELD_GRID:
+            for k in range(3):
+                e = np.ascontiguousarray(E[k], dtype=np.float64)
+                b = np.ascontiguousarray(B[k], dtype=np.float64)
+                assert e.size == n[0] * n[1] * n[2] and b.size == e.size
+                self._keep += [e, b]
+                s.E[k] = e.ctypes.data
+                s.B[k] = b.ctypes.data
+            if dB is not None:
+                for ij in range(3 * ndim):
+                    g = np.ascontiguousarray(dB[ij], dtype=np.float64)
+                    self._keep.append(g)
+                    s.dB[ij] = g.ctypes.data
+        par = list(par) + [0.0] * (16 - len(par))
+        for k in range(16):
+            s.par[k] = float(par[k])
+        self.s = s
+        self.ndim = ndim
+
+
+def grid_field(E, B, dx, dB=None) -> OracleField:
+    """Grid field from component arrays E[3], B[3] (each (ny,nx) or (nz,ny,nx))."""
+    shape = np.asarray(E[0]).shape
+    ndim = len(shape)
+    n = tuple(reversed(shape))
+    return OracleField(FIELD_GRID, ndim, n, dx, E=E, B=B, dB=dB)
+
+
+def uniform_field(E, B, ndim=3) -> OracleField:
+    return OracleField(FIELD_UNIFORM, ndim, par=list(E) + list(B))
+
+
+def harris_field(B0, delta, Bg, Ez, y0=0.0) -> OracleField:
+    return OracleField(FIELD_HARRIS, 2, par=[B0, delta, Bg, Ez, y0])
+
+
+def bottle_field(B0, L, E=(0.0, 0.0, 0.0)) -> OracleField:
+    return OracleField(FIELD_BOTTLE, 3, par=[B0, L] + list(E))
+
+
+def rotor_field(B0, k, E0, ndim=3) -> OracleField:
+    return OracleField(FIELD_ROTOR, ndim, par=[B0, k, E0])
+
+
+def eval_field(field: OracleField, params: Params, x) -> np.ndarray:
+    lib = _load()
+    out = (C.c_double * 15)()
+    xx = (C.c_double * 3)(*(list(x) + [0.0] * (3 - len(x))))
+    lib.orc_eval_field(C.byref(field.s), C.byref(params), xx, out)
+    return np.array(out[:])
+
+
+def switch(E, B, Gam, Q, params: Params):
+    lib = _load()
+    m = C.c_double()
+    S = lib.orc_switch((C.c_double * 3)(*E), (C.c_double * 3)(*B), Gam, Q,
+                       C.byref(params), C.byref(m))
+    return S, m.value
+
+
+def step_one(field: OracleField, params: Params, x, u, dxp, flags=0):
+    """One coupled step of one particle; returns (x, u, dxp, flags, detail)."""
+    lib = _load()
+    xx = (C.c_double * 3)(*(list(x) + [0.0] * (3 - len(x))))
+    uu = (C.c_double * 3)(*u)
+    dd = (C.c_double * 3)(*(list(dxp) + [0.0] * (3 - len(dxp))))
+    fl = C.c_ubyte(flags)
+    det = Detail()
+    lib.orc_step_one(C.byref(field.s), C.byref(params), xx, uu, dd, C.byref(fl),
+                     C.byref(det))
+    nd = field.ndim
+    return np.array(xx[:nd]), np.array(uu[:]), np.array(dd[:nd]), fl.value, det
+
+
+def decompose(field, params, qm, R, u):
+    lib = _load()
+    up, mu, uperp = C.c_double(), C.c_double(), C.c_double()
+    bpg = (C.c_double * 3)()
+    ok = lib.orc_decompose(C.byref(field.s), C.byref(params), qm,
+                           (C.c_double * 3)(*(list(R) + [0.0] * (3 - len(R)))),
+                           (C.c_double * 3)(*u), C.byref(up), C.byref(mu),
+                           C.byref(uperp), bpg)
+    return ok, up.value, mu.value, uperp.value, np.array(bpg[:])
+
+
+def reconstruct(field, params, qm, R, upar, mu, uperp, bpg):
+    lib = _load()
+    u = (C.c_double * 3)()
+    ok = lib.orc_reconstruct(C.byref(field.s), C.byref(params), qm,
+                             (C.c_double * 3)(*(list(R) + [0.0] * (3 - len(R)))),
+                             upar, mu, uperp, (C.c_double * 3)(*bpg), u)
+    return ok, np.array(u[:])
+
+
+def _ptrs(arrs, k):
+    p = (C.c_void_p * 3)()
+    for i in range(k):
+        assert arrs[i].dtype == np.float64 and arrs[i].flags.c_contiguous
+        p[i] = arrs[i].ctypes.data
+    return p
+
+
+def push_sr(state: dict, field: OracleField, params: Params, n_steps: int,
+            nthreads: int = 0) -> dict:
+    """Advance ``state`` (dict x, u, dxp, flags; modified in place) by n_steps."""
+    lib = _load()
+    x, u, dxp, flags = state["x"], state["u"], state["dxp"], state["flags"]
+    nd = field.ndim
+    n = flags.shape[0]
+    assert x.shape == (nd, n) and u.shape == (3, n) and dxp.shape == (nd, n)
+    assert flags.dtype == np.uint8 and flags.flags.c_contiguous
+    xs = [x[k] for k in range(nd)]
+    us = [u[k] for k in range(3)]
+    ds = [dxp[k] for k in range(nd)]
+    st = Stats()
+    rc = lib.orc_push_sr(n, _ptrs(xs, nd), _ptrs(us, 3), _ptrs(ds, nd),
+                         flags.ctypes.data, C.byref(field.s), C.byref(params),
+                         n_steps, nthreads, C.byref(st))
+    if rc != 0:
+        raise RuntimeError(f"orc_push_sr failed ({rc})")
+    return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+
+def push_resolved(state: dict, field: OracleField, params: Params, t_end: float,
+                  dt_max: float, nthreads: int = 0) -> None:
+    """Gyro-resolved Boris reference (adaptive dt = 2 pi / (60 Omega_C))."""
+    lib = _load()
+    x, u, flags = state["x"], state["u"], state["flags"]
+    nd = field.ndim
+    n = flags.shape[0]
+    rc = lib.orc_push_resolved(n, _ptrs([x[k] for k in range(nd)], nd),
+                               _ptrs([u[k] for k in range(3)], 3), flags.ctypes.data,
+                               C.byref(field.s), C.byref(params), t_end, dt_max,
+                               nthreads)
+    if rc != 0:
+        raise RuntimeError("orc_push_resolved failed")

@@ -1,0 +1,127 @@
+/*
+ * gcb_oracle.h -- plain FP64 CPU oracle of the coupled guiding-center / Boris
+ * particle pusher of Bacchini, Ripperda, Philippov & Parfrey (2020).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this code: only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no header, helper, table or kernel
+ * with the CUDA library; it is written to be read against the paper, not to
+ * be fast (the only concession is an OpenMP loop over particles, which does
+ * not change the per-particle arithmetic).
+ *
+ * Conventions (all FP64):
+ *   - flat space, general speed of light c;  alpha_q = q/m is signed,
+ *     Q = |q/m|;  mu is stored as mu/m.
+ *   - fields live on the nodes of a uniform periodic grid, node (i,j,k) at
+ *     position (i dx, j dy, k dz), node index (k*ny + j)*nx + i;  one array
+ *     per component.  In 2D runs (ndim = 2) z is ignorable: positions have two
+ *     components, momenta three.
+ *   - particle state: x^n (ndim comps), u^{n-1/2} (3 comps) and the unwrapped
+ *     displacement dxp = x^n - x^{n-1} (ndim comps), staggered as in Sec. 2.1.
+ *   - flags byte: bit0 S of the last step, bit1 S of the step before,
+ *     bit2 NONCONV, bit3 GCAFAIL, bit4 NONFINITE, bits 6-7 species index.
+ */
+#ifndef GCB_ORACLE_H
+#define GCB_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_FIELD_GRID = 0, ORC_FIELD_UNIFORM = 1, ORC_FIELD_HARRIS = 2,
+       ORC_FIELD_BOTTLE = 3, ORC_FIELD_ROTOR = 4 };
+enum { ORC_GRAD_DW = 0, ORC_GRAD_GRID = 1 };
+enum { ORC_FORCE_NONE = 0, ORC_FORCE_BORIS = 1, ORC_FORCE_GCA = 2 };
+enum { ORC_MU_CONSERVE = 0, ORC_UPERP_CONSERVE = 1 };
+
+enum { ORC_FLAG_S = 1, ORC_FLAG_SPREV = 2, ORC_FLAG_NONCONV = 4,
+       ORC_FLAG_GCAFAIL = 8, ORC_FLAG_NONFINITE = 16 };
+
+typedef struct {
+    int kind;            /* ORC_FIELD_* */
+    int ndim;            /* 2 or 3 */
+    long n[3];           /* nodes per axis (periodic) */
+    double dx[3];        /* node spacing */
+    const double *E[3];  /* node arrays (kind GRID) */
+    const double *B[3];
+    const double *dB[9]; /* dB[3*i+j] = d_i B_j at the nodes (grad_mode GRID) */
+    double par[16];      /* analytic parameters (see gcb_oracle.c) */
+} orc_field;
+
+typedef struct {
+    double c, dt;
+    double f_rho, f_E;   /* switch thresholds (Sec. 4.1) */
+    double dl;           /* effective cell size Delta-ell (Sec. 3) */
+    double qm[4];        /* q/m per species */
+    int curvature;       /* 1: Sec. 2.2.2 scheme, 0: Sec. 2.2.1 scheme */
+    int mu_mode;         /* ORC_MU_CONSERVE or ORC_UPERP_CONSERVE (Sec. 2.2) */
+    int grad_mode;       /* ORC_GRAD_DW or ORC_GRAD_GRID */
+    int force;           /* ORC_FORCE_*: test aid, bypasses the switch */
+    int max_iter;        /* bound of the fixed-point iteration */
+    int fixed_iters;     /* > 0: exactly this many iterations, no test */
+    double tol;          /* absolute stopping tolerance on |R^{k+1}-R^k|_inf */
+} orc_params;
+
+typedef struct {
+    long n_boris, n_gca, n_to_gca, n_to_boris;
+    long n_nonconv, n_gcafail, n_nonfinite, sum_iter;
+    long max_iter;
+    double sum_ekin;     /* sum of (Gamma - 1) after the step */
+} orc_stats;
+
+/* Everything one particle-step computed, for the closed-form tests. */
+typedef struct {
+    int S;               /* switch value (after force) */
+    double margin;       /* signed criterion margin, see orc_switch */
+    int branch;          /* 1 Boris, 0 GCA, -1 frozen */
+    int gcafail, nonconv, iters;
+    double resid;        /* |R^K - R^{K-1}|_inf of the last iteration */
+    double H;            /* |H(R^K)|_inf of the final iterate */
+    double upar_old, upar_new, mu, uperp, Gamma_full;
+    double Gamma1;       /* Gamma(R^n, u_par^{n+1/2}) from the quadratic */
+    double k1, k2, k3;
+    double Rn[3], Rnp1[3], bpg[3];
+} orc_detail;
+
+/* E, B and d_i B_j (out[0..2] E, out[3..5] B, out[6+3i+j] d_i B_j). */
+void orc_eval_field(const orc_field *f, const orc_params *p,
+                    const double x[3], double out[15]);
+
+/* Switch S of Sec. 4.1 (0 = GCA, 1 = Boris) at field point (E,B) for a
+ * particle of Lorentz factor Gam; *margin receives the criterion margin. */
+int orc_switch(const double E[3], const double B[3], double Gam, double Q,
+               const orc_params *p, double *margin);
+
+/* One coupled step of one particle (Sec. 3.1). */
+void orc_step_one(const orc_field *f, const orc_params *p, double x[3],
+                  double u[3], double dxp[3], unsigned char *flags,
+                  orc_detail *d);
+
+/* Full -> GC decomposition (Sec. 3.1) at the point R with full u and the
+ * Lorentz factor of u; returns 0 on an invalid frame. */
+int orc_decompose(const orc_field *f, const orc_params *p, double qm,
+                  const double R[3], const double u[3], double *upar,
+                  double *mu, double *uperp, double bpg[3]);
+
+/* GC -> full reconstruction (Sec. 3.1) at the point R. */
+int orc_reconstruct(const orc_field *f, const orc_params *p, double qm,
+                    const double R[3], double upar, double mu, double uperp,
+                    const double bpg[3], double u[3]);
+
+/* n_steps coupled steps of n particles (SoA, arrays per component). */
+int orc_push_sr(long n, double *const x[3], double *const u[3],
+                double *const dxp[3], unsigned char *flags,
+                const orc_field *f, const orc_params *p, int n_steps,
+                int nthreads, orc_stats *st);
+
+/* Gyro-resolved Boris reference (Sec. 4.1): adaptive step
+ * dt_k = min(dt_max, 2 pi / (60 Omega_C)) until time t_end. */
+int orc_push_resolved(long n, double *const x[3], double *const u[3],
+                      unsigned char *flags, const orc_field *f,
+                      const orc_params *p, double t_end, double dt_max,
+                      int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
