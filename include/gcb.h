@@ -1,0 +1,191 @@
+/*
+ * gcb.h -- C ABI of the GB300 coupled guiding-center / Boris particle pusher.
+ *
+ * Method: Bacchini, Ripperda, Philippov & Parfrey (2020), "A coupled
+ * guiding center-Boris particle pusher for magnetized plasmas in
+ * compact-object magnetospheres".  For each particle one step
+ *   1. gathers E, B (and the gradients of B) at x^n with the linear shape
+ *      function of Sec. 4 (intro): F(x) = sum_N F_N W(x - x_N),
+ *      grad F(x) = sum_N F_N grad W(x - x_N);
+ *   2. evaluates the switch S of Sec. 3 / Sec. 4.1: S = 0 (guiding center)
+ *      iff rho~_C / dl < f_rho and E/B < f_E, rho~_C = m c^2 Gamma/(|q| B);
+ *   3. advances with the relativistic Boris push (S = 1, Sec. 2.1) or with
+ *      the guiding-center leapfrog of Sec. 2.2.1 (no curvature) / Sec. 2.2.2
+ *      (with curvature), converting the full state to (R, u_par, mu) at
+ *      R^{n-1/2} and back at R^{n+1/2} (Sec. 3.1).
+ *
+ * All entry points are asynchronous on the caller's CUDA stream unless
+ * stated otherwise.  The library never allocates device memory: the caller
+ * owns every buffer (including the workspace) and the library keeps no
+ * pointer after a call returns.  Errors are returned as gcb_status; nothing
+ * is launched when an argument check fails.  gcb_last_error() returns a
+ * thread-local message describing the last failure.
+ *
+ * Units: flat space, general speed of light c (all shipped workloads use
+ * c = 1).  u is the spatial part of the 4-velocity (u = gamma v, velocity
+ * units); q/m is signed; mu is stored as mu/m.
+ */
+#ifndef GCB_H
+#define GCB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GCB_OK = 0,
+    GCB_EINVAL = 1,          /* invalid argument (null pointer, bad size, ...) */
+    GCB_ECUDA = 2,           /* a CUDA runtime call failed */
+    GCB_EUNSUPPORTED = 3,    /* valid but not implemented combination */
+    GCB_ENOMEM = 4           /* caller-provided workspace too small */
+} gcb_status;
+
+enum { GCB_F32 = 0, GCB_F64 = 1 };                       /* element types */
+enum { GCB_POS_F64 = 0, GCB_POS_F32PAIR = 1 };           /* position storage */
+enum { GCB_GRAD_DW = 0, GCB_GRAD_GRID = 1 };             /* source of grad B */
+enum { GCB_FORCE_NONE = 0, GCB_FORCE_BORIS = 1, GCB_FORCE_GCA = 2 };
+enum { GCB_MU_CONSERVE = 0, GCB_UPERP_CONSERVE = 1 };
+
+/* Per-particle flag byte. */
+enum {
+    GCB_FLAG_S = 1,          /* S of the last step (1 = Boris, 0 = GCA) */
+    GCB_FLAG_SPREV = 2,      /* S of the step before */
+    GCB_FLAG_NONCONV = 4,    /* last GCA fixed point hit gca_max_iter */
+    GCB_FLAG_GCAFAIL = 8,    /* last GCA step impossible (quadratic without a
+                                root >= 1, B = 0 or v_E >= c on the path):
+                                the particle took a Boris step instead */
+    GCB_FLAG_NONFINITE = 16, /* state non-finite: particle not advanced */
+    GCB_SPECIES_SHIFT = 6    /* bits 6-7: species index into gcb_params.qm */
+};
+
+/*
+ * Field grid in the packed node-record layout.  The grid is uniform and
+ * periodic with n[d] nodes along axis d, node (i,j,k) at (i dx0, j dx1, k dx2),
+ * node index (k n1 + j) n0 + i.  Each node holds one record of `stride`
+ * elements of type `dtype`:
+ *     E0 E1 E2 B0 B1 B2 [d_0B_0 d_0B_1 d_0B_2 d_1B_0 ... d_{ndim-1}B_2] pad
+ * where the gradient block (3*ndim elements) is present iff has_grad, and
+ * the stride (gcb_grid_stride) pads the record to a multiple of 16 bytes.
+ * In 2D (ndim = 2) z is ignorable: positions have two components and
+ * d_z = 0.  Build records with gcb_grid_pack.
+ */
+typedef struct {
+    int32_t ndim;            /* 2 or 3 */
+    int32_t dtype;           /* GCB_F32 or GCB_F64 */
+    int64_t n[3];            /* nodes per axis (n[2] = 1 in 2D) */
+    double dx[3];            /* node spacing per axis (> 0) */
+    int32_t has_grad;        /* records carry d_i B_j (needed by GCB_GRAD_GRID) */
+    int32_t stride;          /* elements per record, = gcb_grid_stride(...) */
+    const void *rec;         /* device pointer, 16-byte aligned */
+} gcb_grid;
+
+/*
+ * Particle state, structure of arrays (device pointers), staggered as in
+ * Sec. 2.1: positions x^n at integer steps, u^{n-1/2} at half steps, and the
+ * unwrapped displacement dxp = x^n - x^{n-1} of the previous step (the
+ * decomposition point R^{n-1/2} = x^n - dxp/2 of Sec. 3.1 needs it).
+ *   pos_mode GCB_POS_F64:     x[d] are double arrays; x_lo unused.
+ *   pos_mode GCB_POS_F32PAIR: x[d] are float "hi" arrays and x_lo[d] float
+ *                             "lo" arrays, position = hi + lo (|lo| <= ulp(hi)/2).
+ *   mom_dtype GCB_F64 / GCB_F32: element type of u[0..2] and dxp[0..ndim-1].
+ * Positions are kept in [0, L_d) (periodic wrap after every step).
+ * Each array must be aligned to its element size.
+ */
+typedef struct {
+    int64_t n;               /* number of particles (>= 0) */
+    int32_t ndim;            /* must equal the grid's ndim */
+    int32_t pos_mode;
+    int32_t mom_dtype;
+    int32_t reserved;
+    void *x[3];
+    void *x_lo[3];
+    void *u[3];
+    void *dxp[3];
+    uint8_t *flags;          /* n bytes, see GCB_FLAG_* */
+} gcb_particles;
+
+typedef struct {
+    double c;                /* speed of light (> 0) */
+    double dt;               /* time step (> 0) */
+    double f_rho, f_E;       /* switch thresholds (> 0); Sec. 4.1 defaults 0.4, 1 */
+    double dl;               /* effective cell size Delta-ell (> 0), Sec. 3 */
+    double qm[4];            /* q/m per species (non-zero for used species) */
+    int32_t curvature;       /* 1: Sec. 2.2.2 scheme; 0: Sec. 2.2.1 scheme */
+    int32_t mu_mode;         /* GCB_MU_CONSERVE (Eq. dmudt) or GCB_UPERP_CONSERVE */
+    int32_t grad_mode;       /* GCB_GRAD_DW (differentiate W) or GCB_GRAD_GRID */
+    int32_t force;           /* GCB_FORCE_*: bypass the switch (tests, studies) */
+    int32_t gca_max_iter;    /* bound of the fixed-point iteration (>= 1) */
+    int32_t gca_fixed_iters; /* > 0: exactly this many iterations, no test */
+    double gca_tol;          /* absolute tolerance on |R^{k+1}-R^k|_inf (Sec. 2.2) */
+} gcb_params;
+
+/* Counters of one gcb_push_sr call, summed over its steps. */
+typedef struct {
+    int64_t n_boris, n_gca;          /* particle-steps per branch */
+    int64_t n_to_gca, n_to_boris;    /* switches S: 1 -> 0 and 0 -> 1 */
+    int64_t n_nonconv, n_gcafail, n_nonfinite;
+    int64_t sum_iter, max_iter;      /* fixed-point iterations */
+    double sum_ekin;                 /* sum of (Gamma - 1) m c^2 / m after each step */
+} gcb_stats;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int gcb_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *gcb_status_string(gcb_status s);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *gcb_last_error(void);
+
+/* Elements per node record for a grid of this shape (0 on bad input). */
+int32_t gcb_grid_stride(int32_t ndim, int32_t dtype, int32_t has_grad);
+
+/*
+ * Pack component arrays into node records (device kernel on `stream`).
+ *   g      : destination description; g->rec must point to a device buffer
+ *            of n0*n1*n2*stride elements of g->dtype (written here).
+ *   comp   : 6 + 3*ndim device pointers to float64 node arrays of n0*n1*n2
+ *            values in node order: E0 E1 E2 B0 B1 B2, then d_i B_j (i major)
+ *            when g->has_grad.  Values are rounded to g->dtype.
+ * Errors: GCB_EINVAL on a null pointer or inconsistent shape/stride.
+ */
+gcb_status gcb_grid_pack(const gcb_grid *g, const double *const *comp, void *cuda_stream);
+
+/*
+ * Split float64 positions into float32 pairs (hi = fl32(x), lo = fl32(x - hi))
+ * and back (x = hi + lo in float64): conversion of a GCB_POS_F64 state to
+ * GCB_POS_F32PAIR storage.  All pointers are device arrays of n elements.
+ */
+gcb_status gcb_pos_split(int64_t n, const double *x, float *hi, float *lo, void *cuda_stream);
+gcb_status gcb_pos_join(int64_t n, const float *hi, const float *lo, double *x, void *cuda_stream);
+
+/* Workspace bytes gcb_push_sr needs for this problem (a device buffer). */
+size_t gcb_workspace_bytes(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm);
+
+/*
+ * Advance every particle by n_steps coupled steps (Sec. 3.1), in place.
+ *   p, g, prm : problem description (host structs, device arrays).
+ *   n_steps   : >= 0; each step is one kernel pass over all particles, so
+ *               the state round-trips HBM every step as in a PiC code.
+ *   stream    : cudaStream_t (NULL = legacy default stream).
+ *   ws        : device workspace of at least gcb_workspace_bytes() bytes,
+ *               256-byte aligned; contents on entry are ignored.
+ *   out       : host gcb_stats, or NULL.  When non-NULL the call
+ *               synchronizes `stream` and fills it; otherwise it returns
+ *               without synchronizing.
+ * Supported precisions: (mom_dtype F64, pos F64, grid F64) = FP64 path;
+ * (mom_dtype F32, pos F64 or F32PAIR, grid F32) = mixed path.
+ * Per-particle numerical events are not errors: they set GCB_FLAG_* bits
+ * and counters.  No device-side trap or assert exists; every loop is bounded.
+ */
+gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                       int n_steps, void *cuda_stream, void *ws, size_t ws_bytes,
+                       gcb_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCB_H */

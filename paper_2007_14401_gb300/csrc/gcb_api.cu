@@ -1,0 +1,279 @@
+// gcb_api.cu -- host side of the C ABI declared in include/gcb.h: argument
+// checks, the step loop, the workspace counters, and the small layout kernels
+// (node-record packing, FP32-pair position split/join).
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "gcb.h"
+#include "gcb_internal.h"
+
+namespace gcb {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+static gcb_status check_grid(const gcb_grid *g)
+{
+    if (!g) { set_error("grid is NULL"); return GCB_EINVAL; }
+    if (g->ndim != 2 && g->ndim != 3) { set_error("grid ndim must be 2 or 3"); return GCB_EINVAL; }
+    if (g->dtype != GCB_F32 && g->dtype != GCB_F64) { set_error("grid dtype"); return GCB_EINVAL; }
+    int64_t nn = 1;
+    for (int d = 0; d < 3; ++d) {
+        int64_t n = g->n[d];
+        if (d >= g->ndim && n != 1) { set_error("grid n[%d] must be 1 in %dD", d, g->ndim); return GCB_EINVAL; }
+        if (d < g->ndim && (n < 2 || !(g->dx[d] > 0.0))) {
+            set_error("grid axis %d needs n >= 2 and dx > 0", d);
+            return GCB_EINVAL;
+        }
+        nn *= n;
+    }
+    if (nn >= (int64_t(1) << 31)) { set_error("grid has too many nodes (>= 2^31)"); return GCB_EUNSUPPORTED; }
+    if (g->stride != gcb_grid_stride(g->ndim, g->dtype, g->has_grad)) {
+        set_error("grid stride %d does not match gcb_grid_stride", g->stride);
+        return GCB_EINVAL;
+    }
+    if (!g->rec || !aligned(g->rec, 16)) { set_error("grid records NULL or not 16-byte aligned"); return GCB_EINVAL; }
+    return GCB_OK;
+}
+
+}  // namespace gcb
+
+using namespace gcb;
+
+extern "C" {
+
+int gcb_version(void) { return 100; }
+
+const char *gcb_status_string(gcb_status s)
+{
+    switch (s) {
+    case GCB_OK: return "GCB_OK";
+    case GCB_EINVAL: return "GCB_EINVAL";
+    case GCB_ECUDA: return "GCB_ECUDA";
+    case GCB_EUNSUPPORTED: return "GCB_EUNSUPPORTED";
+    case GCB_ENOMEM: return "GCB_ENOMEM";
+    }
+    return "GCB_UNKNOWN";
+}
+
+const char *gcb_last_error(void) { return g_err; }
+
+int32_t gcb_grid_stride(int32_t ndim, int32_t dtype, int32_t has_grad)
+{
+    if ((ndim != 2 && ndim != 3) || (dtype != GCB_F32 && dtype != GCB_F64)) return 0;
+    int need = 6 + (has_grad ? 3 * ndim : 0);
+    int chunk = dtype == GCB_F32 ? 4 : 2;  // elements per 16 bytes
+    return (need + chunk - 1) / chunk * chunk;
+}
+
+size_t gcb_workspace_bytes(const gcb_particles *, const gcb_grid *, const gcb_params *)
+{
+    return kStatsBytes;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// layout kernels
+// ---------------------------------------------------------------------------
+struct PackSrc {
+    const double *c[15];
+};
+
+template <typename T>
+__global__ void k_pack(T *rec, int stride, int ncomp, int64_t nnodes, PackSrc src)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnodes;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T *r = rec + i * stride;
+        for (int c = 0; c < stride; ++c) r[c] = c < ncomp ? (T)src.c[c][i] : T(0);
+    }
+}
+
+__global__ void k_split(int64_t n, const double *x, float *hi, float *lo)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = x[i];
+        float h = (float)v;
+        hi[i] = h;
+        lo[i] = (float)(v - (double)h);
+    }
+}
+
+__global__ void k_join(int64_t n, const float *hi, const float *lo, double *x)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (double)hi[i] + (double)lo[i];
+}
+
+static int grid_for(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+static gcb_status launch_check(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("%s: %s", what, cudaGetErrorString(e));
+        return GCB_ECUDA;
+    }
+    return GCB_OK;
+}
+
+extern "C" {
+
+gcb_status gcb_grid_pack(const gcb_grid *g, const double *const *comp, void *cuda_stream)
+{
+    gcb_status s = check_grid(g);
+    if (s != GCB_OK) return s;
+    if (!comp) { set_error("component list is NULL"); return GCB_EINVAL; }
+    int ncomp = 6 + (g->has_grad ? 3 * g->ndim : 0);
+    PackSrc src;
+    memset(&src, 0, sizeof(src));
+    for (int c = 0; c < ncomp; ++c) {
+        if (!comp[c] || !aligned(comp[c], 8)) { set_error("component %d NULL or misaligned", c); return GCB_EINVAL; }
+        src.c[c] = comp[c];
+    }
+    int64_t nn = g->n[0] * g->n[1] * g->n[2];
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (g->dtype == GCB_F32)
+        k_pack<float><<<grid_for(nn), 256, 0, st>>>((float *)g->rec, g->stride, ncomp, nn, src);
+    else
+        k_pack<double><<<grid_for(nn), 256, 0, st>>>((double *)g->rec, g->stride, ncomp, nn, src);
+    return launch_check("gcb_grid_pack");
+}
+
+gcb_status gcb_pos_split(int64_t n, const double *x, float *hi, float *lo, void *cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!x || !hi || !lo))) { set_error("gcb_pos_split: bad arguments"); return GCB_EINVAL; }
+    if (n == 0) return GCB_OK;
+    k_split<<<grid_for(n), 256, 0, (cudaStream_t)cuda_stream>>>(n, x, hi, lo);
+    return launch_check("gcb_pos_split");
+}
+
+gcb_status gcb_pos_join(int64_t n, const float *hi, const float *lo, double *x, void *cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!x || !hi || !lo))) { set_error("gcb_pos_join: bad arguments"); return GCB_EINVAL; }
+    if (n == 0) return GCB_OK;
+    k_join<<<grid_for(n), 256, 0, (cudaStream_t)cuda_stream>>>(n, hi, lo, x);
+    return launch_check("gcb_pos_join");
+}
+
+gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                       int n_steps, void *cuda_stream, void *ws, size_t ws_bytes, gcb_stats *out)
+{
+    g_err[0] = 0;
+    gcb_status s = check_grid(g);
+    if (s != GCB_OK) return s;
+    if (!p || !prm) { set_error("particles or params NULL"); return GCB_EINVAL; }
+    if (n_steps < 0) { set_error("n_steps < 0"); return GCB_EINVAL; }
+    if (p->n < 0) { set_error("particle count < 0"); return GCB_EINVAL; }
+    if (p->ndim != g->ndim) { set_error("particle ndim %d != grid ndim %d", p->ndim, g->ndim); return GCB_EINVAL; }
+    if (!(prm->c > 0) || !(prm->dt > 0) || !(prm->f_rho > 0) || !(prm->f_E > 0) || !(prm->dl > 0)) {
+        set_error("c, dt, f_rho, f_E and dl must be > 0");
+        return GCB_EINVAL;
+    }
+    if (prm->curvature != 0 && prm->curvature != 1) { set_error("curvature must be 0 or 1"); return GCB_EINVAL; }
+    if (prm->mu_mode != GCB_MU_CONSERVE && prm->mu_mode != GCB_UPERP_CONSERVE) { set_error("mu_mode"); return GCB_EINVAL; }
+    if (prm->grad_mode != GCB_GRAD_DW && prm->grad_mode != GCB_GRAD_GRID) { set_error("grad_mode"); return GCB_EINVAL; }
+    if (prm->grad_mode == GCB_GRAD_GRID && !g->has_grad) { set_error("grad_mode GRID needs gradient records"); return GCB_EINVAL; }
+    if (prm->force < GCB_FORCE_NONE || prm->force > GCB_FORCE_GCA) { set_error("force"); return GCB_EINVAL; }
+    if (prm->gca_max_iter < 1 || prm->gca_max_iter > 1000 || prm->gca_fixed_iters < 0 ||
+        prm->gca_fixed_iters > 1000) {
+        set_error("gca_max_iter must be in [1, 1000] and gca_fixed_iters in [0, 1000]");
+        return GCB_EINVAL;
+    }
+    if (!(prm->gca_tol >= 0)) { set_error("gca_tol must be >= 0"); return GCB_EINVAL; }
+
+    bool fp64 = p->mom_dtype == GCB_F64;
+    if (fp64) {
+        if (p->pos_mode != GCB_POS_F64 || g->dtype != GCB_F64) {
+            set_error("FP64 momenta need GCB_POS_F64 positions and an F64 grid");
+            return GCB_EUNSUPPORTED;
+        }
+    } else if (p->mom_dtype == GCB_F32) {
+        if (g->dtype != GCB_F32) { set_error("FP32 momenta need an F32 grid"); return GCB_EUNSUPPORTED; }
+        if (p->pos_mode != GCB_POS_F64 && p->pos_mode != GCB_POS_F32PAIR) { set_error("pos_mode"); return GCB_EINVAL; }
+        if (p->pos_mode == GCB_POS_F32PAIR) {
+            for (int d = 0; d < g->ndim; ++d) {
+                double L = (double)g->n[d] * g->dx[d];
+                if ((double)(float)L != L || (double)(float)g->dx[d] != g->dx[d]) {
+                    set_error("FP32-pair positions need n*dx and dx exact in float");
+                    return GCB_EUNSUPPORTED;
+                }
+            }
+        }
+    } else {
+        set_error("mom_dtype");
+        return GCB_EINVAL;
+    }
+    if (p->n > 0) {
+        size_t me = fp64 ? 8 : 4;
+        size_t pe = p->pos_mode == GCB_POS_F64 ? 8 : 4;
+        for (int d = 0; d < p->ndim; ++d) {
+            if (!p->x[d] || !aligned(p->x[d], pe) || !p->dxp[d] || !aligned(p->dxp[d], me)) {
+                set_error("x[%d] or dxp[%d] NULL or misaligned", d, d);
+                return GCB_EINVAL;
+            }
+            if (p->pos_mode == GCB_POS_F32PAIR && (!p->x_lo[d] || !aligned(p->x_lo[d], 4))) {
+                set_error("x_lo[%d] NULL or misaligned", d);
+                return GCB_EINVAL;
+            }
+        }
+        for (int k = 0; k < 3; ++k)
+            if (!p->u[k] || !aligned(p->u[k], me)) { set_error("u[%d] NULL or misaligned", k); return GCB_EINVAL; }
+        if (!p->flags) { set_error("flags NULL"); return GCB_EINVAL; }
+    }
+    if (!ws || !aligned(ws, 256)) { set_error("workspace NULL or not 256-byte aligned"); return GCB_EINVAL; }
+    if (ws_bytes < kStatsBytes) { set_error("workspace too small"); return GCB_ENOMEM; }
+
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    unsigned long long *stats = (unsigned long long *)ws;
+    if (cudaMemsetAsync(stats, 0, kStatsBytes, st) != cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(cudaGetLastError()));
+        return GCB_ECUDA;
+    }
+    for (int step = 0; step < n_steps; ++step) {
+        s = fp64 ? push_step_f64(p, g, prm, st, stats) : push_step_f32(p, g, prm, st, stats);
+        if (s != GCB_OK) return s;
+    }
+    if (out) {
+        unsigned long long h[ST_COUNT];
+        if (cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("stats readback: %s", cudaGetErrorString(cudaGetLastError()));
+            return GCB_ECUDA;
+        }
+        out->n_boris = (int64_t)h[ST_BORIS];
+        out->n_gca = (int64_t)h[ST_GCA];
+        out->n_to_gca = (int64_t)h[ST_TO_GCA];
+        out->n_to_boris = (int64_t)h[ST_TO_BORIS];
+        out->n_nonconv = (int64_t)h[ST_NONCONV];
+        out->n_gcafail = (int64_t)h[ST_GCAFAIL];
+        out->n_nonfinite = (int64_t)h[ST_NONFINITE];
+        out->sum_iter = (int64_t)h[ST_SUM_ITER];
+        out->max_iter = (int64_t)h[ST_MAX_ITER];
+        double e;
+        memcpy(&e, &h[ST_EKIN], sizeof(e));
+        out->sum_ekin = e;
+    }
+    return GCB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,28 @@
+// gcb_internal.h -- declarations shared by the host API (gcb_api.cu) and the
+// per-precision kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gcb.h"
+
+namespace gcb {
+
+// Device workspace layout of gcb_push_sr (unsigned long long slots).
+enum {
+    ST_BORIS = 0, ST_GCA, ST_TO_GCA, ST_TO_BORIS, ST_NONCONV, ST_GCAFAIL, ST_NONFINITE,
+    ST_SUM_ITER, ST_MAX_ITER, ST_EKIN, ST_COUNT
+};
+constexpr size_t kStatsBytes = 256;
+
+void set_error(const char *fmt, ...);
+
+// One kernel pass (one step) over all particles; stats accumulate into the
+// device counters `stats` (ST_* layout).  Defined per precision.
+gcb_status push_step_f64(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                         cudaStream_t st, unsigned long long *stats);
+gcb_status push_step_f32(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                         cudaStream_t st, unsigned long long *stats);
+
+}  // namespace gcb

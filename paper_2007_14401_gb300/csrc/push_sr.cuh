@@ -1,0 +1,442 @@
+// push_sr.cuh -- one coupled step (Sec. 3.1) over all particles, one kernel.
+//
+// Each block walks tiles of TPB consecutive particles (persistent grid):
+//   phase 1  every thread loads one particle (coalesced SoA loads), gathers
+//            E, B at x^n, evaluates the switch S and stages the particle in
+//            shared memory;
+//   compact  a warp ballot per branch plus a block prefix over the per-warp
+//            counts orders the tile's slots as [GCA ..., Boris ..., frozen],
+//            so all warps but one run a single branch and GCA lanes run the
+//            same loop (the queues of the GCA and Boris branches);
+//   phase 2  thread t advances the particle in slot perm[t];
+//   phase 3  the tile is written back in particle order (coalesced).
+// Counters are reduced per block and added atomically to the workspace.
+#pragma once
+
+#include "gcb_device.cuh"
+#include "gcb_internal.h"
+
+namespace gcb {
+
+constexpr int TPB = 256;
+constexpr int NWARP = TPB / 32;
+
+template <typename R>
+struct PushArgs {
+    DevGrid<R> g;
+    double L[3];              // box length per axis
+    double dxd[3], inv_dxd[3];
+    float Lf[3];              // box length in float (pair positions)
+    int64_t np;
+    void *x[3];               // double (PM 0) or float hi (PM 1)
+    float *xlo[3];
+    R *u[3];
+    R *dxp[3];
+    uint8_t *flags;
+    StepPar<R> sp;            // sp.qm is set per particle
+    R qm[4];
+    R rho_thr;                // f_rho * dl
+    R f_E;
+    R c2;
+    int force;
+    unsigned long long *stats;
+};
+
+template <int PM>
+struct PosType;
+template <>
+struct PosType<0> { using T = double; };
+template <>
+struct PosType<1> { using T = float; };
+
+// x (stored) -> base cell index and offset from the cell origin.
+template <typename R>
+__device__ __forceinline__ void split_pos_f64(double x, double dxd, double inv_dxd, int &ib, R &l)
+{
+    double fl = fmin(fmax(floor(x * inv_dxd), -1e9), 1e9);
+    ib = (int)fl;
+    l = (R)fma(-fl, dxd, x);
+}
+__device__ __forceinline__ void split_pos_pair(float h, float lo, float dx, float inv_dx, int &ib,
+                                               float &l)
+{
+    float fl = fminf(fmaxf(floorf(h * inv_dx), -1e9f), 1e9f);
+    ib = (int)fl;
+    l = fmaf(-fl, dx, h) + lo;
+}
+
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (h, lo) += d for an FP32-pair position, then wrap into [0, L).
+__device__ __forceinline__ void pair_add_wrap(float &h, float &lo, float d, float L)
+{
+    float s, e;
+    two_sum(h, d, s, e);
+    e += lo;
+    h = s + e;
+    lo = e - (h - s);
+    if (h < 0.0f) {
+        two_sum(h, L, s, e);
+        e += lo;
+        h = s + e;
+        lo = e - (h - s);
+    }
+    if (h >= L) {
+        h -= L;  // exact: L <= h < 2L
+        float t = h + lo;
+        lo = lo - (t - h);
+        h = t;
+    }
+    if (h < 0.0f || h >= L) {  // lo pushed the sum across an edge
+        h = 0.0f;
+        lo = 0.0f;
+    }
+}
+
+__device__ __forceinline__ double wrap_f64(double x, double L)
+{
+    if (x < 0.0) x += L;
+    if (x >= L) x -= L;
+    return x;
+}
+
+template <typename R>
+__device__ __forceinline__ bool finite_r(R v) { return isfinite(v); }
+
+template <typename R, int ND, int PM, int GM>
+__global__ void __launch_bounds__(TPB) k_push_sr(const PushArgs<R> a)
+{
+    using PosT = typename PosType<PM>::T;
+    __shared__ PosT s_x[ND][TPB];
+    __shared__ float s_xl[PM ? ND : 1][TPB];
+    __shared__ R s_l[ND][TPB];
+    __shared__ int s_ib[ND][TPB];
+    __shared__ R s_u[3][TPB];
+    __shared__ R s_d[ND][TPB];
+    __shared__ R s_eb[6][TPB];
+    __shared__ uint8_t s_fl[TPB];
+    __shared__ uint8_t s_cls[TPB];
+    __shared__ unsigned short s_perm[TPB];
+    __shared__ int s_wc[2][NWARP];
+    __shared__ unsigned long long s_acc[ST_COUNT];
+    __shared__ double s_ek;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < ST_COUNT) s_acc[tid] = 0ull;
+    if (tid == 0) s_ek = 0.0;
+
+    unsigned nb = 0, ng = 0, tg = 0, tb = 0, nc = 0, gf = 0, nf = 0, si = 0, mi = 0;
+    double ek = 0.0;
+
+    const int64_t ntiles = (a.np + TPB - 1) / TPB;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t i = tile * TPB + tid;
+        const bool valid = i < a.np;
+        int cls = 2;
+        uint8_t fl = 0;
+        PosT xs[ND];
+        float xl[ND];
+        R l[ND], uu[3], dd[ND], E[3] = {R(0), R(0), R(0)}, B[3] = {R(0), R(0), R(0)};
+        int ib[ND];
+        if (valid) {
+            fl = a.flags[i];
+            bool fin = true;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                xs[d] = reinterpret_cast<const PosT *>(a.x[d])[i];
+                xl[d] = PM ? a.xlo[d][i] : 0.0f;
+                dd[d] = a.dxp[d][i];
+                fin = fin && finite_r(xs[d]) && finite_r(xl[d]) && finite_r(dd[d]);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                uu[k] = a.u[k][i];
+                fin = fin && finite_r(uu[k]);
+            }
+            if (fin) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    if (PM == 0)
+                        split_pos_f64<R>((double)xs[d], a.dxd[d], a.inv_dxd[d], ib[d], l[d]);
+                    else {
+                        float lf;
+                        split_pos_pair((float)xs[d], xl[d], (float)a.g.dx[d], (float)a.g.inv_dx[d],
+                                       ib[d], lf);
+                        l[d] = (R)lf;
+                    }
+                }
+                FieldPt<R, ND> F;
+                gather<R, ND, 0>(a.g, ib, l, F);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { E[k] = F.E[k]; B[k] = F.B[k]; }
+                // switch S (Sec. 3, Sec. 4.1) in division-free form:
+                // S = 0 iff c^2 Gamma < f_rho dl |q/m| B and |E| < f_E B.
+                R Q = fabs(a.qm[(fl >> GCB_SPECIES_SHIFT) & 3]);
+                R G = sqrt(R(1) + dot3(uu, uu) * a.sp.inv_c2);
+                R Bm = sqrt(dot3(B, B));
+                R Em = sqrt(dot3(E, E));
+                int S = (a.c2 * G < a.rho_thr * Q * Bm && Em < a.f_E * Bm) ? 0 : 1;
+                if (a.force == GCB_FORCE_BORIS) S = 1;
+                if (a.force == GCB_FORCE_GCA) S = 0;
+                cls = S;
+            } else {
+                fl |= GCB_FLAG_NONFINITE;
+                ++nf;
+            }
+        }
+        __syncthreads();  // the previous tile is written out
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            if (valid) {
+                s_x[d][tid] = xs[d];
+                if (PM) s_xl[d][tid] = xl[d];
+                s_d[d][tid] = dd[d];
+                s_l[d][tid] = l[d];
+                s_ib[d][tid] = ib[d];
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                s_u[k][tid] = uu[k];
+                s_eb[k][tid] = E[k];
+                s_eb[3 + k][tid] = B[k];
+            }
+        }
+        s_fl[tid] = fl;
+        s_cls[tid] = (uint8_t)cls;
+        const unsigned bgm = __ballot_sync(0xffffffffu, cls == 0);
+        const unsigned bbm = __ballot_sync(0xffffffffu, cls == 1);
+        if (lane == 0) {
+            s_wc[0][warp] = __popc(bgm);
+            s_wc[1][warp] = __popc(bbm);
+        }
+        __syncthreads();
+        int offG = 0, offB = 0, totG = 0, totB = 0;
+#pragma unroll
+        for (int w = 0; w < NWARP; ++w) {
+            int cg = s_wc[0][w], cb = s_wc[1][w];
+            if (w < warp) { offG += cg; offB += cb; }
+            totG += cg;
+            totB += cb;
+        }
+        const unsigned lt = (1u << lane) - 1u;
+        if (cls == 0) s_perm[offG + __popc(bgm & lt)] = (unsigned short)tid;
+        if (cls == 1) s_perm[totG + offB + __popc(bbm & lt)] = (unsigned short)tid;
+        __syncthreads();
+
+        // phase 2: advance slot perm[tid]
+        if (tid < totG + totB) {
+            const int sl = s_perm[tid];
+            const bool isg = tid < totG;
+            uint8_t f0 = s_fl[sl];
+            StepPar<R> sp = a.sp;
+            sp.qm = a.qm[(f0 >> GCB_SPECIES_SHIFT) & 3];
+            int ibs[ND];
+            R ls[ND], ds[ND], us[3], disp[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) { ibs[d] = s_ib[d][sl]; ls[d] = s_l[d][sl]; ds[d] = s_d[d][sl]; }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) us[k] = s_u[k][sl];
+            int it = 0;
+            bool ncv = false, fail = false;
+            bool done = false;
+            if (isg) {
+                done = gca_step<R, ND, GM>(a.g, sp, ibs, ls, ds, us, disp, it, ncv);
+                if (!done) {
+                    fail = true;
+                    it = 0;
+                    ncv = false;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) us[k] = s_u[k][sl];
+                }
+            }
+            if (!done) {
+                R Ee[3], Bb[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { Ee[k] = s_eb[k][sl]; Bb[k] = s_eb[3 + k][sl]; }
+                boris<R, ND>(Ee, Bb, sp, us, disp);
+            }
+            // store: x^{n+1} = x^n + disp (wrapped), dxp = disp
+            PosT xn[ND];
+            float xln[ND];
+            bool fin = true;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                if (PM == 0) {
+                    xn[d] = (PosT)wrap_f64((double)s_x[d][sl] + (double)disp[d], a.L[d]);
+                    xln[d] = 0.0f;
+                } else {
+                    float h = (float)s_x[d][sl], lo = s_xl[d][sl];
+                    pair_add_wrap(h, lo, (float)disp[d], a.Lf[d]);
+                    xn[d] = (PosT)h;
+                    xln[d] = lo;
+                }
+                fin = fin && finite_r(disp[d]);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) fin = fin && finite_r(us[k]);
+            const int Sprev = f0 & GCB_FLAG_S;
+            const int Snew = isg ? 0 : 1;
+            uint8_t nfl = (uint8_t)((f0 & 0xC0) | (Sprev ? GCB_FLAG_SPREV : 0) | (Snew ? GCB_FLAG_S : 0));
+            if (fin) {
+                if (fail) nfl |= GCB_FLAG_GCAFAIL;
+                if (ncv) nfl |= GCB_FLAG_NONCONV;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    s_x[d][sl] = xn[d];
+                    if (PM) s_xl[d][sl] = xln[d];
+                    s_d[d][sl] = disp[d];
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s_u[k][sl] = us[k];
+                if (done) ++ng; else ++nb;
+                if (Sprev && !Snew) ++tg;
+                if (!Sprev && Snew) ++tb;
+                if (ncv) ++nc;
+                if (fail) ++gf;
+                si += it;
+                mi = max(mi, (unsigned)it);
+                R u2 = dot3(us, us) * sp.inv_c2;
+                ek += (double)(u2 / (R(1) + sqrt(R(1) + u2)));
+            } else {
+                nfl |= GCB_FLAG_NONFINITE;
+                ++nf;
+            }
+            s_fl[sl] = nfl;
+        }
+        __syncthreads();
+
+        // phase 3: write the tile back in particle order
+        if (valid) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                reinterpret_cast<PosT *>(a.x[d])[i] = s_x[d][tid];
+                if (PM) a.xlo[d][i] = s_xl[d][tid];
+                a.dxp[d][i] = s_d[d][tid];
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) a.u[k][i] = s_u[k][tid];
+            a.flags[i] = s_fl[tid];
+        }
+    }
+
+    // block reduction of the counters
+    unsigned vals[9] = {nb, ng, tg, tb, nc, gf, nf, si, mi};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        unsigned v = __reduce_add_sync(0xffffffffu, vals[k]);
+        if (lane == 0 && v) atomicAdd(&s_acc[k], (unsigned long long)v);
+    }
+    unsigned m = __reduce_max_sync(0xffffffffu, vals[8]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ek += __shfl_xor_sync(0xffffffffu, ek, o);
+    __syncthreads();
+    if (lane == 0) {
+        if (m) atomicMax(&s_acc[ST_MAX_ITER], (unsigned long long)m);
+        atomicAdd(&s_ek, ek);
+    }
+    __syncthreads();
+    if (tid < ST_MAX_ITER) {
+        if (s_acc[tid]) atomicAdd(&a.stats[tid], s_acc[tid]);
+    } else if (tid == ST_MAX_ITER) {
+        if (s_acc[tid]) atomicMax(&a.stats[tid], s_acc[tid]);
+    } else if (tid == ST_EKIN) {
+        atomicAdd(reinterpret_cast<double *>(&a.stats[ST_EKIN]), s_ek);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side: argument packing and launch
+// ---------------------------------------------------------------------------
+template <typename R>
+static void fill_args(PushArgs<R> &a, const gcb_particles *p, const gcb_grid *g,
+                      const gcb_params *prm, unsigned long long *stats)
+{
+    a.g.rec = static_cast<const R *>(g->rec);
+    a.g.stride = g->stride;
+    for (int d = 0; d < 3; ++d) {
+        a.g.n[d] = (int)g->n[d];
+        a.g.dx[d] = (R)g->dx[d];
+        a.g.inv_dx[d] = (R)(1.0 / g->dx[d]);
+        a.L[d] = (double)g->n[d] * g->dx[d];
+        a.Lf[d] = (float)a.L[d];
+        a.dxd[d] = g->dx[d];
+        a.inv_dxd[d] = 1.0 / g->dx[d];
+        a.x[d] = p->x[d];
+        a.xlo[d] = static_cast<float *>(p->x_lo[d]);
+        a.u[d] = static_cast<R *>(p->u[d]);
+        a.dxp[d] = static_cast<R *>(p->dxp[d]);
+    }
+    a.np = p->n;
+    a.flags = p->flags;
+    a.sp.c = (R)prm->c;
+    a.sp.inv_c2 = (R)(1.0 / (prm->c * prm->c));
+    a.sp.dt = (R)prm->dt;
+    a.sp.half_dt = (R)(0.5 * prm->dt);
+    a.sp.qm = R(0);
+    a.sp.curvature = prm->curvature;
+    a.sp.mu_mode = prm->mu_mode;
+    a.sp.max_iter = prm->gca_max_iter;
+    a.sp.fixed_iters = prm->gca_fixed_iters;
+    a.sp.tol = (R)prm->gca_tol;
+    for (int k = 0; k < 4; ++k) a.qm[k] = (R)prm->qm[k];
+    a.rho_thr = (R)(prm->f_rho * prm->dl);
+    a.f_E = (R)prm->f_E;
+    a.c2 = (R)(prm->c * prm->c);
+    a.force = prm->force;
+    a.stats = stats;
+}
+
+template <typename R, int ND, int PM, int GM>
+static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
+{
+    static int grid_cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        set_error("cudaGetDevice failed");
+        return GCB_ECUDA;
+    }
+    int grid = grid_cache[dev];
+    if (grid == 0) {
+        int nsm = 0, occ = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM>, TPB, 0) !=
+                cudaSuccess) {
+            set_error("occupancy query failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return GCB_ECUDA;
+        }
+        grid = nsm * (occ > 0 ? occ : 1);
+        grid_cache[dev] = grid;
+    }
+    int64_t ntiles = (a.np + TPB - 1) / TPB;
+    if (ntiles == 0) return GCB_OK;
+    int nb = (int)(ntiles < grid ? ntiles : grid);
+    k_push_sr<R, ND, PM, GM><<<nb, TPB, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("kernel launch failed: %s", cudaGetErrorString(e));
+        return GCB_ECUDA;
+    }
+    return GCB_OK;
+}
+
+template <typename R, int PM>
+static gcb_status dispatch_push(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                                cudaStream_t st, unsigned long long *stats)
+{
+    PushArgs<R> a;
+    fill_args<R>(a, p, g, prm, stats);
+    const bool grid_grad = prm->grad_mode == GCB_GRAD_GRID;
+    if (g->ndim == 2)
+        return grid_grad ? launch_push<R, 2, PM, 2>(a, st) : launch_push<R, 2, PM, 1>(a, st);
+    return grid_grad ? launch_push<R, 3, PM, 2>(a, st) : launch_push<R, 3, PM, 1>(a, st);
+}
+
+}  // namespace gcb

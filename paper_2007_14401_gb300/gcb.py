@@ -1,0 +1,261 @@
+"""ctypes binding of the CUDA C-ABI library ``libgcb.so`` (declared in include/gcb.h).
+
+Argument marshalling only: device memory comes from PyTorch tensors, every
+step of the push runs in the library's kernels.  Importing this module loads
+the library and raises if it has not been built (no CPU fallback exists).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+F32, F64 = 0, 1
+POS_F64, POS_F32PAIR = 0, 1
+GRAD_DW, GRAD_GRID = 0, 1
+FORCE_NONE, FORCE_BORIS, FORCE_GCA = 0, 1, 2
+MU_CONSERVE, UPERP_CONSERVE = 0, 1
+FLAG_S, FLAG_SPREV, FLAG_NONCONV, FLAG_GCAFAIL, FLAG_NONFINITE = 1, 2, 4, 8, 16
+SPECIES_SHIFT = 6
+STATUS = {0: "GCB_OK", 1: "GCB_EINVAL", 2: "GCB_ECUDA", 3: "GCB_EUNSUPPORTED", 4: "GCB_ENOMEM"}
+
+
+class GcbGrid(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("dtype", C.c_int32), ("n", C.c_int64 * 3),
+                ("dx", C.c_double * 3), ("has_grad", C.c_int32), ("stride", C.c_int32),
+                ("rec", C.c_void_p)]
+
+
+class GcbParticles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("ndim", C.c_int32), ("pos_mode", C.c_int32),
+                ("mom_dtype", C.c_int32), ("reserved", C.c_int32), ("x", C.c_void_p * 3),
+                ("x_lo", C.c_void_p * 3), ("u", C.c_void_p * 3), ("dxp", C.c_void_p * 3),
+                ("flags", C.c_void_p)]
+
+
+class GcbParams(C.Structure):
+    _fields_ = [("c", C.c_double), ("dt", C.c_double), ("f_rho", C.c_double),
+                ("f_E", C.c_double), ("dl", C.c_double), ("qm", C.c_double * 4),
+                ("curvature", C.c_int32), ("mu_mode", C.c_int32), ("grad_mode", C.c_int32),
+                ("force", C.c_int32), ("gca_max_iter", C.c_int32),
+                ("gca_fixed_iters", C.c_int32), ("gca_tol", C.c_double)]
+
+
+class GcbStats(C.Structure):
+    _fields_ = [("n_boris", C.c_int64), ("n_gca", C.c_int64), ("n_to_gca", C.c_int64),
+                ("n_to_boris", C.c_int64), ("n_nonconv", C.c_int64), ("n_gcafail", C.c_int64),
+                ("n_nonfinite", C.c_int64), ("sum_iter", C.c_int64), ("max_iter", C.c_int64),
+                ("sum_ekin", C.c_double)]
+
+
+EXPORTS = ["gcb_version", "gcb_status_string", "gcb_last_error", "gcb_grid_stride",
+           "gcb_grid_pack", "gcb_pos_split", "gcb_pos_join", "gcb_workspace_bytes",
+           "gcb_push_sr"]
+
+
+def load_library(path: str | None = None):
+    """Load libgcb.so and declare its signatures (raises if missing)."""
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: call paper_2007_14401_gb300.build.build()")
+    lib = C.CDLL(path)
+    P = C.POINTER
+    lib.gcb_version.restype = C.c_int
+    lib.gcb_status_string.argtypes = [C.c_int]
+    lib.gcb_status_string.restype = C.c_char_p
+    lib.gcb_last_error.restype = C.c_char_p
+    lib.gcb_grid_stride.argtypes = [C.c_int32, C.c_int32, C.c_int32]
+    lib.gcb_grid_stride.restype = C.c_int32
+    lib.gcb_grid_pack.argtypes = [P(GcbGrid), P(C.c_void_p), C.c_void_p]
+    lib.gcb_grid_pack.restype = C.c_int
+    lib.gcb_pos_split.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.gcb_pos_split.restype = C.c_int
+    lib.gcb_pos_join.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.gcb_pos_join.restype = C.c_int
+    lib.gcb_workspace_bytes.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams)]
+    lib.gcb_workspace_bytes.restype = C.c_size_t
+    lib.gcb_push_sr.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int,
+                                C.c_void_p, C.c_void_p, C.c_size_t, P(GcbStats)]
+    lib.gcb_push_sr.restype = C.c_int
+    return lib
+
+
+_lib = load_library()
+
+
+def lib():
+    return _lib
+
+
+class GcbError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = _lib.gcb_last_error().decode()
+        raise GcbError(f"{what}: {STATUS.get(rc, rc)}: {msg}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# field grid
+# --------------------------------------------------------------------------
+class Grid:
+    """A field grid in the library's packed node-record layout (device)."""
+
+    def __init__(self, fields: dict, dtype: str = "f32", device="cuda", stream=None):
+        E, B, dB = fields["E"], fields["B"], fields.get("dB")
+        shape = np.asarray(E[0]).shape
+        self.ndim = len(shape)
+        self.n = tuple(reversed(shape)) + (1,) * (3 - len(shape))
+        self.dx = tuple(fields["dx"]) + (1.0,) * (3 - self.ndim)
+        self.dtype = F32 if dtype == "f32" else F64
+        self.has_grad = 1 if dB is not None else 0
+        self.stride = _lib.gcb_grid_stride(self.ndim, self.dtype, self.has_grad)
+        nn = int(np.prod(shape))
+        tdt = torch.float32 if self.dtype == F32 else torch.float64
+        self.rec = torch.empty(nn * self.stride, dtype=tdt, device=device)
+        comps = list(E) + list(B) + (list(dB) if dB is not None else [])
+        dev = [torch.as_tensor(np.ascontiguousarray(c, dtype=np.float64).reshape(-1)).to(device)
+               for c in comps]
+        self.s = GcbGrid(self.ndim, self.dtype, (C.c_int64 * 3)(*self.n),
+                         (C.c_double * 3)(*self.dx), self.has_grad, self.stride,
+                         self.rec.data_ptr())
+        ptrs = (C.c_void_p * len(dev))(*[t.data_ptr() for t in dev])
+        _check(_lib.gcb_grid_pack(C.byref(self.s), ptrs, _stream_ptr(stream)), "gcb_grid_pack")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    @property
+    def L(self):
+        return tuple(self.n[d] * self.dx[d] for d in range(self.ndim))
+
+
+# --------------------------------------------------------------------------
+# particle state
+# --------------------------------------------------------------------------
+class State:
+    """Particle state on the device in the library's SoA layout.
+
+    precision "fp64": float64 positions and momenta;  "mixed": float32
+    momenta and displacements, positions float64 (pos_mode "f64") or float32
+    pairs (pos_mode "pair")."""
+
+    def __init__(self, n, ndim, precision="mixed", pos_mode="pair", device="cuda"):
+        self.n, self.ndim, self.precision = int(n), int(ndim), precision
+        self.pos_mode = POS_F32PAIR if (precision == "mixed" and pos_mode == "pair") else POS_F64
+        self.mom_dtype = F64 if precision == "fp64" else F32
+        mdt = torch.float64 if self.mom_dtype == F64 else torch.float32
+        if self.pos_mode == POS_F64:
+            self.x = torch.empty((ndim, self.n), dtype=torch.float64, device=device)
+            self.x_lo = None
+        else:
+            self.x = torch.empty((ndim, self.n), dtype=torch.float32, device=device)
+            self.x_lo = torch.empty((ndim, self.n), dtype=torch.float32, device=device)
+        self.u = torch.empty((3, self.n), dtype=mdt, device=device)
+        self.dxp = torch.empty((ndim, self.n), dtype=mdt, device=device)
+        self.flags = torch.empty((self.n,), dtype=torch.uint8, device=device)
+        self._make_struct()
+
+    def _make_struct(self):
+        s = GcbParticles()
+        s.n, s.ndim, s.pos_mode, s.mom_dtype, s.reserved = (self.n, self.ndim, self.pos_mode,
+                                                            self.mom_dtype, 0)
+        for d in range(self.ndim):
+            s.x[d] = self.x[d].data_ptr()
+            s.dxp[d] = self.dxp[d].data_ptr()
+            if self.x_lo is not None:
+                s.x_lo[d] = self.x_lo[d].data_ptr()
+        for k in range(3):
+            s.u[k] = self.u[k].data_ptr()
+        s.flags = self.flags.data_ptr()
+        self.s = s
+
+    def tensors(self):
+        t = [self.x, self.u, self.dxp, self.flags]
+        return t + ([self.x_lo] if self.x_lo is not None else [])
+
+    @classmethod
+    def from_numpy(cls, st: dict, precision="mixed", pos_mode="pair", device="cuda", stream=None):
+        nd, n = st["x"].shape
+        self = cls(n, nd, precision, pos_mode, device)
+        self.load(st, stream)
+        return self
+
+    def load(self, st: dict, stream=None):
+        """Copy a plain float64 state (oracle layout) into this device state."""
+        mdt = self.u.dtype
+        x64 = torch.as_tensor(np.ascontiguousarray(st["x"], dtype=np.float64)).to(self.x.device)
+        if self.pos_mode == POS_F64:
+            self.x.copy_(x64)
+        elif self.n:
+            for d in range(self.ndim):
+                _check(_lib.gcb_pos_split(self.n, C.c_void_p(x64[d].data_ptr()),
+                                          C.c_void_p(self.x[d].data_ptr()),
+                                          C.c_void_p(self.x_lo[d].data_ptr()), _stream_ptr(stream)),
+                       "gcb_pos_split")
+        self.u.copy_(torch.as_tensor(np.asarray(st["u"], dtype=np.float64)).to(mdt))
+        self.dxp.copy_(torch.as_tensor(np.asarray(st["dxp"], dtype=np.float64)).to(mdt))
+        self.flags.copy_(torch.as_tensor(np.asarray(st["flags"], dtype=np.uint8)))
+        torch.cuda.synchronize()
+
+    def to_numpy(self, stream=None) -> dict:
+        """The state as plain float64 arrays (positions joined from pairs)."""
+        if self.pos_mode == POS_F64:
+            x = self.x.double()
+        else:
+            x = torch.empty((self.ndim, self.n), dtype=torch.float64, device=self.x.device)
+            if self.n:
+                for d in range(self.ndim):
+                    _check(_lib.gcb_pos_join(self.n, C.c_void_p(self.x[d].data_ptr()),
+                                             C.c_void_p(self.x_lo[d].data_ptr()),
+                                             C.c_void_p(x[d].data_ptr()), _stream_ptr(stream)),
+                           "gcb_pos_join")
+        torch.cuda.synchronize()
+        return dict(x=x.cpu().numpy(), u=self.u.double().cpu().numpy(),
+                    dxp=self.dxp.double().cpu().numpy(), flags=self.flags.cpu().numpy())
+
+
+# --------------------------------------------------------------------------
+# parameters and the push
+# --------------------------------------------------------------------------
+def make_params(p: dict, **over) -> GcbParams:
+    q = dict(p)
+    q.update(over)
+    qm = list(q["qm"]) + [0.0] * (4 - len(q["qm"]))
+    return GcbParams(q.get("c", 1.0), q["dt"], q.get("f_rho", 0.4), q.get("f_E", 1.0),
+                     q.get("dl", 1.0), (C.c_double * 4)(*qm), int(q.get("curvature", 1)),
+                     int(q.get("mu_mode", 0)), int(q.get("grad_mode", 0)), int(q.get("force", 0)),
+                     int(q.get("gca_max_iter", 16)), int(q.get("gca_fixed_iters", 0)),
+                     float(q.get("gca_tol", 1e-7)))
+
+
+class Workspace:
+    def __init__(self, state: State, grid: Grid, params: GcbParams, device="cuda"):
+        nb = _lib.gcb_workspace_bytes(C.byref(state.s), C.byref(grid.s), C.byref(params))
+        self.buf = torch.empty(max(256, (nb + 255) // 256 * 256), dtype=torch.uint8, device=device)
+        self.nbytes = self.buf.numel()
+
+
+def push(state: State, grid: Grid, params: GcbParams, n_steps: int = 1, stream=None,
+         workspace: Workspace | None = None, stats: bool = True):
+    """Advance ``state`` by n_steps coupled steps in place; returns the stats
+    dict (synchronizing the stream) when ``stats`` is true, else None."""
+    ws = workspace or Workspace(state, grid, params, state.x.device)
+    out = GcbStats() if stats else None
+    rc = _lib.gcb_push_sr(C.byref(state.s), C.byref(grid.s), C.byref(params), int(n_steps),
+                          _stream_ptr(stream), C.c_void_p(ws.buf.data_ptr()), ws.nbytes,
+                          C.byref(out) if stats else None)
+    _check(rc, "gcb_push_sr")
+    if stats:
+        return {k: getattr(out, k) for k, _ in GcbStats._fields_}
+    return None
