@@ -105,6 +105,8 @@ typedef struct {
     void *u[3];
     void *dxp[3];
     uint8_t *flags;          /* n bytes, see GCB_FLAG_* */
+    int64_t *pid;            /* optional particle ids (NULL = none); sorting
+                                permutes them with the particles */
 } gcb_particles;
 
 typedef struct {
@@ -120,6 +122,10 @@ typedef struct {
     int32_t gca_max_iter;    /* bound of the fixed-point iteration (>= 1) */
     int32_t gca_fixed_iters; /* > 0: exactly this many iterations, no test */
     double gca_tol;          /* absolute tolerance on |R^{k+1}-R^k|_inf (Sec. 2.2) */
+    int32_t sort_every;      /* > 0: sort the particles by cell tile before every
+                                step whose global index is a multiple of it */
+    int32_t sort_tile[3];    /* cells per sort tile along each axis (0 = 8,8,4) */
+    int64_t step_index;      /* global index of the first step of this call */
 } gcb_params;
 
 /* Counters of one gcb_push_sr call, summed over its steps. */
@@ -162,14 +168,31 @@ gcb_status gcb_grid_pack(const gcb_grid *g, const double *const *comp, void *cud
 gcb_status gcb_pos_split(int64_t n, const double *x, float *hi, float *lo, void *cuda_stream);
 gcb_status gcb_pos_join(int64_t n, const float *hi, const float *lo, double *x, void *cuda_stream);
 
-/* Workspace bytes gcb_push_sr needs for this problem (a device buffer). */
+/* Workspace bytes gcb_push_sr / gcb_sort_sr need for this problem (a device
+ * buffer): 256 bytes of counters, plus, when prm->sort_every > 0 (always for
+ * gcb_sort_sr), per-particle keys and one copy of the particle arrays. */
 size_t gcb_workspace_bytes(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm);
+
+/*
+ * Reorder the particles in place by the tile of cells that holds them (tiles
+ * of prm->sort_tile cells, row-major over tiles; non-finite particles last),
+ * a counting sort on the device.  Gathers of particles that are close in
+ * memory then touch the same few field records, which the L1 cache holds.
+ * The order inside a tile is not specified; pid, when given, is permuted
+ * with the particles.  ws as for gcb_push_sr with sorting enabled.
+ * This is a layout step of the GPU design, not part of the paper's method.
+ */
+gcb_status gcb_sort_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                       void *cuda_stream, void *ws, size_t ws_bytes);
 
 /*
  * Advance every particle by n_steps coupled steps (Sec. 3.1), in place.
  *   p, g, prm : problem description (host structs, device arrays).
  *   n_steps   : >= 0; each step is one kernel pass over all particles, so
  *               the state round-trips HBM every step as in a PiC code.
+ *               With prm->sort_every > 0 the particles are first reordered
+ *               (as gcb_sort_sr) before steps whose global index
+ *               prm->step_index + j is a multiple of sort_every.
  *   stream    : cudaStream_t (NULL = legacy default stream).
  *   ws        : device workspace of at least gcb_workspace_bytes() bytes,
  *               256-byte aligned; contents on entry are ignored.

@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libgcb.so")
 OBJ_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["gcb_api.cu", "push_sr_f64.cu", "push_sr_f32.cu"]
+SOURCES = ["gcb_api.cu", "sort_sr.cu", "push_sr_f64.cu", "push_sr_f32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

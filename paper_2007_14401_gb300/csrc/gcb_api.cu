@@ -8,6 +8,7 @@
 
 #include "gcb.h"
 #include "gcb_internal.h"
+#include "sort_sr.h"
 
 namespace gcb {
 
@@ -77,9 +78,12 @@ int32_t gcb_grid_stride(int32_t ndim, int32_t dtype, int32_t has_grad)
     return (need + chunk - 1) / chunk * chunk;
 }
 
-size_t gcb_workspace_bytes(const gcb_particles *, const gcb_grid *, const gcb_params *)
+size_t gcb_workspace_bytes(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm)
 {
-    return kStatsBytes;
+    if (!p || !g || !prm || prm->sort_every <= 0 || p->n <= 0) return kStatsBytes;
+    SortPlan pl;
+    if (!sort_plan(p, g, prm, pl)) return kStatsBytes;
+    return pl.total;
 }
 
 }  // extern "C"
@@ -175,14 +179,11 @@ gcb_status gcb_pos_join(int64_t n, const float *hi, const float *lo, double *x, 
     return launch_check("gcb_pos_join");
 }
 
-gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
-                       int n_steps, void *cuda_stream, void *ws, size_t ws_bytes, gcb_stats *out)
+static gcb_status check_problem(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm)
 {
-    g_err[0] = 0;
     gcb_status s = check_grid(g);
     if (s != GCB_OK) return s;
     if (!p || !prm) { set_error("particles or params NULL"); return GCB_EINVAL; }
-    if (n_steps < 0) { set_error("n_steps < 0"); return GCB_EINVAL; }
     if (p->n < 0) { set_error("particle count < 0"); return GCB_EINVAL; }
     if (p->ndim != g->ndim) { set_error("particle ndim %d != grid ndim %d", p->ndim, g->ndim); return GCB_EINVAL; }
     if (!(prm->c > 0) || !(prm->dt > 0) || !(prm->f_rho > 0) || !(prm->f_E > 0) || !(prm->dl > 0)) {
@@ -200,6 +201,11 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
         return GCB_EINVAL;
     }
     if (!(prm->gca_tol >= 0)) { set_error("gca_tol must be >= 0"); return GCB_EINVAL; }
+    if (prm->sort_every < 0 || prm->sort_tile[0] < 0 || prm->sort_tile[1] < 0 ||
+        prm->sort_tile[2] < 0 || prm->step_index < 0) {
+        set_error("sort_every, sort_tile and step_index must be >= 0");
+        return GCB_EINVAL;
+    }
 
     bool fp64 = p->mom_dtype == GCB_F64;
     if (fp64) {
@@ -239,9 +245,55 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
         for (int k = 0; k < 3; ++k)
             if (!p->u[k] || !aligned(p->u[k], me)) { set_error("u[%d] NULL or misaligned", k); return GCB_EINVAL; }
         if (!p->flags) { set_error("flags NULL"); return GCB_EINVAL; }
+        if (p->pid && !aligned(p->pid, 8)) { set_error("pid misaligned"); return GCB_EINVAL; }
     }
+    return GCB_OK;
+}
+
+// Sort into the workspace; `q` becomes the view of the sorted copy.
+static gcb_status sort_step(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                            cudaStream_t st, void *ws, size_t ws_bytes, gcb_particles &q,
+                            SortPlan &pl, SortedView &v)
+{
+    if (p->n >= (int64_t(1) << 31)) { set_error("sorting needs n < 2^31"); return GCB_EUNSUPPORTED; }
+    if (!sort_plan(p, g, prm, pl)) { set_error("too many sort tiles"); return GCB_EUNSUPPORTED; }
+    if (ws_bytes < pl.total) {
+        set_error("workspace too small for sorting (%zu < %zu bytes)", ws_bytes, pl.total);
+        return GCB_ENOMEM;
+    }
+    gcb_status s = sort_into_workspace(p, g, pl, st, (uint8_t *)ws, v);
+    if (s != GCB_OK) return s;
+    sorted_particles(p, g->ndim, v, q);
+    return GCB_OK;
+}
+
+gcb_status gcb_sort_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                       void *cuda_stream, void *ws, size_t ws_bytes)
+{
+    g_err[0] = 0;
+    gcb_status s = check_problem(p, g, prm);
+    if (s != GCB_OK) return s;
+    if (!ws || !aligned(ws, 256)) { set_error("workspace NULL or not 256-byte aligned"); return GCB_EINVAL; }
+    if (p->n == 0) return GCB_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    gcb_particles q;
+    SortPlan pl;
+    SortedView v;
+    s = sort_step(p, g, prm, st, ws, ws_bytes, q, pl, v);
+    if (s != GCB_OK) return s;
+    return copy_back(p, g, pl, v, st);
+}
+
+gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                       int n_steps, void *cuda_stream, void *ws, size_t ws_bytes, gcb_stats *out)
+{
+    g_err[0] = 0;
+    gcb_status s = check_problem(p, g, prm);
+    if (s != GCB_OK) return s;
+    if (n_steps < 0) { set_error("n_steps < 0"); return GCB_EINVAL; }
     if (!ws || !aligned(ws, 256)) { set_error("workspace NULL or not 256-byte aligned"); return GCB_EINVAL; }
     if (ws_bytes < kStatsBytes) { set_error("workspace too small"); return GCB_ENOMEM; }
+    const bool fp64 = p->mom_dtype == GCB_F64;
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     unsigned long long *stats = (unsigned long long *)ws;
@@ -250,7 +302,16 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
         return GCB_ECUDA;
     }
     for (int step = 0; step < n_steps; ++step) {
-        s = fp64 ? push_step_f64(p, g, prm, st, stats) : push_step_f32(p, g, prm, st, stats);
+        const gcb_particles *in = p;
+        gcb_particles q;
+        if (prm->sort_every > 0 && p->n > 0 && (prm->step_index + step) % prm->sort_every == 0) {
+            SortPlan pl;
+            SortedView v;
+            s = sort_step(p, g, prm, st, ws, ws_bytes, q, pl, v);
+            if (s != GCB_OK) return s;
+            in = &q;
+        }
+        s = fp64 ? push_step_f64(p, in, g, prm, st, stats) : push_step_f32(p, in, g, prm, st, stats);
         if (s != GCB_OK) return s;
     }
     if (out) {

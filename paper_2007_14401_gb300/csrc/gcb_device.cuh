@@ -319,18 +319,18 @@ __device__ __forceinline__ void boris(const R E[3], const R B[3], const StepPar<
 }
 
 // Guiding-center step (Sec. 3.1 with Sec. 2.2.1 / 2.2.2) from local x^n = ln
-// in base cell ib, previous displacement dxp and full u^{n-1/2}.  Returns
+// in base cell ib (fields there: F0), previous displacement dxp and full
+// u^{n-1/2}.  Returns
 // false when the step cannot be taken (B = 0 or v_E >= c on the path, or no
 // Lorentz factor >= 1 solves the quadratic); u and disp are then untouched.
 template <typename R, int ND, int GM>
 __device__ __forceinline__ bool gca_step(const DevGrid<R> &g, const StepPar<R> &s, const int ib[ND],
-                                         const R ln[ND], const R dxp[ND], R u[3], R disp[ND],
-                                         int &iters, bool &nonconv)
+                                         const R ln[ND], const R dxp[ND], const FieldPt<R, ND> &F0,
+                                         R u[3], R disp[ND], int &iters, bool &nonconv)
 {
     FieldPt<R, ND> F;
     Frame<R> f0, f;
-    gather<R, ND, GM>(g, ib, ln, F);
-    make_frame<R, ND, (GM != 0)>(F, s.c, s.inv_c2, f0);
+    make_frame<R, ND, (GM != 0)>(F0, s.c, s.inv_c2, f0);
 
     // conversion at R^{n-1/2} = x^n - dxp/2 (Sec. 3.1)
     R pt[ND];

@@ -18,11 +18,12 @@ constexpr size_t kStatsBytes = 256;
 
 void set_error(const char *fmt, ...);
 
-// One kernel pass (one step) over all particles; stats accumulate into the
-// device counters `stats` (ST_* layout).  Defined per precision.
-gcb_status push_step_f64(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
-                         cudaStream_t st, unsigned long long *stats);
-gcb_status push_step_f32(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
-                         cudaStream_t st, unsigned long long *stats);
+// One kernel pass (one step) over all particles, reading the arrays of `in`
+// (the caller's, or a sorted copy) and writing those of `p`; stats accumulate
+// into the device counters `stats` (ST_* layout).  Defined per precision.
+gcb_status push_step_f64(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
+                         const gcb_params *prm, cudaStream_t st, unsigned long long *stats);
+gcb_status push_step_f32(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
+                         const gcb_params *prm, cudaStream_t st, unsigned long long *stats);
 
 }  // namespace gcb

@@ -18,8 +18,10 @@
 
 namespace gcb {
 
-constexpr int TPB = 256;
-constexpr int NWARP = TPB / 32;
+// particles per tile (= threads per block): 256 for FP32, 128 for FP64, where
+// the staged tile would not fit the 48 KB of static shared memory
+template <typename R>
+struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : 256; };
 
 template <typename R>
 struct PushArgs {
@@ -28,11 +30,20 @@ struct PushArgs {
     double dxd[3], inv_dxd[3];
     float Lf[3];              // box length in float (pair positions)
     int64_t np;
+    // input arrays (the caller's, or the sorted copy in the workspace)
+    const void *xin[3];
+    const float *xloin[3];
+    const R *uin[3];
+    const R *dxpin[3];
+    const uint8_t *flagsin;
+    const int64_t *pidin;
+    // output arrays (always the caller's)
     void *x[3];               // double (PM 0) or float hi (PM 1)
     float *xlo[3];
     R *u[3];
     R *dxp[3];
     uint8_t *flags;
+    int64_t *pid;             // written only when pidin differs
     StepPar<R> sp;            // sp.qm is set per particle
     R qm[4];
     R rho_thr;                // f_rho * dl
@@ -110,8 +121,11 @@ template <typename R>
 __device__ __forceinline__ bool finite_r(R v) { return isfinite(v); }
 
 template <typename R, int ND, int PM, int GM>
-__global__ void __launch_bounds__(TPB) k_push_sr(const PushArgs<R> a)
+__global__ void __launch_bounds__(Tile<R>::n) k_push_sr(const PushArgs<R> a)
 {
+    constexpr int TPB = Tile<R>::n;
+    constexpr int NWARP = TPB / 32;
+    constexpr int NF = (GM != 0) ? 6 + 3 * ND : 6;   // staged field values at x^n
     using PosT = typename PosType<PM>::T;
     __shared__ PosT s_x[ND][TPB];
     __shared__ float s_xl[PM ? ND : 1][TPB];
@@ -119,7 +133,7 @@ __global__ void __launch_bounds__(TPB) k_push_sr(const PushArgs<R> a)
     __shared__ int s_ib[ND][TPB];
     __shared__ R s_u[3][TPB];
     __shared__ R s_d[ND][TPB];
-    __shared__ R s_eb[6][TPB];
+    __shared__ R s_F[NF][TPB];
     __shared__ uint8_t s_fl[TPB];
     __shared__ uint8_t s_cls[TPB];
     __shared__ unsigned short s_perm[TPB];
@@ -140,23 +154,26 @@ __global__ void __launch_bounds__(TPB) k_push_sr(const PushArgs<R> a)
         const bool valid = i < a.np;
         int cls = 2;
         uint8_t fl = 0;
+        int64_t pid = 0;
         PosT xs[ND];
         float xl[ND];
-        R l[ND], uu[3], dd[ND], E[3] = {R(0), R(0), R(0)}, B[3] = {R(0), R(0), R(0)};
+        R l[ND], uu[3], dd[ND];
+        FieldPt<R, ND> F;
         int ib[ND];
         if (valid) {
-            fl = a.flags[i];
+            fl = a.flagsin[i];
+            if (a.pidin != a.pid) pid = a.pidin[i];
             bool fin = true;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
-                xs[d] = reinterpret_cast<const PosT *>(a.x[d])[i];
-                xl[d] = PM ? a.xlo[d][i] : 0.0f;
-                dd[d] = a.dxp[d][i];
+                xs[d] = reinterpret_cast<const PosT *>(a.xin[d])[i];
+                xl[d] = PM ? a.xloin[d][i] : 0.0f;
+                dd[d] = a.dxpin[d][i];
                 fin = fin && finite_r(xs[d]) && finite_r(xl[d]) && finite_r(dd[d]);
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                uu[k] = a.u[k][i];
+                uu[k] = a.uin[k][i];
                 fin = fin && finite_r(uu[k]);
             }
             if (fin) {
@@ -171,16 +188,13 @@ __global__ void __launch_bounds__(TPB) k_push_sr(const PushArgs<R> a)
                         l[d] = (R)lf;
                     }
                 }
-                FieldPt<R, ND> F;
-                gather<R, ND, 0>(a.g, ib, l, F);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) { E[k] = F.E[k]; B[k] = F.B[k]; }
+                gather<R, ND, GM>(a.g, ib, l, F);
                 // switch S (Sec. 3, Sec. 4.1) in division-free form:
                 // S = 0 iff c^2 Gamma < f_rho dl |q/m| B and |E| < f_E B.
                 R Q = fabs(a.qm[(fl >> GCB_SPECIES_SHIFT) & 3]);
                 R G = sqrt(R(1) + dot3(uu, uu) * a.sp.inv_c2);
-                R Bm = sqrt(dot3(B, B));
-                R Em = sqrt(dot3(E, E));
+                R Bm = sqrt(dot3(F.B, F.B));
+                R Em = sqrt(dot3(F.E, F.E));
                 int S = (a.c2 * G < a.rho_thr * Q * Bm && Em < a.f_E * Bm) ? 0 : 1;
                 if (a.force == GCB_FORCE_BORIS) S = 1;
                 if (a.force == GCB_FORCE_GCA) S = 0;
@@ -201,13 +215,22 @@ __global__ void __launch_bounds__(TPB) k_push_sr(const PushArgs<R> a)
                 s_ib[d][tid] = ib[d];
             }
         }
-        if (valid) {
+        if (valid && cls != 2) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                s_u[k][tid] = uu[k];
-                s_eb[k][tid] = E[k];
-                s_eb[3 + k][tid] = B[k];
+                s_F[k][tid] = F.E[k];
+                s_F[3 + k][tid] = F.B[k];
             }
+            if (GM != 0) {
+#pragma unroll
+                for (int ii = 0; ii < ND; ++ii)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) s_F[6 + 3 * ii + j][tid] = F.dB[ii][j];
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s_u[k][tid] = uu[k];
         }
         s_fl[tid] = fl;
         s_cls[tid] = (uint8_t)cls;
@@ -247,8 +270,17 @@ __global__ void __launch_bounds__(TPB) k_push_sr(const PushArgs<R> a)
             int it = 0;
             bool ncv = false, fail = false;
             bool done = false;
+            FieldPt<R, ND> F0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { F0.E[k] = s_F[k][sl]; F0.B[k] = s_F[3 + k][sl]; }
             if (isg) {
-                done = gca_step<R, ND, GM>(a.g, sp, ibs, ls, ds, us, disp, it, ncv);
+                if (GM != 0) {
+#pragma unroll
+                    for (int ii = 0; ii < ND; ++ii)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) F0.dB[ii][j] = s_F[6 + 3 * ii + j][sl];
+                }
+                done = gca_step<R, ND, GM>(a.g, sp, ibs, ls, ds, F0, us, disp, it, ncv);
                 if (!done) {
                     fail = true;
                     it = 0;
@@ -257,12 +289,7 @@ __global__ void __launch_bounds__(TPB) k_push_sr(const PushArgs<R> a)
                     for (int k = 0; k < 3; ++k) us[k] = s_u[k][sl];
                 }
             }
-            if (!done) {
-                R Ee[3], Bb[3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) { Ee[k] = s_eb[k][sl]; Bb[k] = s_eb[3 + k][sl]; }
-                boris<R, ND>(Ee, Bb, sp, us, disp);
-            }
+            if (!done) boris<R, ND>(F0.E, F0.B, sp, us, disp);
             // store: x^{n+1} = x^n + disp (wrapped), dxp = disp
             PosT xn[ND];
             float xln[ND];
@@ -324,6 +351,7 @@ __global__ void __launch_bounds__(TPB) k_push_sr(const PushArgs<R> a)
 #pragma unroll
             for (int k = 0; k < 3; ++k) a.u[k][i] = s_u[k][tid];
             a.flags[i] = s_fl[tid];
+            if (a.pidin != a.pid) a.pid[i] = pid;
         }
     }
 
@@ -356,8 +384,8 @@ __global__ void __launch_bounds__(TPB) k_push_sr(const PushArgs<R> a)
 // host side: argument packing and launch
 // ---------------------------------------------------------------------------
 template <typename R>
-static void fill_args(PushArgs<R> &a, const gcb_particles *p, const gcb_grid *g,
-                      const gcb_params *prm, unsigned long long *stats)
+static void fill_args(PushArgs<R> &a, const gcb_particles *p, const gcb_particles *in,
+                      const gcb_grid *g, const gcb_params *prm, unsigned long long *stats)
 {
     a.g.rec = static_cast<const R *>(g->rec);
     a.g.stride = g->stride;
@@ -373,9 +401,16 @@ static void fill_args(PushArgs<R> &a, const gcb_particles *p, const gcb_grid *g,
         a.xlo[d] = static_cast<float *>(p->x_lo[d]);
         a.u[d] = static_cast<R *>(p->u[d]);
         a.dxp[d] = static_cast<R *>(p->dxp[d]);
+        a.xin[d] = in->x[d];
+        a.xloin[d] = static_cast<const float *>(in->x_lo[d]);
+        a.uin[d] = static_cast<const R *>(in->u[d]);
+        a.dxpin[d] = static_cast<const R *>(in->dxp[d]);
     }
     a.np = p->n;
     a.flags = p->flags;
+    a.flagsin = in->flags;
+    a.pid = p->pid;
+    a.pidin = p->pid ? in->pid : nullptr;
     a.sp.c = (R)prm->c;
     a.sp.inv_c2 = (R)(1.0 / (prm->c * prm->c));
     a.sp.dt = (R)prm->dt;
@@ -407,7 +442,7 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     if (grid == 0) {
         int nsm = 0, occ = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM>, TPB, 0) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM>, Tile<R>::n, 0) !=
                 cudaSuccess) {
             set_error("occupancy query failed: %s", cudaGetErrorString(cudaGetLastError()));
             return GCB_ECUDA;
@@ -415,6 +450,7 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
         grid = nsm * (occ > 0 ? occ : 1);
         grid_cache[dev] = grid;
     }
+    constexpr int TPB = Tile<R>::n;
     int64_t ntiles = (a.np + TPB - 1) / TPB;
     if (ntiles == 0) return GCB_OK;
     int nb = (int)(ntiles < grid ? ntiles : grid);
@@ -428,11 +464,11 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
 }
 
 template <typename R, int PM>
-static gcb_status dispatch_push(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
-                                cudaStream_t st, unsigned long long *stats)
+static gcb_status dispatch_push(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
+                                const gcb_params *prm, cudaStream_t st, unsigned long long *stats)
 {
     PushArgs<R> a;
-    fill_args<R>(a, p, g, prm, stats);
+    fill_args<R>(a, p, in, g, prm, stats);
     const bool grid_grad = prm->grad_mode == GCB_GRAD_GRID;
     if (g->ndim == 2)
         return grid_grad ? launch_push<R, 2, PM, 2>(a, st) : launch_push<R, 2, PM, 1>(a, st);

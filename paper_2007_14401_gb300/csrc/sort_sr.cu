@@ -1,0 +1,267 @@
+// sort_sr.cu -- counting sort of the particle arrays by tile of cells.
+//
+// keys    : tile index of every particle (row-major over tiles, non-finite
+//           particles in an extra last bucket); the rank inside the bucket
+//           comes from one atomicAdd per group of equal keys in a warp
+//           (__match_any_sync), so runs of already-sorted particles cost one
+//           atomic per warp.
+// scan    : exclusive prefix sum of the bucket counts (one block).
+// scatter : every array element moves to offset[key] + rank in a copy held
+//           in the workspace.
+// gcb_push_sr then runs its next step from that copy into the caller's
+// arrays, so a sort costs no separate copy back; gcb_sort_sr copies back.
+#include <cuda_runtime.h>
+
+#include "gcb_internal.h"
+#include "sort_sr.h"
+
+namespace gcb {
+
+static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+bool sort_plan(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm, SortPlan &pl)
+{
+    static const int def_tile[3] = {8, 8, 4};
+    int64_t nt = 1;
+    for (int d = 0; d < 3; ++d) {
+        int t = prm && prm->sort_tile[d] > 0 ? prm->sort_tile[d] : def_tile[d];
+        if (d >= g->ndim) t = 1;
+        pl.tile[d] = t;
+        pl.ntile[d] = (int)((g->n[d] + t - 1) / t);
+        nt *= pl.ntile[d];
+    }
+    pl.nbuckets = nt + 1;
+    if (pl.nbuckets >= (int64_t(1) << 31)) return false;
+    size_t n = (size_t)p->n;
+    size_t off = kStatsBytes;
+    pl.off_keys = off;
+    off += align256(n * 4);
+    pl.off_ranks = off;
+    off += align256(n * 4);
+    pl.off_hist = off;
+    off += align256((size_t)pl.nbuckets * 4);
+    // the permuted copy: x[nd], x_lo[nd] (pair), u[3], dxp[nd], flags, pid
+    size_t pe = p->pos_mode == GCB_POS_F64 ? 8 : 4;
+    size_t me = p->mom_dtype == GCB_F64 ? 8 : 4;
+    int na = 0;
+    auto add = [&](size_t es) {
+        pl.off_arr[na] = off;
+        pl.es[na] = (int)es;
+        off += align256(n * es);
+        ++na;
+    };
+    for (int d = 0; d < g->ndim; ++d) add(pe);
+    if (p->pos_mode == GCB_POS_F32PAIR)
+        for (int d = 0; d < g->ndim; ++d) add(4);
+    for (int k = 0; k < 3; ++k) add(me);
+    for (int d = 0; d < g->ndim; ++d) add(me);
+    add(1);
+    add(8);  // pid slot (used when p->pid != NULL)
+    pl.narr = na;
+    pl.total = off;
+    return true;
+}
+
+// the caller's arrays in the order sort_plan lays them out
+static int caller_arrays(const gcb_particles *p, int ndim, void **a)
+{
+    int na = 0;
+    for (int d = 0; d < ndim; ++d) a[na++] = p->x[d];
+    if (p->pos_mode == GCB_POS_F32PAIR)
+        for (int d = 0; d < ndim; ++d) a[na++] = p->x_lo[d];
+    for (int k = 0; k < 3; ++k) a[na++] = p->u[k];
+    for (int d = 0; d < ndim; ++d) a[na++] = p->dxp[d];
+    a[na++] = p->flags;
+    a[na++] = p->pid;
+    return na;
+}
+
+struct KeyArgs {
+    int64_t n;
+    int ndim, pair;
+    const void *x[3];
+    const float *xlo[3];
+    double inv_dx[3];
+    int ncell[3], tile[3], ntile[3];
+    int32_t *keys, *ranks, *hist;
+    int frozen_key;
+};
+
+__global__ void k_sort_keys(const KeyArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        const bool v = i < a.n;
+        const unsigned act = __ballot_sync(0xffffffffu, v);
+        if (!v) continue;
+        int key = 0, mul = 1;
+        bool fin = true;
+        for (int d = 0; d < a.ndim; ++d) {
+            double xd;
+            if (a.pair) {
+                float h = ((const float *)a.x[d])[i], lo = a.xlo[d][i];
+                fin = fin && isfinite(h) && isfinite(lo);
+                xd = (double)h + (double)lo;
+            } else {
+                xd = ((const double *)a.x[d])[i];
+                fin = fin && isfinite(xd);
+            }
+            double c = floor(xd * a.inv_dx[d]);
+            int ci = fin ? (int)fmin(fmax(c, 0.0), (double)(a.ncell[d] - 1)) : 0;
+            key += (ci / a.tile[d]) * mul;
+            mul *= a.ntile[d];
+        }
+        if (!fin) key = a.frozen_key;
+        const unsigned peers = __match_any_sync(act, key);
+        const int leader = __ffs(peers) - 1;
+        const int before = __popc(peers & ((1u << lane) - 1u));
+        int b = 0;
+        if (lane == leader) b = atomicAdd(&a.hist[key], __popc(peers));
+        b = __shfl_sync(peers, b, leader);
+        a.keys[i] = key;
+        a.ranks[i] = b + before;
+    }
+}
+
+// In-place exclusive scan of hist[0..m) by one block of 1024 threads.
+__global__ void k_scan(int32_t *hist, int64_t m)
+{
+    __shared__ int32_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t chunk = (m + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = t * chunk, hi = lo + chunk < m ? lo + chunk : m;
+    int32_t s = 0;
+    for (int64_t k = lo; k < hi; ++k) s += hist[k];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        int32_t v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int32_t run = part[t] - s;
+    for (int64_t k = lo; k < hi; ++k) {
+        int32_t c = hist[k];
+        hist[k] = run;
+        run += c;
+    }
+}
+
+struct ScatterArgs {
+    int64_t n;
+    int na;
+    const void *src[14];
+    void *dst[14];
+    int es[14];
+    const int32_t *keys, *ranks, *off;
+};
+
+__global__ void k_scatter(const ScatterArgs a)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = (int64_t)a.off[a.keys[i]] + a.ranks[i];
+        for (int k = 0; k < a.na; ++k) {
+            if (!a.src[k]) continue;
+            switch (a.es[k]) {
+            case 1: ((uint8_t *)a.dst[k])[j] = ((const uint8_t *)a.src[k])[i]; break;
+            case 4: ((uint32_t *)a.dst[k])[j] = ((const uint32_t *)a.src[k])[i]; break;
+            default: ((uint64_t *)a.dst[k])[j] = ((const uint64_t *)a.src[k])[i]; break;
+            }
+        }
+    }
+}
+
+static int blocks_for(int64_t n, int tpb)
+{
+    int64_t b = (n + tpb - 1) / tpb;
+    const int64_t cap = 152 * 16;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+gcb_status sort_into_workspace(const gcb_particles *p, const gcb_grid *g, const SortPlan &pl,
+                               cudaStream_t st, uint8_t *ws, SortedView &out)
+{
+    if (p->n == 0) return GCB_OK;
+    int32_t *keys = (int32_t *)(ws + pl.off_keys);
+    int32_t *ranks = (int32_t *)(ws + pl.off_ranks);
+    int32_t *hist = (int32_t *)(ws + pl.off_hist);
+    if (cudaMemsetAsync(hist, 0, (size_t)pl.nbuckets * 4, st) != cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(cudaGetLastError()));
+        return GCB_ECUDA;
+    }
+    KeyArgs ka;
+    ka.n = p->n;
+    ka.ndim = g->ndim;
+    ka.pair = p->pos_mode == GCB_POS_F32PAIR;
+    for (int d = 0; d < 3; ++d) {
+        ka.x[d] = p->x[d];
+        ka.xlo[d] = (const float *)p->x_lo[d];
+        ka.inv_dx[d] = 1.0 / g->dx[d];
+        ka.ncell[d] = (int)g->n[d];
+        ka.tile[d] = pl.tile[d];
+        ka.ntile[d] = pl.ntile[d];
+    }
+    ka.keys = keys;
+    ka.ranks = ranks;
+    ka.hist = hist;
+    ka.frozen_key = (int)(pl.nbuckets - 1);
+    k_sort_keys<<<blocks_for(p->n, 256), 256, 0, st>>>(ka);
+    k_scan<<<1, 1024, 0, st>>>(hist, pl.nbuckets);
+    ScatterArgs sa;
+    sa.n = p->n;
+    void *src[14];
+    sa.na = caller_arrays(p, g->ndim, src);
+    for (int k = 0; k < sa.na; ++k) {
+        sa.src[k] = src[k];
+        sa.dst[k] = src[k] ? (void *)(ws + pl.off_arr[k]) : nullptr;
+        sa.es[k] = pl.es[k];
+        out.arr[k] = sa.dst[k];
+    }
+    out.narr = sa.na;
+    sa.keys = keys;
+    sa.ranks = ranks;
+    sa.off = hist;
+    k_scatter<<<blocks_for(p->n, 256), 256, 0, st>>>(sa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("sort kernels: %s", cudaGetErrorString(e));
+        return GCB_ECUDA;
+    }
+    return GCB_OK;
+}
+
+gcb_status copy_back(const gcb_particles *p, const gcb_grid *g, const SortPlan &pl,
+                     const SortedView &v, cudaStream_t st)
+{
+    void *dst[14];
+    int na = caller_arrays(p, g->ndim, dst);
+    for (int k = 0; k < na; ++k) {
+        if (!dst[k]) continue;
+        if (cudaMemcpyAsync(dst[k], v.arr[k], (size_t)p->n * pl.es[k], cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess) {
+            set_error("cudaMemcpyAsync: %s", cudaGetErrorString(cudaGetLastError()));
+            return GCB_ECUDA;
+        }
+    }
+    return GCB_OK;
+}
+
+// The view of a particle set whose arrays are the sorted copy.
+void sorted_particles(const gcb_particles *p, int ndim, const SortedView &v, gcb_particles &q)
+{
+    q = *p;
+    int k = 0;
+    for (int d = 0; d < ndim; ++d) q.x[d] = v.arr[k++];
+    if (p->pos_mode == GCB_POS_F32PAIR)
+        for (int d = 0; d < ndim; ++d) q.x_lo[d] = v.arr[k++];
+    for (int c = 0; c < 3; ++c) q.u[c] = v.arr[k++];
+    for (int d = 0; d < ndim; ++d) q.dxp[d] = v.arr[k++];
+    q.flags = (uint8_t *)v.arr[k++];
+    q.pid = (int64_t *)v.arr[k++];
+}
+
+}  // namespace gcb

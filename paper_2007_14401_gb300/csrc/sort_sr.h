@@ -1,0 +1,36 @@
+// sort_sr.h -- the cell-tile sort of the particle arrays (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "gcb.h"
+
+namespace gcb {
+
+// Workspace layout of a sort: counters | keys | ranks | bucket offsets |
+// one permuted copy of every particle array (256-byte aligned sections).
+struct SortPlan {
+    int tile[3], ntile[3];
+    int64_t nbuckets;
+    size_t off_keys, off_ranks, off_hist;
+    size_t off_arr[14];
+    int es[14];
+    int narr;
+    size_t total;
+};
+
+struct SortedView {
+    void *arr[14];
+    int narr;
+};
+
+bool sort_plan(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm, SortPlan &pl);
+gcb_status sort_into_workspace(const gcb_particles *p, const gcb_grid *g, const SortPlan &pl,
+                               cudaStream_t st, uint8_t *ws, SortedView &out);
+gcb_status copy_back(const gcb_particles *p, const gcb_grid *g, const SortPlan &pl,
+                     const SortedView &v, cudaStream_t st);
+void sorted_particles(const gcb_particles *p, int ndim, const SortedView &v, gcb_particles &q);
+
+}  // namespace gcb

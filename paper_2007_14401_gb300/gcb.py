@@ -34,7 +34,7 @@ class GcbParticles(C.Structure):
     _fields_ = [("n", C.c_int64), ("ndim", C.c_int32), ("pos_mode", C.c_int32),
                 ("mom_dtype", C.c_int32), ("reserved", C.c_int32), ("x", C.c_void_p * 3),
                 ("x_lo", C.c_void_p * 3), ("u", C.c_void_p * 3), ("dxp", C.c_void_p * 3),
-                ("flags", C.c_void_p)]
+                ("flags", C.c_void_p), ("pid", C.c_void_p)]
 
 
 class GcbParams(C.Structure):
@@ -42,7 +42,9 @@ class GcbParams(C.Structure):
                 ("f_E", C.c_double), ("dl", C.c_double), ("qm", C.c_double * 4),
                 ("curvature", C.c_int32), ("mu_mode", C.c_int32), ("grad_mode", C.c_int32),
                 ("force", C.c_int32), ("gca_max_iter", C.c_int32),
-                ("gca_fixed_iters", C.c_int32), ("gca_tol", C.c_double)]
+                ("gca_fixed_iters", C.c_int32), ("gca_tol", C.c_double),
+                ("sort_every", C.c_int32), ("sort_tile", C.c_int32 * 3),
+                ("step_index", C.c_int64)]
 
 
 class GcbStats(C.Structure):
@@ -54,7 +56,7 @@ class GcbStats(C.Structure):
 
 EXPORTS = ["gcb_version", "gcb_status_string", "gcb_last_error", "gcb_grid_stride",
            "gcb_grid_pack", "gcb_pos_split", "gcb_pos_join", "gcb_workspace_bytes",
-           "gcb_push_sr"]
+           "gcb_sort_sr", "gcb_push_sr"]
 
 
 def load_library(path: str | None = None):
@@ -81,6 +83,9 @@ def load_library(path: str | None = None):
     lib.gcb_push_sr.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int,
                                 C.c_void_p, C.c_void_p, C.c_size_t, P(GcbStats)]
     lib.gcb_push_sr.restype = C.c_int
+    lib.gcb_sort_sr.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_void_p,
+                                C.c_void_p, C.c_size_t]
+    lib.gcb_sort_sr.restype = C.c_int
     return lib
 
 
@@ -150,7 +155,8 @@ class State:
     momenta and displacements, positions float64 (pos_mode "f64") or float32
     pairs (pos_mode "pair")."""
 
-    def __init__(self, n, ndim, precision="mixed", pos_mode="pair", device="cuda"):
+    def __init__(self, n, ndim, precision="mixed", pos_mode="pair", device="cuda",
+                 with_pid=False):
         self.n, self.ndim, self.precision = int(n), int(ndim), precision
         self.pos_mode = POS_F32PAIR if (precision == "mixed" and pos_mode == "pair") else POS_F64
         self.mom_dtype = F64 if precision == "fp64" else F32
@@ -164,6 +170,7 @@ class State:
         self.u = torch.empty((3, self.n), dtype=mdt, device=device)
         self.dxp = torch.empty((ndim, self.n), dtype=mdt, device=device)
         self.flags = torch.empty((self.n,), dtype=torch.uint8, device=device)
+        self.pid = torch.arange(self.n, dtype=torch.int64, device=device) if with_pid else None
         self._make_struct()
 
     def _make_struct(self):
@@ -178,16 +185,19 @@ class State:
         for k in range(3):
             s.u[k] = self.u[k].data_ptr()
         s.flags = self.flags.data_ptr()
+        s.pid = self.pid.data_ptr() if self.pid is not None else None
         self.s = s
 
     def tensors(self):
         t = [self.x, self.u, self.dxp, self.flags]
-        return t + ([self.x_lo] if self.x_lo is not None else [])
+        t += [self.x_lo] if self.x_lo is not None else []
+        return t + ([self.pid] if self.pid is not None else [])
 
     @classmethod
-    def from_numpy(cls, st: dict, precision="mixed", pos_mode="pair", device="cuda", stream=None):
+    def from_numpy(cls, st: dict, precision="mixed", pos_mode="pair", device="cuda", stream=None,
+                   with_pid=False):
         nd, n = st["x"].shape
-        self = cls(n, nd, precision, pos_mode, device)
+        self = cls(n, nd, precision, pos_mode, device, with_pid)
         self.load(st, stream)
         return self
 
@@ -221,8 +231,11 @@ class State:
                                              C.c_void_p(x[d].data_ptr()), _stream_ptr(stream)),
                            "gcb_pos_join")
         torch.cuda.synchronize()
-        return dict(x=x.cpu().numpy(), u=self.u.double().cpu().numpy(),
-                    dxp=self.dxp.double().cpu().numpy(), flags=self.flags.cpu().numpy())
+        out = dict(x=x.cpu().numpy(), u=self.u.double().cpu().numpy(),
+                   dxp=self.dxp.double().cpu().numpy(), flags=self.flags.cpu().numpy())
+        if self.pid is not None:
+            out["pid"] = self.pid.cpu().numpy()
+        return out
 
 
 # --------------------------------------------------------------------------
@@ -232,11 +245,13 @@ def make_params(p: dict, **over) -> GcbParams:
     q = dict(p)
     q.update(over)
     qm = list(q["qm"]) + [0.0] * (4 - len(q["qm"]))
+    tile = list(q.get("sort_tile", (0, 0, 0))) + [0, 0, 0]
     return GcbParams(q.get("c", 1.0), q["dt"], q.get("f_rho", 0.4), q.get("f_E", 1.0),
                      q.get("dl", 1.0), (C.c_double * 4)(*qm), int(q.get("curvature", 1)),
                      int(q.get("mu_mode", 0)), int(q.get("grad_mode", 0)), int(q.get("force", 0)),
                      int(q.get("gca_max_iter", 16)), int(q.get("gca_fixed_iters", 0)),
-                     float(q.get("gca_tol", 1e-7)))
+                     float(q.get("gca_tol", 1e-7)), int(q.get("sort_every", 0)),
+                     (C.c_int32 * 3)(*tile[:3]), int(q.get("step_index", 0)))
 
 
 class Workspace:
@@ -244,6 +259,18 @@ class Workspace:
         nb = _lib.gcb_workspace_bytes(C.byref(state.s), C.byref(grid.s), C.byref(params))
         self.buf = torch.empty(max(256, (nb + 255) // 256 * 256), dtype=torch.uint8, device=device)
         self.nbytes = self.buf.numel()
+
+
+def sort(state: State, grid: Grid, params: GcbParams, stream=None,
+         workspace: Workspace | None = None):
+    """Reorder the particles by cell tile in place (pid follows)."""
+    if workspace is None:
+        q = GcbParams.from_buffer_copy(params)
+        q.sort_every = max(1, q.sort_every)
+        workspace = Workspace(state, grid, q, state.x.device)
+    rc = _lib.gcb_sort_sr(C.byref(state.s), C.byref(grid.s), C.byref(params), _stream_ptr(stream),
+                          C.c_void_p(workspace.buf.data_ptr()), workspace.nbytes)
+    _check(rc, "gcb_sort_sr")
 
 
 def push(state: State, grid: Grid, params: GcbParams, n_steps: int = 1, stream=None,
