@@ -223,7 +223,14 @@ def main():
     barrier()
     clocks = clk.stop()
     ms = t0.elapsed_time(t1)
-    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    # steps that began with a sort run 3 more kernels; the push kernel's own
+    # duration is taken from the steps without one
+    first = args.warmup
+    sorted_step = [args.sort_every > 0 and (first + k) % args.sort_every == 0
+                   for k in range(args.steps)]
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    launch_ms = [t for t, srt in zip(step_ms, sorted_step) if not srt] or step_ms
+    n_sorts = sum(sorted_step)
     tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
@@ -290,7 +297,11 @@ def main():
                              "alg_bytes_per_particle_step": 2 * STATE_B + FIELD_B / n,
                              "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
                 "e2e": e2e,
-                "gpu_launches": args.steps,
+                "gpu_launches": args.steps + 3 * n_sorts,
+                "sort": {"every": args.sort_every, "sorts_in_timed_region": n_sorts,
+                         "ms_step_with_sort": (sum(t for t, q in zip(step_ms, sorted_step) if q)
+                                               / max(1, n_sorts)),
+                         "ms_push_kernel": sum(launch_ms) / len(launch_ms)},
                 "clocks": clocks,
                 "branch_mix": {"boris": stats["n_boris"], "gca": stats["n_gca"],
                                "mean_iter": stats["sum_iter"] / max(1, stats["n_gca"]),

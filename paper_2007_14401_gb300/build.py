@@ -19,6 +19,10 @@ LIB = os.path.join(OUT_DIR, "libgcb.so")
 OBJ_DIR = os.path.join(HERE, "_build")
 
 SOURCES = ["gcb_api.cu", "sort_sr.cu", "push_sr_f64.cu", "push_sr_f32.cu"]
+# the mixed-precision unit uses approximate FP32 division and square root
+# (about 2 ulp) and flushes FP32 denormals; it holds no FP64 arithmetic that
+# these flags would touch.  The FP64 path keeps IEEE operations throughout.
+EXTRA = {"push_sr_f32.cu": ["-use_fast_math"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -46,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OBJ_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *NVFLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *NVFLAGS, *EXTRA.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -33,6 +33,7 @@ struct DevGrid {
     const R *rec;       // node records, `stride` elements each
     int stride;
     int n[3];           // nodes per axis
+    R nR[3];            // n as R
     R dx[3], inv_dx[3];
 };
 
@@ -58,12 +59,28 @@ __device__ __forceinline__ void load_chunk(const double *p, double *v)
 template <typename R>
 struct Chunk { static constexpr int n = 16 / sizeof(R); };
 
-// Node index along an axis, periodic: any int maps into [0, n).
-__device__ __forceinline__ int wrap_node(int i, int n)
+// Cell of local offset l along axis d: fractional position t in the cell and
+// the periodic node indices i0 (left) and i1 (right).  ib is in [0, n); the
+// cell offset is clamped to [-n, n] (NaN to -n), so one conditional add or
+// subtract of n always lands in [0, n): every access stays inside the grid
+// whatever the offset (an offset of more than one box length, possible only
+// for a broken step, is clamped rather than wrapped).
+template <typename R>
+__device__ __forceinline__ void cell_of(const DevGrid<R> &g, int d, int ib, R l, R &t, int &i0,
+                                        int &i1)
 {
-    if ((unsigned)i < (unsigned)n) return i;
-    int r = i % n;
-    return r < 0 ? r + n : r;
+    const int n = g.n[d];
+    R s = l * g.inv_dx[d];
+    R c = floor(s);
+    t = s - c;
+    c = fmin(fmax(c, -g.nR[d]), g.nR[d]);
+    int i = ib + (int)c;
+    i += i < 0 ? n : 0;
+    i -= i >= n ? n : 0;
+    int j = i + 1;
+    j -= j >= n ? n : 0;
+    i0 = i;
+    i1 = j;
 }
 
 // Linear-shape-function gather (Sec. 4 intro): F(x) = sum_N F_N W(x - x_N),
@@ -78,16 +95,7 @@ __device__ __forceinline__ void gather(const DevGrid<R> &g, const int ib[ND], co
     int i0[ND], i1[ND];
     R t[ND];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        R s = l[d] * g.inv_dx[d];
-        R c = floor(s);
-        t[d] = s - c;
-        // clamp before the conversion (NaN maps to the lower bound), so the
-        // node index below is always in range whatever the offset
-        int i = ib[d] + (int)fmin(fmax(c, R(-1048576)), R(1048576));
-        i0[d] = wrap_node(i, g.n[d]);
-        i1[d] = wrap_node(i + 1, g.n[d]);
-    }
+    for (int d = 0; d < ND; ++d) cell_of(g, d, ib[d], l[d], t[d], i0[d], i1[d]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) { F.E[k] = R(0); F.B[k] = R(0); }
     if (GM != 0) {
@@ -146,6 +154,106 @@ __device__ __forceinline__ void gather(const DevGrid<R> &g, const int ib[ND], co
                 for (int j = 0; j < 3; ++j) F.dB[i][j] = fma(v[6 + 3 * i + j], W, F.dB[i][j]);
         }
     }
+}
+
+// FP32 gather with Blackwell's packed FP32x2 FMA: the record is consumed as
+// float pairs, each node adds W * pair to a pair accumulator.  Same sums as
+// gather<float> (one rounding per FMA), half the FMA instructions.
+template <int ND, int GM>
+__device__ __forceinline__ void gather_x2(const DevGrid<float> &g, const int ib[ND],
+                                          const float l[ND], FieldPt<float, ND> &F)
+{
+    int i0[ND], i1[ND];
+    float t[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) cell_of(g, d, ib[d], l[d], t[d], i0[d], i1[d]);
+    constexpr int NEED = (GM == 2) ? 6 + 3 * ND : 6;
+    constexpr int NQ = (NEED + 3) / 4;          // float4 chunks read per record
+    constexpr int NP = 2 * NQ;                  // float pairs accumulated
+    float2 acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = make_float2(0.f, 0.f);
+    float2 dacc[ND][2];                          // grad-W mode: d_i (B0,B1), d_i (B2,-)
+    if (GM == 1) {
+#pragma unroll
+        for (int i = 0; i < ND; ++i) dacc[i][0] = dacc[i][1] = make_float2(0.f, 0.f);
+    }
+    constexpr int NC = 1 << ND;
+#pragma unroll
+    for (int o = 0; o < NC; ++o) {
+        int node;
+        float w[ND];
+        if (ND == 2) {
+            int ix = (o & 1) ? i1[0] : i0[0];
+            int iy = (o & 2) ? i1[1] : i0[1];
+            node = iy * g.n[0] + ix;
+        } else {
+            int ix = (o & 1) ? i1[0] : i0[0];
+            int iy = (o & 2) ? i1[1] : i0[1];
+            int iz = (o & 4) ? i1[ND - 1] : i0[ND - 1];
+            node = (iz * g.n[1] + iy) * g.n[0] + ix;
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) w[d] = ((o >> d) & 1) ? t[d] : 1.f - t[d];
+        float W = w[0];
+#pragma unroll
+        for (int d = 1; d < ND; ++d) W *= w[d];
+        const float2 W2 = make_float2(W, W);
+        const float4 *rp = reinterpret_cast<const float4 *>(g.rec + (size_t)node * g.stride);
+        float2 pr[NP];
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+            float4 q = __ldg(rp + c);
+            pr[2 * c] = make_float2(q.x, q.y);
+            pr[2 * c + 1] = make_float2(q.z, q.w);
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) acc[k] = __ffma2_rn(pr[k], W2, acc[k]);
+        if (GM == 1) {
+            // pairs 1 and 2 hold (E2, B0) and (B1, B2)
+            const float2 b01 = make_float2(pr[1].y, pr[2].x);
+            const float2 b2 = make_float2(pr[2].y, 0.f);
+#pragma unroll
+            for (int i = 0; i < ND; ++i) {
+                float gw = ((o >> i) & 1) ? g.inv_dx[i] : -g.inv_dx[i];
+#pragma unroll
+                for (int e = 0; e < ND; ++e)
+                    if (e != i) gw *= w[e];
+                const float2 G2 = make_float2(gw, gw);
+                dacc[i][0] = __ffma2_rn(b01, G2, dacc[i][0]);
+                dacc[i][1] = __ffma2_rn(b2, G2, dacc[i][1]);
+            }
+        }
+    }
+    float v[2 * NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) { v[2 * k] = acc[k].x; v[2 * k + 1] = acc[k].y; }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { F.E[k] = v[k]; F.B[k] = v[3 + k]; }
+    if (GM == 2) {
+#pragma unroll
+        for (int i = 0; i < ND; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) F.dB[i][j] = v[6 + 3 * i + j];
+    } else if (GM == 1) {
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+            F.dB[i][0] = dacc[i][0].x;
+            F.dB[i][1] = dacc[i][0].y;
+            F.dB[i][2] = dacc[i][1].x;
+        }
+    }
+}
+
+// The gather used by the kernels: packed FP32x2 for float, scalar for double.
+template <typename R, int ND, int GM>
+__device__ __forceinline__ void gather_any(const DevGrid<R> &g, const int ib[ND], const R l[ND],
+                                           FieldPt<R, ND> &F)
+{
+    if constexpr (sizeof(R) == 4)
+        gather_x2<ND, GM>(g, ib, l, F);
+    else
+        gather<R, ND, GM>(g, ib, l, F);
 }
 
 template <typename R>
@@ -336,7 +444,7 @@ __device__ __forceinline__ bool gca_step(const DevGrid<R> &g, const StepPar<R> &
     R pt[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) pt[d] = fma(R(-0.5), dxp[d], ln[d]);
-    gather<R, ND, GM>(g, ib, pt, F);
+    gather_any<R, ND, GM>(g, ib, pt, F);
     make_frame<R, ND, (GM != 0)>(F, s.c, s.inv_c2, f);
     if (!(f0.ok && f.ok)) return false;
     R Gfull = sqrt(R(1) + dot3(u, u) * s.inv_c2);
@@ -395,6 +503,7 @@ __device__ __forceinline__ bool gca_step(const DevGrid<R> &g, const StepPar<R> &
     R V[3] = {Vn[0], Vn[1], Vn[2]};
     iters = 0;
     nonconv = false;
+    bool okall = true;
     for (;;) {
         R res = R(0), big = R(0);
 #pragma unroll
@@ -415,16 +524,17 @@ __device__ __forceinline__ bool gca_step(const DevGrid<R> &g, const StepPar<R> &
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) pt[d] = ln[d] + dk[d];
-        gather<R, ND, GM>(g, ib, pt, F);
+        gather_any<R, ND, GM>(g, ib, pt, F);
         make_frame<R, ND, (GM != 0)>(F, s.c, s.inv_c2, f);
-        if (!f.ok) return false;
+        okall = okall && f.ok;   // a bad frame fails the step after the loop
         gc_vel(f, s, upn, mu, uperp, V);
     }
+    if (!okall) return false;
 
     // reconstruction at R^{n+1/2} = (R^{n+1} + R^n)/2 (Sec. 3.1)
 #pragma unroll
     for (int d = 0; d < ND; ++d) pt[d] = fma(R(0.5), dk[d], ln[d]);
-    gather<R, ND, GM>(g, ib, pt, F);
+    gather_any<R, ND, GM>(g, ib, pt, F);
     make_frame<R, ND, (GM != 0)>(F, s.c, s.inv_c2, f);
     if (!f.ok) return false;
     R Gp = gamma_gc(f, s, upn, mu, uperp);

@@ -23,6 +23,13 @@ namespace gcb {
 template <typename R>
 struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : 256; };
 
+// minimum resident blocks per SM requested from the register allocator
+#ifndef GCB_MIN_BLOCKS_F32
+#define GCB_MIN_BLOCKS_F32 2
+#endif
+template <typename R, int ND>
+struct MinBlocks { static constexpr int n = (sizeof(R) == 8 || ND == 3) ? 1 : GCB_MIN_BLOCKS_F32; };
+
 template <typename R>
 struct PushArgs {
     DevGrid<R> g;
@@ -60,18 +67,21 @@ struct PosType<0> { using T = double; };
 template <>
 struct PosType<1> { using T = float; };
 
-// x (stored) -> base cell index and offset from the cell origin.
+// x (stored) -> base cell index in [0, n) and offset from that cell's origin
+// (positions are kept in [0, L); the clamp only matters for positions that
+// rounding put on an edge or for invalid input).
 template <typename R>
-__device__ __forceinline__ void split_pos_f64(double x, double dxd, double inv_dxd, int &ib, R &l)
+__device__ __forceinline__ void split_pos_f64(double x, double dxd, double inv_dxd, double nmax,
+                                              int &ib, R &l)
 {
-    double fl = fmin(fmax(floor(x * inv_dxd), -1e9), 1e9);
+    double fl = fmin(fmax(floor(x * inv_dxd), 0.0), nmax);
     ib = (int)fl;
     l = (R)fma(-fl, dxd, x);
 }
-__device__ __forceinline__ void split_pos_pair(float h, float lo, float dx, float inv_dx, int &ib,
-                                               float &l)
+__device__ __forceinline__ void split_pos_pair(float h, float lo, float dx, float inv_dx,
+                                               float nmax, int &ib, float &l)
 {
-    float fl = fminf(fmaxf(floorf(h * inv_dx), -1e9f), 1e9f);
+    float fl = fminf(fmaxf(floorf(h * inv_dx), 0.0f), nmax);
     ib = (int)fl;
     l = fmaf(-fl, dx, h) + lo;
 }
@@ -121,7 +131,7 @@ template <typename R>
 __device__ __forceinline__ bool finite_r(R v) { return isfinite(v); }
 
 template <typename R, int ND, int PM, int GM>
-__global__ void __launch_bounds__(Tile<R>::n) k_push_sr(const PushArgs<R> a)
+__global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(const PushArgs<R> a)
 {
     constexpr int TPB = Tile<R>::n;
     constexpr int NWARP = TPB / 32;
@@ -180,15 +190,16 @@ __global__ void __launch_bounds__(Tile<R>::n) k_push_sr(const PushArgs<R> a)
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
                     if (PM == 0)
-                        split_pos_f64<R>((double)xs[d], a.dxd[d], a.inv_dxd[d], ib[d], l[d]);
+                        split_pos_f64<R>((double)xs[d], a.dxd[d], a.inv_dxd[d],
+                                         (double)(a.g.n[d] - 1), ib[d], l[d]);
                     else {
                         float lf;
                         split_pos_pair((float)xs[d], xl[d], (float)a.g.dx[d], (float)a.g.inv_dx[d],
-                                       ib[d], lf);
+                                       (float)(a.g.n[d] - 1), ib[d], lf);
                         l[d] = (R)lf;
                     }
                 }
-                gather<R, ND, GM>(a.g, ib, l, F);
+                gather_any<R, ND, GM>(a.g, ib, l, F);
                 // switch S (Sec. 3, Sec. 4.1) in division-free form:
                 // S = 0 iff c^2 Gamma < f_rho dl |q/m| B and |E| < f_E B.
                 R Q = fabs(a.qm[(fl >> GCB_SPECIES_SHIFT) & 3]);
@@ -391,6 +402,7 @@ static void fill_args(PushArgs<R> &a, const gcb_particles *p, const gcb_particle
     a.g.stride = g->stride;
     for (int d = 0; d < 3; ++d) {
         a.g.n[d] = (int)g->n[d];
+        a.g.nR[d] = (R)g->n[d];
         a.g.dx[d] = (R)g->dx[d];
         a.g.inv_dx[d] = (R)(1.0 / g->dx[d]);
         a.L[d] = (double)g->n[d] * g->dx[d];

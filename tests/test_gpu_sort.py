@@ -32,7 +32,7 @@ def tile_key(x, dx, n, tile):
                                                 ("fp64", "f64")])
 def test_sort_is_a_tile_ordered_permutation(G, precision, pos_mode):
     fields, st, p = inputs.reconnection_2d(nx=256, ny=128, n_particles=50001, seed=2)
-    st["u"][0, 17] = np.nan          # frozen particles go last
+    st["x"][0, 17] = np.nan          # non-finite positions go last
     grid = G.Grid(fields, dtype="f32" if precision == "mixed" else "f64")
     ds = G.State.from_numpy(st, precision=precision, pos_mode=pos_mode, with_pid=True)
     gp = G.make_params(p, sort_every=1, sort_tile=(16, 8, 1))
@@ -42,11 +42,11 @@ def test_sort_is_a_tile_ordered_permutation(G, precision, pos_mode):
     pid = after["pid"]
     assert np.array_equal(np.sort(pid), np.arange(st["flags"].size))
     for k in ("x", "u", "dxp", "flags"):
-        assert np.array_equal(after[k], before[k][..., pid])
+        assert np.array_equal(after[k], before[k][..., pid], equal_nan=(k != "flags"))
     fin = np.isfinite(after["x"]).all(0) & np.isfinite(after["u"]).all(0)
     key = tile_key(after["x"][:, fin], (1.0, 1.0), (256, 128), (16, 8))
     assert np.all(np.diff(key) >= 0)
-    assert not fin[-1] or np.isfinite(after["u"]).all()
+    assert pid[-1] == 17 and fin[:-1].all()
 
 
 def test_push_with_sorting_matches_push_without(G):
