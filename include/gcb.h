@@ -208,6 +208,32 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
                        int n_steps, void *cuda_stream, void *ws, size_t ws_bytes,
                        gcb_stats *out);
 
+/*
+ * Size of the fixed scratch array behind gcb_push_sr_noalloc (per GPU).
+ */
+#define GCB_NOALLOC_SCRATCH_BYTES (1u << 20)
+
+/*
+ * gcb_push_sr without a caller-provided workspace.  The paper has no
+ * counterpart: this is a convenience of the library for callers that
+ * cannot call cudaMalloc (a host callback or plugin hook that forbids
+ * allocation, a device whose memory is held by a pool the caller does not
+ * control, a loop that must not allocate after start-up).  The caller still
+ * passes the particle arrays and the field records; the scratch comes from a
+ * static device array of GCB_NOALLOC_SCRATCH_BYTES (1 MiB) that every GPU
+ * loading the library holds until the process exits.
+ *   Same arguments, behaviour and results as gcb_push_sr, minus ws/ws_bytes.
+ *   Errors: as gcb_push_sr; GCB_ENOMEM (with a message) when the problem
+ *   needs more scratch than the array holds -- sorting (prm->sort_every > 0)
+ *   needs about 70 bytes per particle, so it fits only small problems;
+ *   without sorting the need is 256 bytes.
+ *   The first call on a device looks up the array's device address with
+ *   cudaGetSymbolAddress (make it before any stream capture).  All calls
+ *   share the array: calls whose GPU work overlaps race on it.
+ */
+gcb_status gcb_push_sr_noalloc(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                               int n_steps, void *cuda_stream, gcb_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,7 +56,7 @@ class GcbStats(C.Structure):
 
 EXPORTS = ["gcb_version", "gcb_status_string", "gcb_last_error", "gcb_grid_stride",
            "gcb_grid_pack", "gcb_pos_split", "gcb_pos_join", "gcb_workspace_bytes",
-           "gcb_sort_sr", "gcb_push_sr"]
+           "gcb_sort_sr", "gcb_push_sr", "gcb_push_sr_noalloc"]
 
 
 def load_library(path: str | None = None):
@@ -86,6 +86,9 @@ def load_library(path: str | None = None):
     lib.gcb_sort_sr.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_void_p,
                                 C.c_void_p, C.c_size_t]
     lib.gcb_sort_sr.restype = C.c_int
+    lib.gcb_push_sr_noalloc.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int,
+                                        C.c_void_p, P(GcbStats)]
+    lib.gcb_push_sr_noalloc.restype = C.c_int
     return lib
 
 
