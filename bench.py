@@ -32,7 +32,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s"
 NX, NY, NP = 2048, 1024, 1 << 24
-SORT_EVERY = 16
+SORT_EVERY = 8
+SORT_TILE = (1, 1)
 # algorithmic bytes per particle-step of the mixed path: state read + write
 # (x as 2 float32 pairs 16 B, u 12 B, dxp 8 B, flags 1 B) and the field
 # records (48 B per node) read once per step, divided over the particles.
@@ -46,12 +47,13 @@ def alg_bytes_per_launch(n, fp64=False):
     return (2 * (STATE_B64 if fp64 else STATE_B)) * n + (FIELD_B64 if fp64 else FIELD_B)
 
 
-def workload_config(n_total, ngpu):
+def workload_config(n_total, ngpu, sort_every=SORT_EVERY, sort_tile=SORT_TILE):
     return {"workload": f"2D double Harris + GEM + 64 modes, {NX}x{NY} grid, "
                         f"{n_total} particles, mixed FP32 (FP32-pair positions)",
             "grid": [NX, NY], "particles": n_total, "particles_per_gpu": n_total // ngpu,
             "dt": 0.45, "omega_c_dt_max": 1e5, "curvature": 1, "grad_mode": "grid",
-            "gca_tol": 1e-7, "steps_per_call": 1, "sort_every": SORT_EVERY,
+            "gca_tol": 1e-7, "steps_per_call": 1, "sort_every": sort_every,
+            "sort_tile": list(sort_tile),
             "l2": "inputs larger than L2 (particle state 620 MB per GPU)"}
 
 
@@ -165,6 +167,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sort-every", type=int, default=SORT_EVERY)
+    ap.add_argument("--sort-tile", default=",".join(map(str, SORT_TILE)),
+                    help="cells per sort tile, e.g. 2,2")
     ap.add_argument("--particles", type=int, default=NP,
                     help="particles per GPU (smaller cases for profiling only)")
     args = ap.parse_args()
@@ -189,7 +193,8 @@ def main():
                                            seed=1 + rank)
     grid = G.Grid(fields, dtype="f32")
     ds = G.State.from_numpy(st, precision="mixed", pos_mode="pair")
-    gp = G.make_params(p, sort_every=args.sort_every)
+    tile = tuple(int(v) for v in args.sort_tile.split(","))
+    gp = G.make_params(p, sort_every=args.sort_every, sort_tile=tile)
     ws = G.Workspace(ds, grid, gp)
     stream = torch.cuda.current_stream()
     step = [0]
@@ -290,7 +295,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": workload_config(n * world, world),
+                "config": workload_config(n * world, world, args.sort_every, tile),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                              "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
                              "traffic": None, "kernel": "k_push_sr<float,2,1,2>",

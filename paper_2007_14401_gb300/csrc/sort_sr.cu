@@ -5,7 +5,7 @@
 //           comes from one atomicAdd per group of equal keys in a warp
 //           (__match_any_sync), so runs of already-sorted particles cost one
 //           atomic per warp.
-// scan    : exclusive prefix sum of the bucket counts (one block).
+// scan    : exclusive prefix sum of the bucket counts (multi-block).
 // scatter : every array element moves to offset[key] + rank in a copy held
 //           in the workspace.
 // gcb_push_sr then runs its next step from that copy into the caller's
@@ -18,6 +18,11 @@
 namespace gcb {
 
 static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// multi-block scan: each block of kScanThreads threads owns kScanChunk counts
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int64_t kScanChunk = (int64_t)kScanThreads * kScanItems;
 
 bool sort_plan(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm, SortPlan &pl)
 {
@@ -40,6 +45,9 @@ bool sort_plan(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
     off += align256(n * 4);
     pl.off_hist = off;
     off += align256((size_t)pl.nbuckets * 4);
+    pl.nscan_blocks = (pl.nbuckets + kScanChunk - 1) / kScanChunk;
+    pl.off_bsum = off;
+    off += align256((size_t)pl.nscan_blocks * 4);
     // the permuted copy: x[nd], x_lo[nd] (pair), u[3], dxp[nd], flags, pid
     size_t pe = p->pos_mode == GCB_POS_F64 ? 8 : 4;
     size_t me = p->mom_dtype == GCB_F64 ? 8 : 4;
@@ -125,7 +133,72 @@ __global__ void k_sort_keys(const KeyArgs a)
     }
 }
 
-// In-place exclusive scan of hist[0..m) by one block of 1024 threads.
+// Exclusive scan of hist[0..m) in place, three passes: per-chunk sums,
+// a scan of the chunk sums (one block), and the per-chunk scan with its
+// offset.  Thread t of a block owns items [t*I, t*I + I) of the chunk.
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *sh, int32_t &total)
+{
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int32_t s = lane < nw ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) sh[lane] = s;
+    }
+    __syncthreads();
+    total = sh[nw - 1];
+    int32_t excl = x - v + (w > 0 ? sh[w - 1] : 0);
+    __syncthreads();
+    return excl;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int32_t *hist, int64_t m,
+                                                            int32_t *bsum)
+{
+    __shared__ int32_t sh[32];
+    const int64_t base = blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < m) s += hist[base + k];
+    int32_t tot;
+    block_excl_scan(s, sh, tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(int32_t *hist, int64_t m,
+                                                            const int32_t *boff)
+{
+    __shared__ int32_t sh[32];
+    const int64_t base = blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < m ? hist[base + k] : 0;
+        s += v[k];
+    }
+    int32_t tot;
+    int32_t run = block_excl_scan(s, sh, tot) + boff[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < m) hist[base + k] = run;
+        run += v[k];
+    }
+}
+
+// In-place exclusive scan of a short array (the chunk sums) by one block.
 __global__ void k_scan(int32_t *hist, int64_t m)
 {
     __shared__ int32_t part[1024];
@@ -210,7 +283,10 @@ gcb_status sort_into_workspace(const gcb_particles *p, const gcb_grid *g, const 
     ka.hist = hist;
     ka.frozen_key = (int)(pl.nbuckets - 1);
     k_sort_keys<<<blocks_for(p->n, 256), 256, 0, st>>>(ka);
-    k_scan<<<1, 1024, 0, st>>>(hist, pl.nbuckets);
+    int32_t *bsum = (int32_t *)(ws + pl.off_bsum);
+    k_scan_sums<<<(unsigned)pl.nscan_blocks, kScanThreads, 0, st>>>(hist, pl.nbuckets, bsum);
+    k_scan<<<1, 1024, 0, st>>>(bsum, pl.nscan_blocks);
+    k_scan_down<<<(unsigned)pl.nscan_blocks, kScanThreads, 0, st>>>(hist, pl.nbuckets, bsum);
     ScatterArgs sa;
     sa.n = p->n;
     void *src[14];

@@ -14,7 +14,8 @@ namespace gcb {
 struct SortPlan {
     int tile[3], ntile[3];
     int64_t nbuckets;
-    size_t off_keys, off_ranks, off_hist;
+    int64_t nscan_blocks;    // blocks of the multi-block scan of the counts
+    size_t off_keys, off_ranks, off_hist, off_bsum;
     size_t off_arr[14];
     int es[14];
     int narr;

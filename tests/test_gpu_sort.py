@@ -28,14 +28,15 @@ def tile_key(x, dx, n, tile):
     return key
 
 
-@pytest.mark.parametrize("precision,pos_mode", [("mixed", "pair"), ("mixed", "f64"),
-                                                ("fp64", "f64")])
-def test_sort_is_a_tile_ordered_permutation(G, precision, pos_mode):
+@pytest.mark.parametrize("precision,pos_mode,tile", [("mixed", "pair", (16, 8)),
+                                                     ("mixed", "f64", (1, 1)),
+                                                     ("fp64", "f64", (2, 4))])
+def test_sort_is_a_tile_ordered_permutation(G, precision, pos_mode, tile):
     fields, st, p = inputs.reconnection_2d(nx=256, ny=128, n_particles=50001, seed=2)
     st["x"][0, 17] = np.nan          # non-finite positions go last
     grid = G.Grid(fields, dtype="f32" if precision == "mixed" else "f64")
     ds = G.State.from_numpy(st, precision=precision, pos_mode=pos_mode, with_pid=True)
-    gp = G.make_params(p, sort_every=1, sort_tile=(16, 8, 1))
+    gp = G.make_params(p, sort_every=1, sort_tile=tile + (1,))
     before = ds.to_numpy()
     G.sort(ds, grid, gp)
     after = ds.to_numpy()
@@ -44,7 +45,7 @@ def test_sort_is_a_tile_ordered_permutation(G, precision, pos_mode):
     for k in ("x", "u", "dxp", "flags"):
         assert np.array_equal(after[k], before[k][..., pid], equal_nan=(k != "flags"))
     fin = np.isfinite(after["x"]).all(0) & np.isfinite(after["u"]).all(0)
-    key = tile_key(after["x"][:, fin], (1.0, 1.0), (256, 128), (16, 8))
+    key = tile_key(after["x"][:, fin], (1.0, 1.0), (256, 128), tile)
     assert np.all(np.diff(key) >= 0)
     assert pid[-1] == 17 and fin[:-1].all()
 
