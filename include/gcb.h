@@ -225,7 +225,7 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
  *   Same arguments, behaviour and results as gcb_push_sr, minus ws/ws_bytes.
  *   Errors: as gcb_push_sr; GCB_ENOMEM (with a message) when the problem
  *   needs more scratch than the array holds -- sorting (prm->sort_every > 0)
- *   needs about 70 bytes per particle, so it fits only small problems;
+ *   needs about 75 bytes per particle, so it fits only small problems;
  *   without sorting the need is 256 bytes.
  *   The first call on a device looks up the array's device address with
  *   cudaGetSymbolAddress (make it before any stream capture).  All calls

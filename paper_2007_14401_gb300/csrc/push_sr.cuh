@@ -20,8 +20,11 @@ namespace gcb {
 
 // particles per tile (= threads per block): 256 for FP32, 128 for FP64, where
 // the staged tile would not fit the 48 KB of static shared memory
+#ifndef GCB_TILE_F32
+#define GCB_TILE_F32 256
+#endif
 template <typename R>
-struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : 256; };
+struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : GCB_TILE_F32; };
 
 // minimum resident blocks per SM requested from the register allocator
 #ifndef GCB_MIN_BLOCKS_F32

@@ -6,8 +6,9 @@
 //           (__match_any_sync), so runs of already-sorted particles cost one
 //           atomic per warp.
 // scan    : exclusive prefix sum of the bucket counts (multi-block).
-// scatter : every array element moves to offset[key] + rank in a copy held
-//           in the workspace.
+// inverse : inv[offset[key] + rank] = i, the one scattered store per particle;
+// gather  : position j of the sorted copy (held in the workspace) takes
+//           element inv[j] of every array -- scattered reads, coalesced writes.
 // gcb_push_sr then runs its next step from that copy into the caller's
 // arrays, so a sort costs no separate copy back; gcb_sort_sr copies back.
 #include <cuda_runtime.h>
@@ -48,6 +49,8 @@ bool sort_plan(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
     pl.nscan_blocks = (pl.nbuckets + kScanChunk - 1) / kScanChunk;
     pl.off_bsum = off;
     off += align256((size_t)pl.nscan_blocks * 4);
+    pl.off_inv = off;
+    off += align256(n * 4);
     // the permuted copy: x[nd], x_lo[nd] (pair), u[3], dxp[nd], flags, pid
     size_t pe = p->pos_mode == GCB_POS_F64 ? 8 : 4;
     size_t me = p->mom_dtype == GCB_F64 ? 8 : 4;
@@ -89,7 +92,7 @@ struct KeyArgs {
     int ndim, pair;
     const void *x[3];
     const float *xlo[3];
-    double inv_dx[3];
+    float inv_dx[3];
     int ncell[3], tile[3], ntile[3];
     int32_t *keys, *ranks, *hist;
     int frozen_key;
@@ -107,17 +110,20 @@ __global__ void k_sort_keys(const KeyArgs a)
         int key = 0, mul = 1;
         bool fin = true;
         for (int d = 0; d < a.ndim; ++d) {
-            double xd;
+            // the cell in FP32: a particle within rounding of a cell face may
+            // be filed in the neighbouring cell, which does not matter here
+            float xf;
             if (a.pair) {
-                float h = ((const float *)a.x[d])[i], lo = a.xlo[d][i];
-                fin = fin && isfinite(h) && isfinite(lo);
-                xd = (double)h + (double)lo;
+                float lo = a.xlo[d][i];
+                xf = ((const float *)a.x[d])[i];
+                fin = fin && isfinite(xf) && isfinite(lo);
             } else {
-                xd = ((const double *)a.x[d])[i];
+                double xd = ((const double *)a.x[d])[i];
                 fin = fin && isfinite(xd);
+                xf = (float)xd;
             }
-            double c = floor(xd * a.inv_dx[d]);
-            int ci = fin ? (int)fmin(fmax(c, 0.0), (double)(a.ncell[d] - 1)) : 0;
+            float c = floorf(xf * a.inv_dx[d]);
+            int ci = fin ? (int)fminf(fmaxf(c, 0.0f), (float)(a.ncell[d] - 1)) : 0;
             key += (ci / a.tile[d]) * mul;
             mul *= a.ntile[d];
         }
@@ -223,20 +229,29 @@ __global__ void k_scan(int32_t *hist, int64_t m)
     }
 }
 
-struct ScatterArgs {
+__global__ void k_inverse(int64_t n, const int32_t *keys, const int32_t *ranks,
+                          const int32_t *off, int32_t *inv)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        inv[(int64_t)off[keys[i]] + ranks[i]] = (int32_t)i;
+}
+
+struct GatherArgs {
     int64_t n;
     int na;
     const void *src[14];
     void *dst[14];
     int es[14];
-    const int32_t *keys, *ranks, *off;
+    const int32_t *inv;
 };
 
-__global__ void k_scatter(const ScatterArgs a)
+__global__ void k_gather_copy(const GatherArgs a)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = (int64_t)a.off[a.keys[i]] + a.ranks[i];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a.inv[j];
+#pragma unroll 1
         for (int k = 0; k < a.na; ++k) {
             if (!a.src[k]) continue;
             switch (a.es[k]) {
@@ -273,7 +288,7 @@ gcb_status sort_into_workspace(const gcb_particles *p, const gcb_grid *g, const 
     for (int d = 0; d < 3; ++d) {
         ka.x[d] = p->x[d];
         ka.xlo[d] = (const float *)p->x_lo[d];
-        ka.inv_dx[d] = 1.0 / g->dx[d];
+        ka.inv_dx[d] = (float)(1.0 / g->dx[d]);
         ka.ncell[d] = (int)g->n[d];
         ka.tile[d] = pl.tile[d];
         ka.ntile[d] = pl.ntile[d];
@@ -287,21 +302,21 @@ gcb_status sort_into_workspace(const gcb_particles *p, const gcb_grid *g, const 
     k_scan_sums<<<(unsigned)pl.nscan_blocks, kScanThreads, 0, st>>>(hist, pl.nbuckets, bsum);
     k_scan<<<1, 1024, 0, st>>>(bsum, pl.nscan_blocks);
     k_scan_down<<<(unsigned)pl.nscan_blocks, kScanThreads, 0, st>>>(hist, pl.nbuckets, bsum);
-    ScatterArgs sa;
-    sa.n = p->n;
+    int32_t *inv = (int32_t *)(ws + pl.off_inv);
+    k_inverse<<<blocks_for(p->n, 256), 256, 0, st>>>(p->n, keys, ranks, hist, inv);
+    GatherArgs ga;
+    ga.n = p->n;
     void *src[14];
-    sa.na = caller_arrays(p, g->ndim, src);
-    for (int k = 0; k < sa.na; ++k) {
-        sa.src[k] = src[k];
-        sa.dst[k] = src[k] ? (void *)(ws + pl.off_arr[k]) : nullptr;
-        sa.es[k] = pl.es[k];
-        out.arr[k] = sa.dst[k];
+    ga.na = caller_arrays(p, g->ndim, src);
+    for (int k = 0; k < ga.na; ++k) {
+        ga.src[k] = src[k];
+        ga.dst[k] = src[k] ? (void *)(ws + pl.off_arr[k]) : nullptr;
+        ga.es[k] = pl.es[k];
+        out.arr[k] = ga.dst[k];
     }
-    out.narr = sa.na;
-    sa.keys = keys;
-    sa.ranks = ranks;
-    sa.off = hist;
-    k_scatter<<<blocks_for(p->n, 256), 256, 0, st>>>(sa);
+    out.narr = ga.na;
+    ga.inv = inv;
+    k_gather_copy<<<blocks_for(p->n, 256), 256, 0, st>>>(ga);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("sort kernels: %s", cudaGetErrorString(e));

@@ -10,12 +10,13 @@
 namespace gcb {
 
 // Workspace layout of a sort: counters | keys | ranks | bucket offsets |
-// one permuted copy of every particle array (256-byte aligned sections).
+// chunk sums | inverse permutation | one permuted copy of every particle
+// array (256-byte aligned sections).
 struct SortPlan {
     int tile[3], ntile[3];
     int64_t nbuckets;
     int64_t nscan_blocks;    // blocks of the multi-block scan of the counts
-    size_t off_keys, off_ranks, off_hist, off_bsum;
+    size_t off_keys, off_ranks, off_hist, off_bsum, off_inv;
     size_t off_arr[14];
     int es[14];
     int narr;
