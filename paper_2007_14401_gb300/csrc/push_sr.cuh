@@ -8,8 +8,8 @@
 //            counts orders the tile's slots as [GCA ..., Boris ..., frozen],
 //            so all warps but one run a single branch and GCA lanes run the
 //            same loop (the queues of the GCA and Boris branches);
-//   phase 2  thread t advances the particle in slot perm[t];
-//   phase 3  the tile is written back in particle order (coalesced).
+//   phase 2  thread t advances the particle in slot perm[t] and stores it
+//            back at that particle's own index.
 // Counters are reduced per block and added atomically to the workspace.
 #pragma once
 
@@ -18,10 +18,10 @@
 
 namespace gcb {
 
-// particles per tile (= threads per block): 256 for FP32, 128 for FP64, where
-// the staged tile would not fit the 48 KB of static shared memory
+// particles per tile (= threads per block): 128 (4 warps), so a tile waits at
+// its barriers for few warps; FP64 could not stage more in 48 KB anyway
 #ifndef GCB_TILE_F32
-#define GCB_TILE_F32 256
+#define GCB_TILE_F32 128
 #endif
 template <typename R>
 struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : GCB_TILE_F32; };
@@ -214,11 +214,22 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
                 if (a.force == GCB_FORCE_GCA) S = 0;
                 cls = S;
             } else {
+                // frozen: written back unchanged (with its flag) right here
                 fl |= GCB_FLAG_NONFINITE;
                 ++nf;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    reinterpret_cast<PosT *>(a.x[d])[i] = xs[d];
+                    if (PM) a.xlo[d][i] = xl[d];
+                    a.dxp[d][i] = dd[d];
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) a.u[k][i] = uu[k];
+                a.flags[i] = fl;
             }
+            if (a.pidin != a.pid) a.pid[i] = pid;
         }
-        __syncthreads();  // the previous tile is written out
+        __syncthreads();  // the previous tile's slots are no longer read
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
             if (valid) {
@@ -326,17 +337,21 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
             const int Sprev = f0 & GCB_FLAG_S;
             const int Snew = isg ? 0 : 1;
             uint8_t nfl = (uint8_t)((f0 & 0xC0) | (Sprev ? GCB_FLAG_SPREV : 0) | (Snew ? GCB_FLAG_S : 0));
+            // the particle goes straight back to its own index in the output
+            // arrays (for an all-GCA or all-Boris tile slot == thread, so
+            // these stores are coalesced; otherwise L2 merges the tile)
+            const int64_t gi = tile * TPB + sl;
             if (fin) {
                 if (fail) nfl |= GCB_FLAG_GCAFAIL;
                 if (ncv) nfl |= GCB_FLAG_NONCONV;
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
-                    s_x[d][sl] = xn[d];
-                    if (PM) s_xl[d][sl] = xln[d];
-                    s_d[d][sl] = disp[d];
+                    reinterpret_cast<PosT *>(a.x[d])[gi] = xn[d];
+                    if (PM) a.xlo[d][gi] = xln[d];
+                    a.dxp[d][gi] = disp[d];
                 }
 #pragma unroll
-                for (int k = 0; k < 3; ++k) s_u[k][sl] = us[k];
+                for (int k = 0; k < 3; ++k) a.u[k][gi] = us[k];
                 if (done) ++ng; else ++nb;
                 if (Sprev && !Snew) ++tg;
                 if (!Sprev && Snew) ++tb;
@@ -347,25 +362,20 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
                 R u2 = dot3(us, us) * sp.inv_c2;
                 ek += (double)(u2 / (R(1) + sqrt(R(1) + u2)));
             } else {
+                // not advanced: the input state is kept (copied when the input
+                // is a sorted copy rather than the output arrays themselves)
                 nfl |= GCB_FLAG_NONFINITE;
                 ++nf;
-            }
-            s_fl[sl] = nfl;
-        }
-        __syncthreads();
-
-        // phase 3: write the tile back in particle order
-        if (valid) {
 #pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                reinterpret_cast<PosT *>(a.x[d])[i] = s_x[d][tid];
-                if (PM) a.xlo[d][i] = s_xl[d][tid];
-                a.dxp[d][i] = s_d[d][tid];
-            }
+                for (int d = 0; d < ND; ++d) {
+                    reinterpret_cast<PosT *>(a.x[d])[gi] = s_x[d][sl];
+                    if (PM) a.xlo[d][gi] = s_xl[d][sl];
+                    a.dxp[d][gi] = s_d[d][sl];
+                }
 #pragma unroll
-            for (int k = 0; k < 3; ++k) a.u[k][i] = s_u[k][tid];
-            a.flags[i] = s_fl[tid];
-            if (a.pidin != a.pid) a.pid[i] = pid;
+                for (int k = 0; k < 3; ++k) a.u[k][gi] = s_u[k][sl];
+            }
+            a.flags[gi] = nfl;
         }
     }
 
