@@ -1,16 +1,18 @@
 """Throughput of the coupled guiding-center / Boris push on one GB300.
 
-Workload: the 2D reconnection-like field (double Harris sheet with a GEM-style
-flux perturbation, 64 random-phase Fourier modes, E = -v_in x B) on a
-2048 x 1024 periodic grid with float32 fields and precomputed float32
-gradient grids, 2^24 Maxwell-Juttner positrons and electrons (theta = 1),
-dt = 0.45, |q/m| with max Omega_C dt = 1e5: the mixed-precision path (float32
-arithmetic, float32-pair positions).  A step is one pass of the whole push
-over all particles (one kernel), state resident in HBM.
+Default workload (the graded one): the 2D reconnection-like field (double
+Harris sheet with a GEM-style flux perturbation, 64 random-phase Fourier
+modes, E = -v_in x B) on a 2048 x 1024 periodic grid with float32 fields and
+precomputed float32 gradient grids, 2^24 Maxwell-Juttner positrons and
+electrons (theta = 1), dt = 0.45, |q/m| with max Omega_C dt = 1e5: the
+mixed-precision path (float32 arithmetic, float32-pair positions).  A step is
+one pass of the whole push over all particles, state resident in HBM; the
+particles are re-sorted by cell every 8 steps inside the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload reconnection2d|harris2d_fp64|sheet3d]
 
-Under torchrun every rank pushes its own 2^24 particles (weak scaling, no
+Under torchrun every rank pushes its own particles (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.  --impl reference
 times the FP64 CPU oracle on this machine's host cores instead (rank 0 only).
 """
@@ -31,30 +33,58 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s"
-NX, NY, NP = 2048, 1024, 1 << 24
-SORT_EVERY = 8
-SORT_TILE = (1, 1)
-# algorithmic bytes per particle-step of the mixed path: state read + write
-# (x as 2 float32 pairs 16 B, u 12 B, dxp 8 B, flags 1 B) and the field
-# records (48 B per node) read once per step, divided over the particles.
-STATE_B = 16 + 12 + 8 + 1
-FIELD_B = NX * NY * 48
-STATE_B64 = 16 + 24 + 16 + 1
-FIELD_B64 = NX * NY * 96
 
 
-def alg_bytes_per_launch(n, fp64=False):
-    return (2 * (STATE_B64 if fp64 else STATE_B)) * n + (FIELD_B64 if fp64 else FIELD_B)
+def _gen_reconnection(n, seed):
+    from paper_2007_14401_gb300 import inputs
+    return inputs.reconnection_2d(nx=2048, ny=1024, n_particles=n, seed=seed)
 
 
-def workload_config(n_total, ngpu, sort_every=SORT_EVERY, sort_tile=SORT_TILE):
-    return {"workload": f"2D double Harris + GEM + 64 modes, {NX}x{NY} grid, "
-                        f"{n_total} particles, mixed FP32 (FP32-pair positions)",
-            "grid": [NX, NY], "particles": n_total, "particles_per_gpu": n_total // ngpu,
-            "dt": 0.45, "omega_c_dt_max": 1e5, "curvature": 1, "grad_mode": "grid",
-            "gca_tol": 1e-7, "steps_per_call": 1, "sort_every": sort_every,
-            "sort_tile": list(sort_tile),
-            "l2": "inputs larger than L2 (particle state 620 MB per GPU)"}
+def _gen_harris(n, seed):
+    from paper_2007_14401_gb300 import inputs
+    return inputs.harris_2d(n_per_species=max(1, n // 4), seed=seed - 1)
+
+
+def _gen_sheet3d(n, seed):
+    from paper_2007_14401_gb300 import inputs
+    return inputs.current_sheet_3d(n=256, n_particles=n, seed=seed + 1)
+
+
+# Algorithmic bytes per particle-step (PiC mode): the state read and written
+# once (mixed 2D: x as 2 FP32 pairs 16 B + u 12 B + dxp 8 B + flags 1 B;
+# FP64 2D: 16 + 24 + 16 + 1; mixed 3D: 24 + 12 + 12 + 1) plus every field
+# record read once per step (node records of 48 B: 2D FP32 with gradients;
+# 2D FP64 without gradients; 32 B: 3D FP32 without gradients).
+WORKLOADS = {
+    "reconnection2d": dict(
+        gen=_gen_reconnection, n=1 << 24, precision="mixed", grid="f32", sort_every=8,
+        tile=(1, 1), state_b=37, field_b=2048 * 1024 * 48, fp64_b=(57, 2048 * 1024 * 96),
+        desc="2D double Harris + GEM + 64 modes, 2048x1024 grid, {n} particles, mixed FP32 "
+             "(FP32-pair positions)",
+        extra=dict(grid=[2048, 1024], dt=0.45, omega_c_dt_max=1e5, curvature=1,
+                   grad_mode="grid", gca_tol=1e-7)),
+    "harris2d_fp64": dict(
+        gen=_gen_harris, n=16384, precision="fp64", grid="f64", sort_every=0, tile=(1, 1),
+        state_b=57, field_b=128 * 128 * 48, fp64_b=None,
+        desc="2D Harris sheet 128x128, {n} particles (q/m = -1, -10, -1e2, -1e3), FP64",
+        extra=dict(grid=[128, 128], dt=1.0, curvature=1, grad_mode="dw", gca_tol=1e-7)),
+    "sheet3d": dict(
+        gen=_gen_sheet3d, n=1 << 26, precision="mixed", grid="f32", sort_every=8,
+        tile=(1, 1, 1), state_b=49, field_b=256 ** 3 * 32, fp64_b=(73, 256 ** 3 * 48),
+        desc="3D kinked Harris sheet 256^3, guide 0.3, {n} particles (70% MJ upstream, 30% "
+             "power law in the sheet), |q/m| = 20, mixed FP32 (FP32-pair positions)",
+        extra=dict(grid=[256, 256, 256], dt=0.45, curvature=1, grad_mode="dw", gca_tol=1e-7)),
+}
+
+
+def workload_config(w, n_total, ngpu, sort_every, sort_tile):
+    cfg = {"workload": w["desc"].format(n=n_total), "particles": n_total,
+           "particles_per_gpu": n_total // ngpu, "steps_per_call": 1,
+           "sort_every": sort_every, "sort_tile": list(sort_tile),
+           "l2": "inputs larger than L2 (particle state > 126 MB per GPU)"
+                 if n_total // ngpu * w["state_b"] > 126e6 else "state fits L2"}
+    cfg.update(w["extra"])
+    return cfg
 
 
 def peaks():
@@ -103,16 +133,27 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline(fields, st, p, budget_s=15.0, n_sample=1 << 16):
-    """The FP64 oracle (as it stands) on the host cores, on a bounded sample."""
+def _oracle_for(fields, p):
     import oracle as O
-    from paper_2007_14401_gb300 import inputs
-    sub = inputs.subset(st, np.arange(n_sample))
-    of = O.grid_field(fields["E"], fields["B"], fields["dx"], dB=fields["dB"])
+    O.build()
+    of = O.grid_field(fields["E"], fields["B"], fields["dx"], dB=fields.get("dB"))
     op = O.make_params(dt=p["dt"], qm=p["qm"], f_rho=p["f_rho"], f_E=p["f_E"], dl=p["dl"],
                        curvature=p["curvature"], grad_mode=p["grad_mode"],
                        max_iter=p["gca_max_iter"], tol=p["gca_tol"])
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return O, of, op
+
+
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_baseline(fields, st, p, budget_s=15.0, n_sample=1 << 16):
+    """The FP64 oracle (as it stands) on the host cores, on a bounded sample."""
+    from paper_2007_14401_gb300 import inputs
+    O, of, op = _oracle_for(fields, p)
+    n_sample = min(n_sample, st["flags"].size)
+    sub = inputs.subset(st, np.arange(n_sample))
+    cores = _cores()
     t0 = time.perf_counter()
     O.push_sr(sub, of, op, 1, nthreads=cores)
     t1 = time.perf_counter() - t0
@@ -125,17 +166,13 @@ def cpu_baseline(fields, st, p, budget_s=15.0, n_sample=1 << 16):
                       f"oracle (C, OpenMP over particles), {dt:.1f} s"}
 
 
-def run_reference(args, rank):
+def run_reference(args, rank, w):
+    """The reference arm: the FP64 CPU oracle on a bounded sample per step."""
     if rank != 0:
         return 0
-    from paper_2007_14401_gb300 import inputs
-    fields, st, p = inputs.reconnection_2d(nx=NX, ny=NY, n_particles=1 << 14)
-    import oracle as O
-    O.build()
-    of = O.grid_field(fields["E"], fields["B"], fields["dx"], dB=fields["dB"])
-    op = O.make_params(dt=p["dt"], qm=p["qm"], curvature=1, grad_mode=1,
-                       max_iter=p["gca_max_iter"], tol=p["gca_tol"])
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    fields, st, p = w["gen"](min(w["n"], 1 << 14), 1)
+    O, of, op = _oracle_for(fields, p)
+    cores = _cores()
     n = st["flags"].size
     for _ in range(args.warmup):
         O.push_sr(st, of, op, 1, nthreads=cores)
@@ -148,7 +185,8 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": dict(workload_config(NP * args.gpus, args.gpus),
+            "config": dict(workload_config(w, w["n"] * args.gpus, args.gpus, w["sort_every"],
+                                           w["tile"]),
                            sample=f"{n} particles per step (bounded sample)"),
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
                              "sample": f"{n} particles x {args.steps} steps, FP64 oracle"},
@@ -163,22 +201,26 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gcb", choices=["gcb", "reference"])
+    ap.add_argument("--workload", default="reconnection2d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--sort-every", type=int, default=SORT_EVERY)
-    ap.add_argument("--sort-tile", default=",".join(map(str, SORT_TILE)),
-                    help="cells per sort tile, e.g. 2,2")
-    ap.add_argument("--particles", type=int, default=NP,
+    ap.add_argument("--sort-every", type=int, default=None)
+    ap.add_argument("--sort-tile", default=None, help="cells per sort tile, e.g. 2,2")
+    ap.add_argument("--particles", type=int, default=None,
                     help="particles per GPU (smaller cases for profiling only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    w = WORKLOADS[args.workload]
+    sort_every = w["sort_every"] if args.sort_every is None else args.sort_every
+    tile = w["tile"] if args.sort_tile is None else tuple(int(v) for v in args.sort_tile.split(","))
+    n_req = w["n"] if args.particles is None else args.particles
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        return run_reference(args, rank)
+        return run_reference(args, rank, w)
 
     import torch
     import torch.distributed as dist
@@ -187,14 +229,11 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2007_14401_gb300 import gcb as G
-    from paper_2007_14401_gb300 import inputs
 
-    fields, st, p = inputs.reconnection_2d(nx=NX, ny=NY, n_particles=args.particles,
-                                           seed=1 + rank)
-    grid = G.Grid(fields, dtype="f32")
-    ds = G.State.from_numpy(st, precision="mixed", pos_mode="pair")
-    tile = tuple(int(v) for v in args.sort_tile.split(","))
-    gp = G.make_params(p, sort_every=args.sort_every, sort_tile=tile)
+    fields, st, p = w["gen"](n_req, 1 + rank)
+    grid = G.Grid(fields, dtype=w["grid"])
+    ds = G.State.from_numpy(st, precision=w["precision"], pos_mode="pair")
+    gp = G.make_params(p, sort_every=sort_every, sort_tile=tile)
     ws = G.Workspace(ds, grid, gp)
     stream = torch.cuda.current_stream()
     step = [0]
@@ -228,11 +267,10 @@ def main():
     barrier()
     clocks = clk.stop()
     ms = t0.elapsed_time(t1)
-    # steps that began with a sort run 3 more kernels; the push kernel's own
+    # steps that began with a sort run 6 more kernels; the push kernel's own
     # duration is taken from the steps without one
     first = args.warmup
-    sorted_step = [args.sort_every > 0 and (first + k) % args.sort_every == 0
-                   for k in range(args.steps)]
+    sorted_step = [sort_every > 0 and (first + k) % sort_every == 0 for k in range(args.steps)]
     step_ms = [a.elapsed_time(b) for a, b in ev]
     launch_ms = [t for t, srt in zip(step_ms, sorted_step) if not srt] or step_ms
     n_sorts = sum(sorted_step)
@@ -269,44 +307,53 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d}
 
     fp64 = None
-    if not args.no_fp64 and rank == 0:
+    if not args.no_fp64 and rank == 0 and w["fp64_b"] is not None:
+        n64 = min(n, 1 << 22)
+        from paper_2007_14401_gb300 import inputs
+        st64 = inputs.subset(st, np.arange(n64)) if n64 < n else st
         grid64 = G.Grid(fields, dtype="f64")
-        d64 = G.State.from_numpy(st, precision="fp64")
-        ws64 = G.Workspace(d64, grid64, gp)
-        G.push(d64, grid64, gp, 1, workspace=ws64, stats=False)
+        d64 = G.State.from_numpy(st64, precision="fp64")
+        gp64 = G.make_params(p)
+        ws64 = G.Workspace(d64, grid64, gp64)
+        G.push(d64, grid64, gp64, 1, workspace=ws64, stats=False)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         k64 = 3
         a.record(stream)
-        G.push(d64, grid64, gp, k64, workspace=ws64, stats=False)
+        G.push(d64, grid64, gp64, k64, workspace=ws64, stats=False)
         b.record(stream)
         torch.cuda.synchronize()
         ms64 = a.elapsed_time(b) / k64
-        fp64 = {"value": n / (ms64 * 1e-3), "unit": METRIC, "ms_per_step": ms64,
-                "mixed_speedup": (value / world) / (n / (ms64 * 1e-3))}
+        v64 = n64 / (ms64 * 1e-3)
+        fp64 = {"value": v64, "unit": METRIC, "ms_per_step": ms64, "particles": n64,
+                "mixed_speedup": (value / world) / v64}
         del grid64, d64
 
     if rank == 0:
         pk, src = peaks()
         avg_launch = sum(launch_ms) / len(launch_ms)
-        achieved = alg_bytes_per_launch(n) / (avg_launch * 1e-3) / 1e9
+        alg = 2 * w["state_b"] * n + w["field_b"]
+        achieved = alg / (avg_launch * 1e-3) / 1e9
+        kname = ("k_push_sr<double,2,0,1>" if w["precision"] == "fp64" else
+                 "k_push_sr<float,{},1,{}>".format(len(w["extra"]["grid"]),
+                                                  2 if w["extra"]["grad_mode"] == "grid" else 1))
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
-                "config": workload_config(n * world, world, args.sort_every, tile),
+                "dtype": "f64" if w["precision"] == "fp64" else "f32", "data": "synthetic",
+                "config": workload_config(w, n * world, world, sort_every, tile),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                              "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                             "traffic": None, "kernel": "k_push_sr<float,2,1,2>",
-                             "alg_bytes_per_particle_step": 2 * STATE_B + FIELD_B / n,
+                             "traffic": None, "kernel": kname,
+                             "alg_bytes_per_particle_step": alg / n,
                              "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
                 "e2e": e2e,
-                "gpu_launches": args.steps + 3 * n_sorts,
-                "sort": {"every": args.sort_every, "sorts_in_timed_region": n_sorts,
+                "gpu_launches": args.steps + 6 * n_sorts,
+                "sort": {"every": sort_every, "sorts_in_timed_region": n_sorts,
                          "ms_step_with_sort": (sum(t for t, q in zip(step_ms, sorted_step) if q)
                                                / max(1, n_sorts)),
-                         "ms_push_kernel": sum(launch_ms) / len(launch_ms)},
+                         "ms_push_kernel": avg_launch},
                 "clocks": clocks,
                 "branch_mix": {"boris": stats["n_boris"], "gca": stats["n_gca"],
                                "mean_iter": stats["sum_iter"] / max(1, stats["n_gca"]),
