@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gcb_oracle.c")
+_SRC_KS = os.path.join(_HERE, "gcb_oracle_ks.c")
 _HDR = os.path.join(_HERE, "gcb_oracle.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
@@ -29,7 +30,8 @@ FIELD_GRID, FIELD_UNIFORM, FIELD_HARRIS, FIELD_BOTTLE, FIELD_ROTOR = 0, 1, 2, 3,
 GRAD_DW, GRAD_GRID = 0, 1
 FORCE_NONE, FORCE_BORIS, FORCE_GCA = 0, 1, 2
 MU_CONSERVE, UPERP_CONSERVE = 0, 1
-FLAG_S, FLAG_SPREV, FLAG_NONCONV, FLAG_GCAFAIL, FLAG_NONFINITE = 1, 2, 4, 8, 16
+FLAG_S, FLAG_SPREV, FLAG_NONCONV, FLAG_GCAFAIL, FLAG_NONFINITE, FLAG_EXITED = 1, 2, 4, 8, 16, 32
+KS_GRID, KS_VACUUM, KS_MONOPOLE = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -45,11 +47,12 @@ def build(force: bool = False) -> str:
         return alt
     os.makedirs(_BUILD, exist_ok=True)
     stale = force or not os.path.exists(_LIB) or max(
-        os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(_LIB)
+        os.path.getmtime(_SRC), os.path.getmtime(_SRC_KS),
+        os.path.getmtime(_HDR)) > os.path.getmtime(_LIB)
     if stale:
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
+               "-o", tmp, _SRC, _SRC_KS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -86,6 +89,16 @@ class Detail(C.Structure):
                 ("Rnp1", C.c_double * 3), ("bpg", C.c_double * 3)]
 
 
+class KsField(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nr", C.c_int), ("nth", C.c_int), ("logr0", C.c_double),
+                ("dlogr", C.c_double), ("dth", C.c_double), ("D", C.c_void_p * 3),
+                ("B", C.c_void_p * 3), ("par", C.c_double * 8)]
+
+
+class KsParams(C.Structure):
+    _fields_ = [("a", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double)]
+
+
 def _load():
     global _lib
     with _lock:
@@ -112,6 +125,17 @@ def _load():
                                               C.c_void_p, P(Field), P(Params), C.c_double,
                                               C.c_double, C.c_int]
             lib.orc_push_resolved.restype = C.c_int
+            lib.orc_ks_metric.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double * 64]
+            lib.orc_ks_gather.argtypes = [P(KsField), C.c_double, C.c_double, D3, D3]
+            lib.orc_ks_cell_sizes.argtypes = [P(KsField), C.c_double, C.c_void_p]
+            lib.orc_ks_frame.argtypes = [C.c_double, C.c_double, C.c_double, D3, D3,
+                                         C.c_double * 6]
+            lib.orc_ks_step_one.argtypes = [P(KsField), P(KsParams), P(Params), C.c_void_p,
+                                            D3, D3, P(C.c_ubyte), P(Detail)]
+            lib.orc_push_ks.argtypes = [C.c_long, C.c_void_p * 3, C.c_void_p * 3, C.c_void_p,
+                                        P(KsField), P(KsParams), P(Params), C.c_void_p,
+                                        C.c_int, C.c_int, P(Stats)]
+            lib.orc_push_ks.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -273,3 +297,100 @@ def push_resolved(state: dict, field: OracleField, params: Params, t_end: float,
                                nthreads)
     if rc != 0:
         raise RuntimeError("orc_push_resolved failed")
+
+
+# --------------------------------------------------------------------------
+# Kerr-Schild (covariant) scheme
+# --------------------------------------------------------------------------
+class OracleKsField:
+    """A Kerr-Schild field for the oracle (keeps its arrays alive)."""
+
+    def __init__(self, kind, nr=2, nth=2, logr0=0.0, dlogr=1.0, D=None, B=None, par=()):
+        self._keep = []
+        s = KsField()
+        s.kind, s.nr, s.nth = kind, nr, nth
+        s.logr0, s.dlogr = logr0, dlogr
+        s.dth = np.pi / (nth - 1)
+        if kind == KS_GRID:
+            for k in range(3):
+                d = np.ascontiguousarray(D[k], dtype=np.float64).reshape(-1)
+                b = np.ascontiguousarray(B[k], dtype=np.float64).reshape(-1)
+                assert d.size == nr * nth and b.size == d.size
+                self._keep += [d, b]
+                s.D[k] = d.ctypes.data
+                s.B[k] = b.ctypes.data
+        par = list(par) + [0.0] * (8 - len(par))
+        for k in range(8):
+            s.par[k] = float(par[k])
+        self.s = s
+        self.nr, self.nth = nr, nth
+
+
+def ks_grid_field(fields) -> OracleKsField:
+    """From a dict with D, B (lists of (nth, nr) arrays), logr0, dlogr."""
+    nth, nr = np.asarray(fields["D"][0]).shape
+    return OracleKsField(KS_GRID, nr, nth, fields["logr0"], fields["dlogr"], D=fields["D"],
+                         B=fields["B"])
+
+
+def ks_params(a, r_in, r_out) -> KsParams:
+    return KsParams(a, r_in, r_out)
+
+
+def ks_metric(a, r, th) -> dict:
+    lib = _load()
+    out = (C.c_double * 64)()
+    lib.orc_ks_metric(a, r, th, out)
+    v = np.array(out[:])
+    return dict(alpha=v[0], beta=v[1:4], gdn=v[4:13].reshape(3, 3), gup=v[13:22].reshape(3, 3),
+                sqrtg=v[22], dalpha=v[23:26], dbeta=v[26:35].reshape(3, 3),
+                dgup=v[35:62].reshape(3, 3, 3))
+
+
+def ks_gather(field: OracleKsField, r, th):
+    lib = _load()
+    D, B = (C.c_double * 3)(), (C.c_double * 3)()
+    lib.orc_ks_gather(C.byref(field.s), r, th, D, B)
+    return np.array(D[:]), np.array(B[:])
+
+
+def ks_cell_sizes(field: OracleKsField, a) -> np.ndarray:
+    lib = _load()
+    out = np.empty((field.nth - 1, field.nr - 1))
+    lib.orc_ks_cell_sizes(C.byref(field.s), a, out.ctypes.data)
+    return out
+
+
+def ks_frame(a, r, th, u, F):
+    lib = _load()
+    out = (C.c_double * 6)()
+    lib.orc_ks_frame(a, r, th, (C.c_double * 3)(*u), (C.c_double * 3)(*F), out)
+    return np.array(out[:3]), np.array(out[3:])
+
+
+def ks_step_one(field, kp, params, x, u, flags=0, dl=None):
+    lib = _load()
+    xx, uu = (C.c_double * 3)(*x), (C.c_double * 3)(*u)
+    fl = C.c_ubyte(flags)
+    det = Detail()
+    dptr = None if dl is None else np.ascontiguousarray(dl, dtype=np.float64)
+    lib.orc_ks_step_one(C.byref(field.s), C.byref(kp), C.byref(params),
+                        None if dptr is None else dptr.ctypes.data, xx, uu, C.byref(fl),
+                        C.byref(det))
+    return np.array(xx[:]), np.array(uu[:]), fl.value, det
+
+
+def push_ks(state: dict, field, kp, params, n_steps, dl=None, nthreads=0) -> dict:
+    """Advance state (x (3,n) r,theta,phi; u (3,n) covariant; flags) in place."""
+    lib = _load()
+    x, u, flags = state["x"], state["u"], state["flags"]
+    n = flags.shape[0]
+    dptr = None if dl is None else np.ascontiguousarray(dl, dtype=np.float64)
+    st = Stats()
+    rc = lib.orc_push_ks(n, _ptrs([x[k] for k in range(3)], 3), _ptrs([u[k] for k in range(3)], 3),
+                         flags.ctypes.data, C.byref(field.s), C.byref(kp), C.byref(params),
+                         None if dptr is None else dptr.ctypes.data, n_steps, nthreads,
+                         C.byref(st))
+    if rc != 0:
+        raise RuntimeError("orc_push_ks failed")
+    return {k: getattr(st, k) for k, _ in Stats._fields_}

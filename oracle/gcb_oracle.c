@@ -631,7 +631,7 @@ int orc_push_sr(long n, double *const x[3], double *const u[3],
         acc.n_nonconv += nc; acc.n_gcafail += gf; acc.n_nonfinite += nf;
         acc.sum_iter += si;
         if (mi > acc.max_iter) acc.max_iter = mi;
-        acc.sum_ekin = ek;  /* energy after the last step */
+        acc.sum_ekin += ek;
     }
     if (st) *st = acc;
     return 0;

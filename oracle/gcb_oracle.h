@@ -19,7 +19,8 @@
  *   - particle state: x^n (ndim comps), u^{n-1/2} (3 comps) and the unwrapped
  *     displacement dxp = x^n - x^{n-1} (ndim comps), staggered as in Sec. 2.1.
  *   - flags byte: bit0 S of the last step, bit1 S of the step before,
- *     bit2 NONCONV, bit3 GCAFAIL, bit4 NONFINITE, bits 6-7 species index.
+ *     bit2 NONCONV, bit3 GCAFAIL, bit4 NONFINITE, bit5 EXITED (covariant
+ *     scheme: left [r_in, r_out]), bits 6-7 species index.
  */
 #ifndef GCB_ORACLE_H
 #define GCB_ORACLE_H
@@ -35,7 +36,10 @@ enum { ORC_FORCE_NONE = 0, ORC_FORCE_BORIS = 1, ORC_FORCE_GCA = 2 };
 enum { ORC_MU_CONSERVE = 0, ORC_UPERP_CONSERVE = 1 };
 
 enum { ORC_FLAG_S = 1, ORC_FLAG_SPREV = 2, ORC_FLAG_NONCONV = 4,
-       ORC_FLAG_GCAFAIL = 8, ORC_FLAG_NONFINITE = 16 };
+       ORC_FLAG_GCAFAIL = 8, ORC_FLAG_NONFINITE = 16, ORC_FLAG_EXITED = 32 };
+
+/* Kerr-Schild fields (covariant scheme, geometrized units c = G = M = 1). */
+enum { ORC_KS_GRID = 0, ORC_KS_VACUUM = 1, ORC_KS_MONOPOLE = 2 };
 
 typedef struct {
     int kind;            /* ORC_FIELD_* */
@@ -66,8 +70,26 @@ typedef struct {
     long n_boris, n_gca, n_to_gca, n_to_boris;
     long n_nonconv, n_gcafail, n_nonfinite, sum_iter;
     long max_iter;
-    double sum_ekin;     /* sum of (Gamma - 1) after the step */
+    double sum_ekin;     /* sum of (Gamma - 1) over particles and steps */
 } orc_stats;
+
+/* Kerr-Schild field on the axisymmetric node grid (log r, theta):
+ * node (i, j) at log r = logr0 + i dlogr, theta = j dth (j = 0 .. nth-1,
+ * dth = pi / (nth - 1)); D^i, B^i contravariant KS components, index
+ * j * nr + i.  MONOPOLE: B^r = par[0] sin(theta) / sqrt(gamma) with
+ * par[1] = spin, D = 0.  VACUUM: no field. */
+typedef struct {
+    int kind;
+    int nr, nth;
+    double logr0, dlogr, dth;
+    const double *D[3], *B[3];
+    double par[8];
+} orc_ks_field;
+
+typedef struct {
+    double a;            /* black-hole spin */
+    double r_in, r_out;  /* particles leaving [r_in, r_out] are flagged EXITED */
+} orc_ks_params;
 
 /* Everything one particle-step computed, for the closed-form tests. */
 typedef struct {
@@ -120,6 +142,30 @@ int orc_push_resolved(long n, double *const x[3], double *const u[3],
                       unsigned char *flags, const orc_field *f,
                       const orc_params *p, double t_end, double dt_max,
                       int nthreads);
+
+/* Kerr-Schild metric at (r, theta): out[0] alpha, [1..3] beta^i, [4..12]
+ * gamma_ij, [13..21] gamma^{ij}, [22] sqrt(gamma), [23..25] d_i alpha,
+ * [26..34] d_i beta^j, [35..61] d_i gamma^{jk} (i = r, theta, phi). */
+void orc_ks_metric(double a, double r, double th, double out[64]);
+
+void orc_ks_gather(const orc_ks_field *f, double r, double th, double D[3], double B[3]);
+
+/* Effective cell sizes of Eq. (volint), (nr-1)*(nth-1) values, index j*(nr-1)+i. */
+void orc_ks_cell_sizes(const orc_ks_field *f, double a, double *dl);
+
+/* Local-frame components: out[0..2] of covariant u, out[3..5] of contravariant F. */
+void orc_ks_frame(double a, double r, double th, const double u[3], const double F[3],
+                  double out[6]);
+
+/* One coupled covariant step (Sec. 3.2) of one particle (x = r, theta, phi;
+ * u covariant); dl is the cell-size table (NULL: dl = 1). */
+void orc_ks_step_one(const orc_ks_field *f, const orc_ks_params *kp, const orc_params *p,
+                     const double *dl, double x[3], double u[3], unsigned char *flags,
+                     orc_detail *d);
+
+int orc_push_ks(long n, double *const x[3], double *const u[3], unsigned char *flags,
+                const orc_ks_field *f, const orc_ks_params *kp, const orc_params *p,
+                const double *dl, int n_steps, int nthreads, orc_stats *st);
 
 #ifdef __cplusplus
 }

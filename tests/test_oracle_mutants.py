@@ -20,6 +20,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "gcb_oracle.c")
+SRC_KS = os.path.join(ROOT, "oracle", "gcb_oracle_ks.c")
 HDR = os.path.join(ROOT, "oracle", "gcb_oracle.h")
 
 MUTANTS = [
@@ -57,23 +58,59 @@ MUTANTS = [
 ]
 
 
-def _build_mutant(tmp, old, new):
-    src = open(SRC).read()
-    assert src.count(old) == 1, old
-    with open(os.path.join(tmp, "gcb_oracle.c"), "w") as fh:
-        fh.write(src.replace(old, new))
+# mistakes in the covariant (Kerr-Schild) oracle
+MUTANTS_KS = [
+    ("ks_lapse", "m->alpha = ddiv(dc(1.0), dsqrt(onez));", "m->alpha = ddiv(dc(1.0), onez);"),
+    ("ks_shift", "m->beta[0] = ddiv(z, onez);", "m->beta[0] = ddiv(z, dadd(onez, onez));"),
+    ("ks_grphi_sign", "m->gdn[0][2] = m->gdn[2][0] = dscale(dmul(onez, s2), -a);",
+     "m->gdn[0][2] = m->gdn[2][0] = dscale(dmul(onez, s2), a);"),
+    ("geodesic_lapse_sign", "G[i] = -Gam * M->dalpha[i] + ub - M->alpha * uu / (2.0 * Gam);",
+     "G[i] = Gam * M->dalpha[i] + ub - M->alpha * uu / (2.0 * Gam);"),
+    ("geodesic_half", "G[i] = -Gam * M->dalpha[i] + ub - M->alpha * uu / (2.0 * Gam);",
+     "G[i] = -Gam * M->dalpha[i] + ub - M->alpha * uu / Gam;"),
+    ("velocity_shift_sign", "V[i] = M->alpha * s / Gam - M->beta[i];",
+     "V[i] = M->alpha * s / Gam + M->beta[i];"),
+    ("half_kick_full_dt", "boris_local(Dh, Bh, qm, 0.5 * dt * M.alpha, uh);",
+     "boris_local(Dh, Bh, qm, dt * M.alpha, uh);"),
+    ("frame_transposed", "for (int i = 0; i < 3; ++i) uh[a] += L[i][a] * u[i];",
+     "for (int i = 0; i < 3; ++i) uh[a] += L[a][i] * u[i];"),
+    ("gca_drift_dropped", "for (int j = 0; j < 3; ++j) s += Fb.M.gup[i][j] * (ub * Fb.bdn[j] / Gam + Fb.vE[j]);",
+     "for (int j = 0; j < 3; ++j) s += Fb.M.gup[i][j] * (ub * Fb.bdn[j] / Gam);"),
+    ("drift_sign", "F->vE[2] = sg * (D[0] * B[1] - D[1] * B[0]) / B2;",
+     "F->vE[2] = sg * (D[1] * B[0] - D[0] * B[1]) / B2;"),
+    ("cell_size_not_rooted", "dl[(long)j * (f->nr - 1) + i] = sqrt(area);",
+     "dl[(long)j * (f->nr - 1) + i] = area;"),
+    ("imr_not_midpoint", "for (int k = 0; k < 3; ++k) { xb[k] = 0.5 * (xk[k] + x[k]); ub[k] = 0.5 * (wk[k] + up[k]); }",
+     "for (int k = 0; k < 3; ++k) { xb[k] = xk[k]; ub[k] = wk[k]; }"),
+]
+
+
+def _build_mutant(tmp, src_path, old, new):
+    names = {SRC: "gcb_oracle.c", SRC_KS: "gcb_oracle_ks.c"}
+    for path, name in names.items():
+        text = open(path).read()
+        if path == src_path:
+            assert text.count(old) == 1, old
+            text = text.replace(old, new)
+        with open(os.path.join(tmp, name), "w") as fh:
+            fh.write(text)
     shutil.copy(HDR, os.path.join(tmp, "gcb_oracle.h"))
     lib = os.path.join(tmp, "libmut.so")
     subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", lib,
-                    os.path.join(tmp, "gcb_oracle.c"), "-lm"], check=True)
+                    os.path.join(tmp, "gcb_oracle.c"), os.path.join(tmp, "gcb_oracle_ks.c"),
+                    "-lm"], check=True)
     return lib
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_planted_mistake(name, old, new, tmp_path):
-    lib = _build_mutant(str(tmp_path), old, new)
+CASES = [(n, SRC, o, w) for n, o, w in MUTANTS] + [(n, SRC_KS, o, w) for n, o, w in MUTANTS_KS]
+
+
+@pytest.mark.parametrize("name,src,old,new", CASES, ids=[c[0] for c in CASES])
+def test_pins_catch_planted_mistake(name, src, old, new, tmp_path):
+    lib = _build_mutant(str(tmp_path), src, old, new)
     env = dict(os.environ, GCB_ORACLE_LIB=lib)
+    pins = "test_oracle_pins.py" if src == SRC else "test_oracle_ks_pins.py"
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
