@@ -10,7 +10,7 @@ one pass of the whole push over all particles, state resident in HBM; the
 particles are re-sorted by cell every 8 steps inside the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload reconnection2d|harris2d_fp64|sheet3d]
+                  [--workload reconnection2d|harris2d_fp64|sheet3d|kerr_wald]
 
 Under torchrun every rank pushes its own particles (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.  --impl reference
@@ -45,6 +45,11 @@ def _gen_harris(n, seed):
     return inputs.harris_2d(n_per_species=max(1, n // 4), seed=seed - 1)
 
 
+def _gen_kerr(n, seed):
+    from paper_2007_14401_gb300 import inputs
+    return inputs.kerr_wald(n_particles=n, seed=seed + 3)
+
+
 def _gen_sheet3d(n, seed):
     from paper_2007_14401_gb300 import inputs
     return inputs.current_sheet_3d(n=256, n_particles=n, seed=seed + 1)
@@ -68,6 +73,12 @@ WORKLOADS = {
         state_b=57, field_b=128 * 128 * 48, fp64_b=None,
         desc="2D Harris sheet 128x128, {n} particles (q/m = -1, -10, -1e2, -1e3), FP64",
         extra=dict(grid=[128, 128], dt=1.0, curvature=1, grad_mode="dw", gca_tol=1e-7)),
+    "kerr_wald": dict(
+        gen=_gen_kerr, n=1 << 22, precision="ks", grid="f32", sort_every=0, tile=(1, 1),
+        state_b=49, field_b=512 * 512 * 32, fp64_b=None,
+        desc="Kerr-Schild a=0.9, Wald field + split monopole, 512x512 (log r, theta) grid, "
+             "{n} electrons, |q/m| = 1e3, FP32 field records, FP64 metric and state",
+        extra=dict(grid=[512, 512], dt=0.02, spin=0.9)),
     "sheet3d": dict(
         gen=_gen_sheet3d, n=1 << 26, precision="mixed", grid="f32", sort_every=8,
         tile=(1, 1, 1), state_b=49, field_b=256 ** 3 * 32, fp64_b=(73, 256 ** 3 * 48),
@@ -133,6 +144,25 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def _oracle_ks(fields, p):
+    import oracle as O
+    O.build()
+    of = O.ks_grid_field(fields)
+    kp = O.ks_params(p["a"], p["r_in"], p["r_out"])
+    op = O.make_params(c=1.0, dt=p["dt"], f_rho=p["f_rho"], f_E=p["f_E"], qm=p["qm"],
+                       max_iter=p["gca_max_iter"], tol=p["gca_tol"])
+    dl = O.ks_cell_sizes(of, p["a"])
+    return lambda st, n, threads: O.push_ks(st, of, kp, op, n, dl=dl, nthreads=threads)
+
+
+def _oracle_push(fields, p):
+    """A callable (state, n_steps, threads) running the FP64 oracle."""
+    if "r_in" in p:
+        return _oracle_ks(fields, p)
+    O, of, op = _oracle_for(fields, p)
+    return lambda st, n, threads: O.push_sr(st, of, op, n, nthreads=threads)
+
+
 def _oracle_for(fields, p):
     import oracle as O
     O.build()
@@ -150,16 +180,16 @@ def _cores():
 def cpu_baseline(fields, st, p, budget_s=15.0, n_sample=1 << 16):
     """The FP64 oracle (as it stands) on the host cores, on a bounded sample."""
     from paper_2007_14401_gb300 import inputs
-    O, of, op = _oracle_for(fields, p)
+    run = _oracle_push(fields, p)
     n_sample = min(n_sample, st["flags"].size)
     sub = inputs.subset(st, np.arange(n_sample))
     cores = _cores()
     t0 = time.perf_counter()
-    O.push_sr(sub, of, op, 1, nthreads=cores)
+    run(sub, 1, cores)
     t1 = time.perf_counter() - t0
     steps = max(1, min(2000, int(budget_s / max(t1, 1e-3))))
     t0 = time.perf_counter()
-    O.push_sr(sub, of, op, steps, nthreads=cores)
+    run(sub, steps, cores)
     dt = time.perf_counter() - t0
     return {"value": n_sample * steps / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
             "sample": f"{n_sample} particles x {steps} steps of the same workload, FP64 "
@@ -171,14 +201,14 @@ def run_reference(args, rank, w):
     if rank != 0:
         return 0
     fields, st, p = w["gen"](min(w["n"], 1 << 14), 1)
-    O, of, op = _oracle_for(fields, p)
+    run = _oracle_push(fields, p)
     cores = _cores()
     n = st["flags"].size
     for _ in range(args.warmup):
-        O.push_sr(st, of, op, 1, nthreads=cores)
+        run(st, 1, cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.push_sr(st, of, op, 1, nthreads=cores)
+        run(st, 1, cores)
     dt = time.perf_counter() - t0
     v = n * args.steps / dt
     line = {"metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
@@ -231,16 +261,26 @@ def main():
     from paper_2007_14401_gb300 import gcb as G
 
     fields, st, p = w["gen"](n_req, 1 + rank)
-    grid = G.Grid(fields, dtype=w["grid"])
-    ds = G.State.from_numpy(st, precision=w["precision"], pos_mode="pair")
+    ks = w["precision"] == "ks"
+    if ks:
+        grid = G.KsGrid(fields, p["a"], p["r_in"], p["r_out"], dtype=w["grid"])
+        ds = G.State.from_numpy(st, precision="fp64")
+    else:
+        grid = G.Grid(fields, dtype=w["grid"])
+        ds = G.State.from_numpy(st, precision=w["precision"], pos_mode="pair")
     gp = G.make_params(p, sort_every=sort_every, sort_tile=tile)
-    ws = G.Workspace(ds, grid, gp)
+    ws = G.Workspace(ds, grid, gp) if not ks else None
     stream = torch.cuda.current_stream()
     step = [0]
 
+    def push(n):
+        if ks:
+            return G.push_ks(ds, grid, gp, n, stats=n == 1 and False)
+        return G.push(ds, grid, gp, n, workspace=ws, stats=False)
+
     def one_step():
         gp.step_index = step[0]
-        G.push(ds, grid, gp, 1, workspace=ws, stats=False)
+        push(1)
         step[0] += 1
 
     def barrier():
@@ -280,7 +320,7 @@ def main():
     ms = float(tmax.item())
     n = ds.n
     value = n * world * args.steps / (ms * 1e-3)
-    stats = G.push(ds, grid, gp, 1, workspace=ws)
+    stats = G.push_ks(ds, grid, gp, 1) if ks else G.push(ds, grid, gp, 1, workspace=ws)
 
     # end to end through host buffers: per step, the state is copied in from
     # pinned host memory, pushed, and copied back out
@@ -335,13 +375,17 @@ def main():
         avg_launch = sum(launch_ms) / len(launch_ms)
         alg = 2 * w["state_b"] * n + w["field_b"]
         achieved = alg / (avg_launch * 1e-3) / 1e9
-        kname = ("k_push_sr<double,2,0,1>" if w["precision"] == "fp64" else
-                 "k_push_sr<float,{},1,{}>".format(len(w["extra"]["grid"]),
-                                                  2 if w["extra"]["grad_mode"] == "grid" else 1))
+        if ks:
+            kname = "k_push_ks<float>"
+        elif w["precision"] == "fp64":
+            kname = "k_push_sr<double,2,0,1>"
+        else:
+            kname = "k_push_sr<float,{},1,{}>".format(
+                len(w["extra"]["grid"]), 2 if w["extra"]["grad_mode"] == "grid" else 1)
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if w["precision"] == "fp64" else "f32", "data": "synthetic",
+                "dtype": "f32" if w["precision"] == "mixed" else "f64", "data": "synthetic",
                 "config": workload_config(w, n * world, world, sort_every, tile),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                              "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],

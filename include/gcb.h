@@ -58,6 +58,7 @@ enum {
                                 root >= 1, B = 0 or v_E >= c on the path):
                                 the particle took a Boris step instead */
     GCB_FLAG_NONFINITE = 16, /* state non-finite: particle not advanced */
+    GCB_FLAG_EXITED = 32,    /* covariant scheme: left [r_in, r_out]; frozen */
     GCB_SPECIES_SHIFT = 6    /* bits 6-7: species index into gcb_params.qm */
 };
 
@@ -207,6 +208,55 @@ gcb_status gcb_sort_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
 gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
                        int n_steps, void *cuda_stream, void *ws, size_t ws_bytes,
                        gcb_stats *out);
+
+/*
+ * ---- Covariant (Kerr-Schild) scheme: Sec. 2.3 (GREOM), Sec. 2.4 (GRGCA),
+ * Sec. 3.2 (coupling).  Geometrized units c = G = M = 1 (prm->c must be 1).
+ *
+ * Grid: axisymmetric, uniform in (log r, theta): g.ndim = 2, axis 0 radial
+ * with n[0] nodes at log r = logr0 + i dx[0], axis 1 polar with n[1] nodes at
+ * theta = j dx[1], dx[1] = pi / (n[1] - 1) (nodes on both poles).  Records
+ * (has_grad = 0): D^r D^theta D^phi B^r B^theta B^phi, contravariant
+ * Kerr-Schild components (D^i = alpha F^{0i}, B^i = e^{ijk} F_jk / 2).  The
+ * linear shape function is used in (log r, theta), not periodic.
+ * dl: device array of (n[0]-1)*(n[1]-1) effective cell sizes, index
+ * j*(n[0]-1)+i, from gcb_ks_cell_size.
+ * Particles: ndim = 3, x = (r, theta, phi), u covariant (u_r, u_theta,
+ * u_phi), both FP64 (pos_mode GCB_POS_F64, mom_dtype GCB_F64), not staggered
+ * (Sec. 3.2); dxp unused.  Records may be FP32 (FP32 field interpolation) or
+ * FP64; all other arithmetic, including the metric, is FP64.
+ */
+typedef struct {
+    gcb_grid g;
+    double logr0;
+    const double *dl;
+} gcb_grid_ks;
+
+typedef struct {
+    double a;                /* spin, 0 <= a < 1 */
+    double r_in, r_out;      /* particles leaving [r_in, r_out] get GCB_FLAG_EXITED */
+} gcb_ks_params;
+
+/*
+ * Effective cell sizes of Eq. (volint), Sec. 3: on the (r, theta) grid,
+ * dl = (integral over the cell of sqrt(gamma_rr gamma_thth - gamma_rth^2)
+ * dr dtheta)^(1/2) (the proper meridional area; 4x4 Gauss-Legendre), written
+ * to the device array dl_out ((n[0]-1)*(n[1]-1) doubles).  Asynchronous.
+ */
+gcb_status gcb_ks_cell_size(const gcb_grid_ks *g, const gcb_ks_params *kp, double *dl_out,
+                            void *cuda_stream);
+
+/*
+ * n_steps coupled covariant steps (Sec. 3.2), in place: the switch of Sec. 3
+ * with rho~_C = Gamma/(|q/m| B) and E/B in the local frame of the normal
+ * observer; GRGCA (decomposition at x^n, half kick of u_par by D_par,
+ * implicit midpoint on (R, u_par), half kick, reconstruction at R^{n+1}) or
+ * GREOM (local-frame Boris half kicks over alpha dt/2 around an implicit
+ * midpoint geodesic step).  ws/out as gcb_push_sr (sorting unsupported here).
+ */
+gcb_status gcb_push_ks(const gcb_particles *p, const gcb_grid_ks *g, const gcb_ks_params *kp,
+                       const gcb_params *prm, int n_steps, void *cuda_stream, void *ws,
+                       size_t ws_bytes, gcb_stats *out);
 
 /*
  * Size of the fixed scratch array behind gcb_push_sr_noalloc (per GPU).

@@ -2,6 +2,7 @@
 // checks, the step loop, the workspace counters, and the small layout kernels
 // (node-record packing, FP32-pair position split/join).
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -179,6 +180,31 @@ gcb_status gcb_pos_join(int64_t n, const float *hi, const float *lo, double *x, 
     return launch_check("gcb_pos_join");
 }
 
+// Copy the device counters to `out` (synchronizing the stream) when non-NULL.
+static gcb_status read_stats(const unsigned long long *stats, cudaStream_t st, gcb_stats *out)
+{
+    if (!out) return GCB_OK;
+    unsigned long long h[ST_COUNT];
+    if (cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("stats readback: %s", cudaGetErrorString(cudaGetLastError()));
+        return GCB_ECUDA;
+    }
+    out->n_boris = (int64_t)h[ST_BORIS];
+    out->n_gca = (int64_t)h[ST_GCA];
+    out->n_to_gca = (int64_t)h[ST_TO_GCA];
+    out->n_to_boris = (int64_t)h[ST_TO_BORIS];
+    out->n_nonconv = (int64_t)h[ST_NONCONV];
+    out->n_gcafail = (int64_t)h[ST_GCAFAIL];
+    out->n_nonfinite = (int64_t)h[ST_NONFINITE];
+    out->sum_iter = (int64_t)h[ST_SUM_ITER];
+    out->max_iter = (int64_t)h[ST_MAX_ITER];
+    double e;
+    memcpy(&e, &h[ST_EKIN], sizeof(e));
+    out->sum_ekin = e;
+    return GCB_OK;
+}
+
 static gcb_status check_problem(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm)
 {
     gcb_status s = check_grid(g);
@@ -284,6 +310,82 @@ gcb_status gcb_sort_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
     return copy_back(p, g, pl, v, st);
 }
 
+static gcb_status check_ks(const gcb_grid_ks *gk, const gcb_ks_params *kp)
+{
+    if (!gk || !kp) { set_error("grid or spacetime parameters NULL"); return GCB_EINVAL; }
+    gcb_status s = check_grid(&gk->g);
+    if (s != GCB_OK) return s;
+    const gcb_grid *g = &gk->g;
+    if (g->ndim != 2 || g->has_grad) { set_error("Kerr-Schild grid: ndim 2, no gradient records"); return GCB_EINVAL; }
+    if (fabs(g->dx[1] * (double)(g->n[1] - 1) - 3.141592653589793) > 1e-9) {
+        set_error("Kerr-Schild grid: theta nodes must span [0, pi]");
+        return GCB_EINVAL;
+    }
+    if (!(kp->a >= 0.0 && kp->a < 1.0) || !(kp->r_in > 0.0) || !(kp->r_out > kp->r_in)) {
+        set_error("need 0 <= a < 1 and 0 < r_in < r_out");
+        return GCB_EINVAL;
+    }
+    return GCB_OK;
+}
+
+gcb_status gcb_ks_cell_size(const gcb_grid_ks *g, const gcb_ks_params *kp, double *dl_out,
+                            void *cuda_stream)
+{
+    g_err[0] = 0;
+    gcb_status s = check_ks(g, kp);
+    if (s != GCB_OK) return s;
+    if (!dl_out || !aligned(dl_out, 8)) { set_error("dl_out NULL or misaligned"); return GCB_EINVAL; }
+    return ks_cell_size(g, kp, dl_out, (cudaStream_t)cuda_stream);
+}
+
+gcb_status gcb_push_ks(const gcb_particles *p, const gcb_grid_ks *gk, const gcb_ks_params *kp,
+                       const gcb_params *prm, int n_steps, void *cuda_stream, void *ws,
+                       size_t ws_bytes, gcb_stats *out)
+{
+    g_err[0] = 0;
+    gcb_status s = check_ks(gk, kp);
+    if (s != GCB_OK) return s;
+    if (!p || !prm) { set_error("particles or params NULL"); return GCB_EINVAL; }
+    if (n_steps < 0 || p->n < 0) { set_error("negative n_steps or particle count"); return GCB_EINVAL; }
+    if (p->ndim != 3 || p->pos_mode != GCB_POS_F64 || p->mom_dtype != GCB_F64) {
+        set_error("Kerr-Schild particles: ndim 3, FP64 positions and momenta");
+        return GCB_EUNSUPPORTED;
+    }
+    if (prm->c != 1.0) { set_error("the covariant scheme uses c = 1"); return GCB_EINVAL; }
+    if (!(prm->dt > 0) || !(prm->f_rho > 0) || !(prm->f_E > 0)) { set_error("dt, f_rho, f_E must be > 0"); return GCB_EINVAL; }
+    if (prm->mu_mode != GCB_MU_CONSERVE && prm->mu_mode != GCB_UPERP_CONSERVE) { set_error("mu_mode"); return GCB_EINVAL; }
+    if (prm->force < GCB_FORCE_NONE || prm->force > GCB_FORCE_GCA) { set_error("force"); return GCB_EINVAL; }
+    if (prm->gca_max_iter < 1 || prm->gca_max_iter > 1000 || prm->gca_fixed_iters < 0 ||
+        prm->gca_fixed_iters > 1000 || !(prm->gca_tol >= 0)) {
+        set_error("iteration bounds");
+        return GCB_EINVAL;
+    }
+    if (prm->sort_every != 0) { set_error("sorting is not supported by the covariant scheme"); return GCB_EUNSUPPORTED; }
+    if (!gk->dl || !aligned(gk->dl, 8)) { set_error("cell-size table NULL or misaligned"); return GCB_EINVAL; }
+    if (p->n > 0) {
+        for (int k = 0; k < 3; ++k)
+            if (!p->x[k] || !p->u[k] || !aligned(p->x[k], 8) || !aligned(p->u[k], 8)) {
+                set_error("x or u NULL or misaligned");
+                return GCB_EINVAL;
+            }
+        if (!p->flags) { set_error("flags NULL"); return GCB_EINVAL; }
+        if (p->pid && !aligned(p->pid, 8)) { set_error("pid misaligned"); return GCB_EINVAL; }
+    }
+    if (!ws || !aligned(ws, 256)) { set_error("workspace NULL or not 256-byte aligned"); return GCB_EINVAL; }
+    if (ws_bytes < kStatsBytes) { set_error("workspace too small"); return GCB_ENOMEM; }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    unsigned long long *stats = (unsigned long long *)ws;
+    if (cudaMemsetAsync(stats, 0, kStatsBytes, st) != cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(cudaGetLastError()));
+        return GCB_ECUDA;
+    }
+    for (int step = 0; step < n_steps; ++step) {
+        s = push_step_ks(p, p, gk, kp, prm, st, stats);
+        if (s != GCB_OK) return s;
+    }
+    return read_stats(stats, st, out);
+}
+
 gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
                        int n_steps, void *cuda_stream, void *ws, size_t ws_bytes, gcb_stats *out)
 {
@@ -314,27 +416,7 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
         s = fp64 ? push_step_f64(p, in, g, prm, st, stats) : push_step_f32(p, in, g, prm, st, stats);
         if (s != GCB_OK) return s;
     }
-    if (out) {
-        unsigned long long h[ST_COUNT];
-        if (cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            set_error("stats readback: %s", cudaGetErrorString(cudaGetLastError()));
-            return GCB_ECUDA;
-        }
-        out->n_boris = (int64_t)h[ST_BORIS];
-        out->n_gca = (int64_t)h[ST_GCA];
-        out->n_to_gca = (int64_t)h[ST_TO_GCA];
-        out->n_to_boris = (int64_t)h[ST_TO_BORIS];
-        out->n_nonconv = (int64_t)h[ST_NONCONV];
-        out->n_gcafail = (int64_t)h[ST_GCAFAIL];
-        out->n_nonfinite = (int64_t)h[ST_NONFINITE];
-        out->sum_iter = (int64_t)h[ST_SUM_ITER];
-        out->max_iter = (int64_t)h[ST_MAX_ITER];
-        double e;
-        memcpy(&e, &h[ST_EKIN], sizeof(e));
-        out->sum_ekin = e;
-    }
-    return GCB_OK;
+    return read_stats(stats, st, out);
 }
 
 }  // extern "C"

@@ -26,4 +26,10 @@ gcb_status push_step_f64(const gcb_particles *p, const gcb_particles *in, const 
 gcb_status push_step_f32(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
                          const gcb_params *prm, cudaStream_t st, unsigned long long *stats);
 
+// Covariant scheme (gcb_ks.cu).
+gcb_status push_step_ks(const gcb_particles *p, const gcb_particles *in, const gcb_grid_ks *g,
+                        const gcb_ks_params *kp, const gcb_params *prm, cudaStream_t st,
+                        unsigned long long *stats);
+gcb_status ks_cell_size(const gcb_grid_ks *g, const gcb_ks_params *kp, double *dl, cudaStream_t st);
+
 }  // namespace gcb

@@ -19,7 +19,7 @@ POS_F64, POS_F32PAIR = 0, 1
 GRAD_DW, GRAD_GRID = 0, 1
 FORCE_NONE, FORCE_BORIS, FORCE_GCA = 0, 1, 2
 MU_CONSERVE, UPERP_CONSERVE = 0, 1
-FLAG_S, FLAG_SPREV, FLAG_NONCONV, FLAG_GCAFAIL, FLAG_NONFINITE = 1, 2, 4, 8, 16
+FLAG_S, FLAG_SPREV, FLAG_NONCONV, FLAG_GCAFAIL, FLAG_NONFINITE, FLAG_EXITED = 1, 2, 4, 8, 16, 32
 SPECIES_SHIFT = 6
 STATUS = {0: "GCB_OK", 1: "GCB_EINVAL", 2: "GCB_ECUDA", 3: "GCB_EUNSUPPORTED", 4: "GCB_ENOMEM"}
 
@@ -54,9 +54,18 @@ class GcbStats(C.Structure):
                 ("sum_ekin", C.c_double)]
 
 
+class GcbGridKs(C.Structure):
+    _fields_ = [("g", GcbGrid), ("logr0", C.c_double), ("dl", C.c_void_p)]
+
+
+class GcbKsParams(C.Structure):
+    _fields_ = [("a", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double)]
+
+
 EXPORTS = ["gcb_version", "gcb_status_string", "gcb_last_error", "gcb_grid_stride",
            "gcb_grid_pack", "gcb_pos_split", "gcb_pos_join", "gcb_workspace_bytes",
-           "gcb_sort_sr", "gcb_push_sr", "gcb_push_sr_noalloc"]
+           "gcb_sort_sr", "gcb_push_sr", "gcb_push_sr_noalloc", "gcb_ks_cell_size",
+           "gcb_push_ks"]
 
 
 def load_library(path: str | None = None):
@@ -89,6 +98,11 @@ def load_library(path: str | None = None):
     lib.gcb_push_sr_noalloc.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int,
                                         C.c_void_p, P(GcbStats)]
     lib.gcb_push_sr_noalloc.restype = C.c_int
+    lib.gcb_ks_cell_size.argtypes = [P(GcbGridKs), P(GcbKsParams), C.c_void_p, C.c_void_p]
+    lib.gcb_ks_cell_size.restype = C.c_int
+    lib.gcb_push_ks.argtypes = [P(GcbParticles), P(GcbGridKs), P(GcbKsParams), P(GcbParams),
+                                C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, P(GcbStats)]
+    lib.gcb_push_ks.restype = C.c_int
     return lib
 
 
@@ -286,6 +300,55 @@ def push(state: State, grid: Grid, params: GcbParams, n_steps: int = 1, stream=N
                           _stream_ptr(stream), C.c_void_p(ws.buf.data_ptr()), ws.nbytes,
                           C.byref(out) if stats else None)
     _check(rc, "gcb_push_sr")
+    if stats:
+        return {k: getattr(out, k) for k, _ in GcbStats._fields_}
+    return None
+
+
+# --------------------------------------------------------------------------
+# covariant (Kerr-Schild) scheme
+# --------------------------------------------------------------------------
+class KsGrid:
+    """Kerr-Schild field records on the (log r, theta) grid plus the cell-size
+    table of Eq. (volint), both on the device."""
+
+    def __init__(self, fields: dict, a: float, r_in: float, r_out: float, dtype: str = "f32",
+                 device="cuda", stream=None):
+        nth, nr = np.asarray(fields["D"][0]).shape
+        self.dtype = F32 if dtype == "f32" else F64
+        self.stride = _lib.gcb_grid_stride(2, self.dtype, 0)
+        tdt = torch.float32 if self.dtype == F32 else torch.float64
+        self.rec = torch.empty(nr * nth * self.stride, dtype=tdt, device=device)
+        comps = list(fields["D"]) + list(fields["B"])
+        dev = [torch.as_tensor(np.ascontiguousarray(c, dtype=np.float64).reshape(-1)).to(device)
+               for c in comps]
+        g = GcbGrid(2, self.dtype, (C.c_int64 * 3)(nr, nth, 1),
+                    (C.c_double * 3)(fields["dlogr"], np.pi / (nth - 1), 1.0), 0, self.stride,
+                    self.rec.data_ptr())
+        ptrs = (C.c_void_p * 6)(*[t.data_ptr() for t in dev])
+        _check(_lib.gcb_grid_pack(C.byref(g), ptrs, _stream_ptr(stream)), "gcb_grid_pack")
+        self.dl = torch.empty((nth - 1) * (nr - 1), dtype=torch.float64, device=device)
+        self.s = GcbGridKs(g, fields["logr0"], self.dl.data_ptr())
+        self.kp = GcbKsParams(a, r_in, r_out)
+        _check(_lib.gcb_ks_cell_size(C.byref(self.s), C.byref(self.kp),
+                                     C.c_void_p(self.dl.data_ptr()), _stream_ptr(stream)),
+               "gcb_ks_cell_size")
+        torch.cuda.synchronize()
+        self._keep = dev
+
+
+def push_ks(state: State, grid: KsGrid, params: GcbParams, n_steps: int = 1, stream=None,
+            workspace: Workspace | None = None, stats: bool = True):
+    """n_steps covariant coupled steps of ``state`` (FP64, ndim 3) in place."""
+    if workspace is None:
+        workspace = Workspace.__new__(Workspace)
+        workspace.buf = torch.empty(256, dtype=torch.uint8, device=state.x.device)
+        workspace.nbytes = 256
+    out = GcbStats() if stats else None
+    rc = _lib.gcb_push_ks(C.byref(state.s), C.byref(grid.s), C.byref(grid.kp), C.byref(params),
+                          int(n_steps), _stream_ptr(stream), C.c_void_p(workspace.buf.data_ptr()),
+                          workspace.nbytes, C.byref(out) if stats else None)
+    _check(rc, "gcb_push_ks")
     if stats:
         return {k: getattr(out, k) for k, _ in GcbStats._fields_}
     return None

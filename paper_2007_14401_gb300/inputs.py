@@ -218,3 +218,91 @@ def current_sheet_3d(n=256, dx=1.0, B0=1.0, delta=6.0, Bg=0.3, kink=0.05, Ey=0.1
 def subset(state, idx):
     """The particles ``idx`` of a state (copies)."""
     return {k: np.ascontiguousarray(v[..., idx]) for k, v in state.items()}
+
+
+# --------------------------------------------------------------------------
+# Kerr black hole: Wald field plus a split monopole (covariant scheme)
+# --------------------------------------------------------------------------
+def _ks_line_element(a, r, th):
+    """Kerr metric in Kerr-Schild coordinates (t, r, theta, phi), M = 1:
+    g_{mu nu} for arrays r, th (shape (..., 4, 4))."""
+    s, c = np.sin(th), np.cos(th)
+    rho2 = r * r + a * a * c * c
+    z = 2.0 * r / rho2
+    g = np.zeros(np.shape(r) + (4, 4))
+    g[..., 0, 0] = -(1.0 - z)
+    g[..., 0, 1] = g[..., 1, 0] = z
+    g[..., 0, 3] = g[..., 3, 0] = -a * z * s * s
+    g[..., 1, 1] = 1.0 + z
+    g[..., 1, 3] = g[..., 3, 1] = -a * (1.0 + z) * s * s
+    g[..., 2, 2] = rho2
+    g[..., 3, 3] = (r * r + a * a + z * a * a * s * s) * s * s
+    return g
+
+
+def kerr_wald(nr=512, nth=512, a=0.9, B0=1.0, Qm=1.0, r_out=50.0, n_particles=1 << 22,
+              theta_mj=1.0, qm=-1e3, dt=0.02, seed=4):
+    """Kerr-Schild grid uniform in (log r, theta), r in [1.2 r_h, r_out], theta
+    in [0, pi] (nodes on the poles).  Field: Wald's uniform-at-infinity
+    solution A_mu = (B0/2)(g_{mu phi} + 2 a g_{mu t}) (Wald 1974) plus a split
+    monopole A_phi = -Qm s(theta) cos(theta), s a sign of cos(theta) smoothed
+    over two cells, whose reversal is an equatorial current sheet.  D^i =
+    alpha F^{t i}, B^i = epsilon^{ijk} F_jk / (2 sqrt(gamma)), contravariant
+    Kerr-Schild components, derivatives of A by central differences.
+    Electrons uniform in (log r, theta, phi), Maxwell-Juttner momenta in the
+    frame of the normal observer (triad from the Cholesky factor of gamma^{ij})."""
+    rh = 1.0 + np.sqrt(1.0 - a * a)
+    r_in = 1.2 * rh
+    logr0 = np.log(r_in)
+    dlogr = (np.log(r_out) - logr0) / (nr - 1)
+    dth = np.pi / (nth - 1)
+    R = np.exp(logr0 + dlogr * np.arange(nr))[None, :] * np.ones((nth, 1))
+    # the metric is singular on the axis: evaluate the pole rows just off it
+    # (they are replaced by the neighbouring rows below)
+    T = np.clip((dth * np.arange(nth))[:, None] * np.ones((1, nr)), 0.25 * dth, np.pi - 0.25 * dth)
+    w = 2.0 * dth
+
+    def potential(r, th):
+        g = _ks_line_element(a, r, th)
+        A = 0.5 * B0 * (g[..., :, 3] + 2.0 * a * g[..., :, 0])
+        A[..., 3] += -Qm * np.tanh(np.cos(th) / w) * np.cos(th)
+        return A
+
+    hr, ht = 1e-6 * R, 1e-6
+    dA_r = (potential(R + hr, T) - potential(R - hr, T)) / (2 * hr)[..., None]
+    Tp, Tm = T + ht, T - ht
+    dA_t = (potential(R, Tp) - potential(R, Tm)) / (Tp - Tm)[..., None]
+    F = np.zeros((nth, nr, 4, 4))
+    for mu, dA in ((1, dA_r), (2, dA_t)):      # F_{mu nu} = d_mu A_nu - d_nu A_mu
+        F[..., mu, :] += dA
+        F[..., :, mu] -= dA
+    g4 = _ks_line_element(a, R, T)
+    gi = np.linalg.inv(g4)
+    det3 = np.linalg.det(g4[..., 1:, 1:])
+    sqrtg = np.sqrt(np.maximum(det3, 1e-300))
+    alpha = 1.0 / np.sqrt(-gi[..., 0, 0])
+    Fup = np.einsum("...am,...bn,...mn->...ab", gi, gi, F)
+    D = [alpha * Fup[..., 0, i] for i in (1, 2, 3)]
+    B = [F[..., 2, 3] / sqrtg, F[..., 3, 1] / sqrtg, F[..., 1, 2] / sqrtg]
+    # on the poles sqrt(gamma) = 0: take the limit from the neighbouring row
+    for comp in D + B:
+        comp[0, :] = comp[1, :]
+        comp[-1, :] = comp[-2, :]
+    fields = dict(D=D, B=B, logr0=logr0, dlogr=dlogr, dth=dth, a=a, r_in=r_in, r_out=r_out)
+    rng = np.random.default_rng(seed)
+    n = n_particles
+    lr = rng.uniform(logr0, np.log(r_out), n)
+    th = np.arccos(rng.uniform(-1.0, 1.0, n) * 0.98)
+    ph = rng.uniform(0.0, 2 * np.pi, n)
+    r = np.exp(lr)
+    uh = maxwell_juttner(rng, n, theta_mj)
+    g4p = _ks_line_element(a, r, th)
+    gup = np.linalg.inv(g4p[:, 1:, 1:])
+    L = np.linalg.cholesky(gup)                 # gamma^{ij} = L L^T
+    u = np.linalg.solve(np.swapaxes(L, 1, 2), uh.T[..., None])[..., 0].T
+    state = dict(x=np.ascontiguousarray(np.stack([r, th, ph])), u=np.ascontiguousarray(u),
+                 dxp=np.zeros((3, n)), flags=np.zeros(n, dtype=np.uint8))
+    params = dict(c=1.0, dt=dt, f_rho=1.0, f_E=1.0, dl=1.0, qm=(qm,), curvature=0,
+                  mu_mode=0, grad_mode=0, gca_max_iter=16, gca_fixed_iters=0, gca_tol=1e-7,
+                  n_steps=1000, a=a, r_in=r_in, r_out=r_out)
+    return fields, state, params

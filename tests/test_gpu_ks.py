@@ -1,0 +1,128 @@
+"""Parity of the covariant (Kerr-Schild) CUDA path with the FP64 oracle.
+
+FP64 records: one step from identical states reproduces the oracle's flags
+bit-exactly where the switch margin exceeds 1e-12 and its state to a relative
+1e-12 (fixed implicit-midpoint iteration count on both sides).  FP32 records
+(FP32 field interpolation, FP64 everything else): within FP32 rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_14401_gb300 import inputs
+from tests.helpers import copy_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_14401_gb300 import gcb
+    return gcb
+
+
+@pytest.fixture(scope="module")
+def wald():
+    return inputs.kerr_wald(nr=96, nth=80, n_particles=3000, seed=41)
+
+
+def oracle_setup(fields, p, **over):
+    q = dict(p, **over)
+    of = O.ks_grid_field(fields)
+    kp = O.ks_params(q["a"], q["r_in"], q["r_out"])
+    op = O.make_params(c=1.0, dt=q["dt"], f_rho=q["f_rho"], f_E=q["f_E"], qm=q["qm"],
+                       mu_mode=q.get("mu_mode", 0), force=q.get("force", 0),
+                       max_iter=q.get("gca_max_iter", 16), fixed_iters=q.get("gca_fixed_iters", 0),
+                       tol=q.get("gca_tol", 1e-7))
+    return of, kp, op, O.ks_cell_sizes(of, q["a"])
+
+
+def run_both(G, fields, st, p, n_steps=1, dtype="f64", **over):
+    q = dict(p, **over)
+    grid = G.KsGrid(fields, q["a"], q["r_in"], q["r_out"], dtype=dtype)
+    ds = G.State.from_numpy(st, precision="fp64")
+    gs = G.push_ks(ds, grid, G.make_params(q), n_steps)
+    got = ds.to_numpy()
+    ref = copy_state(st)
+    of, kp, op, dl = oracle_setup(fields, p, **over)
+    os_ = O.push_ks(ref, of, kp, op, n_steps, dl=dl)
+    return got, ref, gs, os_, grid, dl
+
+
+def margins(fields, st, p, **over):
+    of, kp, op, dl = oracle_setup(fields, p, **over)
+    m = np.empty(st["flags"].size)
+    for i in range(m.size):
+        _, _, _, det = O.ks_step_one(of, kp, op, st["x"][:, i], st["u"][:, i],
+                                     int(st["flags"][i]), dl)
+        m[i] = det.margin
+    return m
+
+
+def test_cell_sizes_match(G, wald):
+    fields, st, p = wald
+    grid = G.KsGrid(fields, p["a"], p["r_in"], p["r_out"], dtype="f64")
+    dl_gpu = grid.dl.cpu().numpy().reshape(79, 95)
+    dl_orc = O.ks_cell_sizes(O.ks_grid_field(fields), p["a"])
+    assert np.allclose(dl_gpu, dl_orc, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("qm,force", [(-1e3, 0), (-3.0, 0), (-1e3, 1), (-1e3, 2), (-30.0, 0)])
+def test_fp64_one_step(G, wald, qm, force):
+    fields, st, p = wald
+    over = dict(qm=(qm,), force=force, gca_fixed_iters=5)
+    m = margins(fields, st, p, **over)
+    got, ref, gs, os_, _, _ = run_both(G, fields, st, p, **over)
+    robust = np.abs(m) > 1e-12
+    assert not np.any((got["flags"] != ref["flags"]) & robust)
+    same = got["flags"] == ref["flags"]
+    assert same.mean() > 0.999
+    dx = np.abs(got["x"] - ref["x"])[:, same]
+    dx[2] = np.minimum(dx[2], 2 * np.pi - dx[2])
+    assert np.all(dx <= 1e-12 * np.maximum(np.abs(ref["x"][:, same]), 1.0))
+    un = np.linalg.norm(ref["u"][:, same], axis=0) + 1.0
+    assert np.all(np.abs(got["u"] - ref["u"])[:, same] <= 1e-12 * un)
+    for k in ("n_boris", "n_gca", "n_gcafail", "n_nonfinite", "sum_iter", "max_iter"):
+        assert gs[k] == os_[k], k
+    if force == 0 and qm == -30.0:
+        assert gs["n_boris"] > 0 and gs["n_gca"] > 0
+
+
+def test_fp64_tolerance_mode_and_ten_steps(G, wald):
+    fields, st, p = wald
+    got, ref, gs, os_, _, _ = run_both(G, fields, st, p, n_steps=10, qm=(-30.0,))
+    same = (got["flags"] == ref["flags"])
+    assert same.mean() > 0.99
+    d = np.abs(got["x"] - ref["x"])[:, same]
+    d[2] = np.minimum(d[2], 2 * np.pi - d[2])
+    assert np.median(d) < 1e-12 and np.max(d[0]) < 1e-6
+    assert abs(gs["n_gca"] - os_["n_gca"]) <= 0.01 * max(1, os_["n_gca"])
+
+
+def test_fp32_records_close_to_oracle(G, wald):
+    fields, st, p = wald
+    got, ref, gs, os_, _, _ = run_both(G, fields, st, p, dtype="f32", qm=(-1e3,),
+                                       gca_fixed_iters=5)
+    same = got["flags"] == ref["flags"]
+    assert same.mean() > 0.995
+    rel = np.abs(got["x"][0] - ref["x"][0]) / ref["x"][0]
+    assert np.max(rel[same]) < 1e-6
+    un = np.linalg.norm(ref["u"], axis=0) + 1.0
+    assert np.max((np.abs(got["u"] - ref["u"]) / un)[:, same]) < 1e-4
+
+
+def test_exits_and_frozen(G, wald):
+    fields, st, p = wald
+    st = copy_state(st)
+    st["x"][0, :5] = p["r_in"] * 1.0001           # at the inner edge, falling in
+    st["u"][0, :5] = -5.0
+    st["u"][1, 7] = np.nan
+    got, ref, gs, os_, _, _ = run_both(G, fields, st, p, n_steps=3, qm=(-3.0,),
+                                       gca_fixed_iters=5)
+    assert np.array_equal(got["flags"] & (G.FLAG_EXITED | G.FLAG_NONFINITE),
+                          ref["flags"] & (O.FLAG_EXITED | O.FLAG_NONFINITE))
+    assert np.all(got["flags"][:5] & G.FLAG_EXITED)
+    assert gs["n_nonfinite"] == os_["n_nonfinite"]
