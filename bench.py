@@ -275,7 +275,7 @@ def main():
 
     def push(n):
         if ks:
-            return G.push_ks(ds, grid, gp, n, stats=n == 1 and False)
+            return G.push_ks(ds, grid, gp, n, stats=False)
         return G.push(ds, grid, gp, n, workspace=ws, stats=False)
 
     def one_step():
