@@ -210,6 +210,49 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
                        gcb_stats *out);
 
 /*
+ * ---- Adjoint of the flat-space push (2D, gradient-grid records, no sorting).
+ * Gradients of an observable L of the final state with respect to the
+ * initial state and to every field-record value.  Not part of the paper: a
+ * reverse sweep over the steps (branch and iteration count of every
+ * particle-step held fixed), from checkpoints stored every ckpt_every steps
+ * with the segment between checkpoints recomputed forward.
+ *
+ * Workspace bytes for gcb_adjoint_sr (256-byte aligned device buffer).
+ */
+#define GCB_ADJOINT_MAX_ITER 22   /* gca_max_iter / gca_fixed_iters limit */
+
+size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, int n_steps,
+                                   int ckpt_every);
+
+/*
+ *   p0         : initial state (device arrays, read only; FP64 or mixed
+ *                layout as for gcb_push_sr, ndim 2).
+ *   g, prm     : as for gcb_push_sr; needs g->has_grad and grad_mode GRID;
+ *                sorting is not applied.  Use gca_fixed_iters > 0 so every
+ *                particle-step has the same iteration count as the forward.
+ *   lam[7]     : device arrays of n elements of the momentum type, in the
+ *                order x0 x1 u0 u1 u2 dxp0 dxp1: on entry dL/d(final state),
+ *                on return dL/d(initial state).
+ *   grad_rec   : device array of n0*n1*12 doubles, overwritten with dL/d(record
+ *                value) for every node and record component.
+ * Errors: GCB_EINVAL / GCB_EUNSUPPORTED / GCB_ENOMEM as for gcb_push_sr.
+ */
+gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_params *prm,
+                          int n_steps, int ckpt_every, void *const *lam, double *grad_rec,
+                          void *cuda_stream, void *ws, size_t ws_bytes);
+
+/*
+ * Fields linear in n_modes amplitudes a_m: rec = base + sum_m a_m pat_m
+ * (gcb_grid_combine, writes g->rec) and dL/da_m = <grad_rec, pat_m>
+ * (gcb_grad_project, out: n_modes doubles).  base, pat: device records in
+ * g's layout, pat holding n_modes consecutive record sets; n_modes <= 64.
+ */
+gcb_status gcb_grid_combine(const gcb_grid *g, const void *base, const void *pat,
+                            const double *amps, int n_modes, void *cuda_stream);
+gcb_status gcb_grad_project(const gcb_grid *g, const double *grad_rec, const void *pat,
+                            int n_modes, double *out, void *cuda_stream);
+
+/*
  * ---- Covariant (Kerr-Schild) scheme: Sec. 2.3 (GREOM), Sec. 2.4 (GRGCA),
  * Sec. 3.2 (coupling).  Geometrized units c = G = M = 1 (prm->c must be 1).
  *

@@ -18,8 +18,8 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libgcb.so")
 OBJ_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["gcb_api.cu", "sort_sr.cu", "gcb_noalloc.cu", "gcb_ks.cu", "push_sr_f64.cu",
-           "push_sr_f32.cu"]
+SOURCES = ["gcb_api.cu", "sort_sr.cu", "gcb_noalloc.cu", "gcb_ks.cu", "adjoint_sr.cu",
+           "push_sr_f64.cu", "push_sr_f32.cu"]
 # the mixed-precision unit uses approximate FP32 division and square root
 # (about 2 ulp) and flushes FP32 denormals; it holds no FP64 arithmetic that
 # these flags would touch.  The FP64 path keeps IEEE operations throughout.

@@ -1,0 +1,395 @@
+// adjoint_sr.cu -- reverse-mode adjoint of the flat-space coupled push
+// (2D, gradient-grid records), for gradients of trajectory observables with
+// respect to the initial state and the field records.
+//
+// One particle-step maps s = (x, u, dxp) and the fields interpolated at the
+// step's gather points F_g (12 components each) to s'.  Given the adjoint
+// lambda' = dL/ds', the kernel forms
+//     dL/ds   = (ds'/ds)^T lambda'                     (kept per particle)
+//     dL/dF_g = (ds'/dF_g)^T lambda'                   (scattered to nodes)
+// and a node record value f_N receives W_g(N) dL/dF_g, the linear shape
+// function being the only way it enters the step.  The columns of the step's
+// Jacobian come from replaying the step on dual numbers (value + N tangents)
+// in registers, N directions per pass; the branch taken and the fixed-point
+// iteration count are those of the plain replay (held fixed, not
+// differentiated).  The sweep over steps runs backwards from checkpoints
+// stored every `ckpt_every` steps, recomputing each segment forward.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include "dual.cuh"
+#include "gcb_internal.h"
+#include "push_sr.cuh"
+
+namespace gcb {
+namespace adj {
+
+constexpr int TPB = 128;
+constexpr int NDIR = 4;          // tangent directions per pass
+constexpr int MAXG = GCB_ADJOINT_MAX_ITER + 2;   // gathers per step: x^n, R^{n-1/2},
+                                                // iterates 1..iters-1, R^{n+1/2}
+constexpr int NF = 12;           // interpolated components per gather (2D, gradient grids)
+constexpr int NS = 7;            // state directions: x(2), u(3), dxp(2)
+
+// Gather on dual positions from plain records: the weights carry the
+// position tangents; this pass's field directions are seeded on the result;
+// nodes and weights of every gather are recorded for the scatter.
+template <typename T, int N>
+struct DualGather {
+    DevGrid<T> g;
+    int *count;
+    int base;
+    int *nodes;
+    T *wts;
+    __device__ __forceinline__ void operator()(const int ib[2], const Dual<T, N> l[2],
+                                               FieldPt<Dual<T, N>, 2> &F) const
+    {
+        using D = Dual<T, N>;
+        const int k = (*count)++;
+        int i0[2], i1[2];
+        D t[2];
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            T tv;
+            cell_of(g, d, ib[d], l[d].v, tv, i0[d], i1[d]);
+            const T c = floor(l[d].v * g.inv_dx[d]);
+            t[d] = l[d] * g.inv_dx[d] - c;   // = tv, with the position's tangent
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { F.E[c] = D(T(0)); F.B[c] = D(T(0)); }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) F.dB[i][j] = D(T(0));
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const int ix = (o & 1) ? i1[0] : i0[0];
+            const int iy = (o & 2) ? i1[1] : i0[1];
+            const int node = iy * g.n[0] + ix;
+            const D wx = (o & 1) ? t[0] : T(1) - t[0];
+            const D wy = (o & 2) ? t[1] : T(1) - t[1];
+            const D W = wx * wy;
+            if (k < MAXG) {
+                nodes[k * 4 + o] = node;
+                wts[k * 4 + o] = W.v;
+            }
+            const T *rp = g.rec + (size_t)node * g.stride;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                F.E[c] = fma(W, D(__ldg(rp + c)), F.E[c]);
+                F.B[c] = fma(W, D(__ldg(rp + 3 + c)), F.B[c]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) F.dB[i][j] = fma(W, D(__ldg(rp + 6 + 3 * i + j)), F.dB[i][j]);
+        }
+        // seed d(output)/d(F_k,c) for the directions of this pass
+        const int d0 = NS + NF * k - base;
+#pragma unroll
+        for (int c = 0; c < NF; ++c) {
+            const int j = d0 + c;
+            if (j >= 0 && j < N) {
+                D &f = c < 3 ? F.E[c] : (c < 6 ? F.B[c - 3] : F.dB[(c - 6) / 3][(c - 6) % 3]);
+                f.d[j] += T(1);
+            }
+        }
+    }
+};
+
+template <typename T>
+struct AdjArgs {
+    DevGrid<T> g;
+    int64_t np;
+    int pair;                    // positions as FP32 pairs
+    const void *x[2];
+    const float *xlo[2];
+    const T *u[3];
+    const T *dxp[2];
+    const uint8_t *flags;
+    T *lam[NS];                  // in: dL/d(state after the step); out: before it
+    double *grad;                // node records' adjoint, stride 12 per node
+    StepPar<T> sp;
+    T qm[4];
+    T rho_thr, f_E, c2;
+    int force;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_pos(const AdjArgs<T> &a, int64_t i, int d, int &ib, T &l,
+                                         bool &fin)
+{
+    if (a.pair) {
+        const float h = ((const float *)a.x[d])[i], lo = a.xlo[d][i];
+        fin = fin && isfinite(h) && isfinite(lo);
+        float lf;
+        split_pos_pair(h, lo, (float)a.g.dx[d], (float)a.g.inv_dx[d], (float)(a.g.n[d] - 1), ib, lf);
+        l = (T)lf;
+    } else {
+        const double x = ((const double *)a.x[d])[i];
+        fin = fin && isfinite(x);
+        split_pos_f64<T>(x, (double)a.g.dx[d], 1.0 / (double)a.g.dx[d], (double)(a.g.n[d] - 1), ib, l);
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(TPB) k_adjoint_sr(const AdjArgs<T> a)
+{
+    using D = Dual<T, N>;
+    int nodes[MAXG * 4];
+    T wts[MAXG * 4];
+    for (int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x; i < a.np;
+         i += (int64_t)gridDim.x * TPB) {
+        const uint8_t fl = a.flags[i];
+        bool fin = true;
+        int ib[2];
+        T l[2], u[3], dxp[2], lo[NS];
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            load_pos(a, i, d, ib[d], l[d], fin);
+            dxp[d] = a.dxp[d][i];
+            fin = fin && isfinite(dxp[d]);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { u[k] = a.u[k][i]; fin = fin && isfinite(u[k]); }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) lo[k] = a.lam[k][i];
+        if (!fin) continue;          // a frozen particle's step is the identity
+
+        // plain replay: the switch, the branch and the iteration count
+        StepPar<T> sp = a.sp;
+        sp.qm = a.qm[(fl >> GCB_SPECIES_SHIFT) & 3];
+        FieldPt<T, 2> F0;
+        gather<T, 2, 2>(a.g, ib, l, F0);
+        const T Q = fabs(sp.qm);
+        const T G = sqrt(T(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * sp.inv_c2);
+        const T Bm = sqrt(F0.B[0] * F0.B[0] + F0.B[1] * F0.B[1] + F0.B[2] * F0.B[2]);
+        const T Em = sqrt(F0.E[0] * F0.E[0] + F0.E[1] * F0.E[1] + F0.E[2] * F0.E[2]);
+        int S = (a.c2 * G < a.rho_thr * Q * Bm && Em < a.f_E * Bm) ? 0 : 1;
+        if (a.force == GCB_FORCE_BORIS) S = 1;
+        if (a.force == GCB_FORCE_GCA) S = 0;
+        int iters = 0;
+        bool gca = false;
+        if (S == 0) {
+            T uu[3] = {u[0], u[1], u[2]}, disp[2];
+            bool ncv;
+            gca = gca_step<T, 2, 2>(PlainGather<T, 2, 2>{a.g}, sp, ib, l, dxp, F0, uu, disp, iters, ncv);
+        }
+        const int ngather = gca ? iters + 2 : 1;
+        if (ngather > MAXG) continue;    // excluded by the host's iteration-cap check
+        const int ndir = NS + NF * ngather;
+
+        StepPar<D> sd;
+        sd.c = D(sp.c);
+        sd.inv_c2 = D(sp.inv_c2);
+        sd.dt = D(sp.dt);
+        sd.half_dt = D(sp.half_dt);
+        sd.qm = D(sp.qm);
+        sd.curvature = sp.curvature;
+        sd.mu_mode = sp.mu_mode;
+        sd.max_iter = sp.max_iter;
+        sd.fixed_iters = gca ? iters : sp.fixed_iters;   // replay exactly this many
+        sd.tol = D(T(-1));
+        T li[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) li[k] = T(0);
+        for (int base = 0; base < ndir; base += N) {
+            D ld[2], ud[3], dd[2];
+#pragma unroll
+            for (int d = 0; d < 2; ++d) { ld[d] = D(l[d]); dd[d] = D(dxp[d]); }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) ud[k] = D(u[k]);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const int dir = base + j;
+                if (dir < 2) ld[dir].d[j] = T(1);
+                else if (dir < 5) ud[dir - 2].d[j] = T(1);
+                else if (dir < 7) dd[dir - 5].d[j] = T(1);
+            }
+            int count = 0;
+            DualGather<T, N> gth{a.g, &count, base, nodes, wts};
+            FieldPt<D, 2> Fd;
+            gth(ib, ld, Fd);
+            D disp[2];
+            bool ok = false;
+            if (gca) {
+                int it2;
+                bool ncv2;
+                ok = gca_step<D, 2, 2>(gth, sd, ib, ld, dd, Fd, ud, disp, it2, ncv2);
+            }
+            if (!ok) boris<D, 2>(Fd.E, Fd.B, sd, ud, disp);
+            // columns of this pass, contracted with the output adjoint
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const int dir = base + j;
+                if (dir >= ndir) break;
+                T c = lo[2] * ud[0].d[j] + lo[3] * ud[1].d[j] + lo[4] * ud[2].d[j];
+#pragma unroll
+                for (int d = 0; d < 2; ++d)
+                    c += lo[d] * (ld[d].d[j] + disp[d].d[j]) + lo[5 + d] * disp[d].d[j];
+                if (dir < NS) {
+                    li[dir] = c;
+                } else if (c != T(0)) {
+                    const int gk = (dir - NS) / NF, comp = (dir - NS) % NF;
+#pragma unroll
+                    for (int o = 0; o < 4; ++o)
+                        atomicAdd(&a.grad[(size_t)nodes[gk * 4 + o] * 12 + comp],
+                                  (double)(wts[gk * 4 + o] * c));
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) a.lam[k][i] = li[k];
+    }
+}
+
+template <typename T>
+static gcb_status launch(const AdjArgs<T> &a, cudaStream_t st)
+{
+    if (a.np == 0) return GCB_OK;
+    int64_t nb = (a.np + TPB - 1) / TPB;
+    if (nb > 152 * 64) nb = 152 * 64;
+    k_adjoint_sr<T, NDIR><<<(int)nb, TPB, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("k_adjoint_sr launch: %s", cudaGetErrorString(e));
+        return GCB_ECUDA;
+    }
+    return GCB_OK;
+}
+
+}  // namespace adj
+
+// The adjoint of one step for all particles whose pre-step state is `s`.
+gcb_status adjoint_step(const gcb_particles *s, const gcb_grid *g, const gcb_params *prm,
+                        void *const lam[7], double *grad, cudaStream_t st)
+{
+    auto fill = [&](auto &a, auto tag) {
+        using T = decltype(tag);
+        a.g.rec = static_cast<const T *>(g->rec);
+        a.g.stride = g->stride;
+        for (int d = 0; d < 3; ++d) {
+            a.g.n[d] = (int)g->n[d];
+            a.g.nR[d] = (T)g->n[d];
+            a.g.dx[d] = (T)g->dx[d];
+            a.g.inv_dx[d] = (T)(1.0 / g->dx[d]);
+        }
+        a.np = s->n;
+        a.pair = s->pos_mode == GCB_POS_F32PAIR;
+        for (int d = 0; d < 2; ++d) {
+            a.x[d] = s->x[d];
+            a.xlo[d] = static_cast<const float *>(s->x_lo[d]);
+            a.dxp[d] = static_cast<const T *>(s->dxp[d]);
+        }
+        for (int k = 0; k < 3; ++k) a.u[k] = static_cast<const T *>(s->u[k]);
+        a.flags = s->flags;
+        for (int k = 0; k < 7; ++k) a.lam[k] = static_cast<T *>(lam[k]);
+        a.grad = grad;
+        a.sp.c = (T)prm->c;
+        a.sp.inv_c2 = (T)(1.0 / (prm->c * prm->c));
+        a.sp.dt = (T)prm->dt;
+        a.sp.half_dt = (T)(0.5 * prm->dt);
+        a.sp.qm = T(0);
+        a.sp.curvature = prm->curvature;
+        a.sp.mu_mode = prm->mu_mode;
+        a.sp.max_iter = prm->gca_max_iter;
+        a.sp.fixed_iters = prm->gca_fixed_iters;
+        a.sp.tol = (T)prm->gca_tol;
+        for (int k = 0; k < 4; ++k) a.qm[k] = (T)prm->qm[k];
+        a.rho_thr = (T)(prm->f_rho * prm->dl);
+        a.f_E = (T)prm->f_E;
+        a.c2 = (T)(prm->c * prm->c);
+        a.force = prm->force;
+    };
+    if (s->mom_dtype == GCB_F64) {
+        adj::AdjArgs<double> a;
+        fill(a, 0.0);
+        return adj::launch(a, st);
+    }
+    adj::AdjArgs<float> a;
+    fill(a, 0.0f);
+    return adj::launch(a, st);
+}
+
+}  // namespace gcb
+
+// ---------------------------------------------------------------------------
+// mode projection and field combination (fields linear in mode amplitudes)
+// ---------------------------------------------------------------------------
+namespace gcb {
+namespace adj {
+
+// dL/da_m = sum_e grad[e] pat_m[e]; grid row m = blockIdx.y.
+template <typename PT>
+__global__ void __launch_bounds__(256) k_project(const double *grad, const PT *pat, int64_t nelem,
+                                                 double *out)
+{
+    __shared__ double s_w[8];
+    const int m = blockIdx.y;
+    const PT *pm = pat + (size_t)m * nelem;
+    double acc = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nelem;
+         e += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(grad[e], (double)pm[e], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w];
+        atomicAdd(&out[m], t);
+    }
+}
+
+template <typename PT>
+__global__ void k_combine(PT *rec, const PT *base, const PT *pat, const double *amps, int64_t nelem,
+                          int nmodes)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nelem;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double v = (double)base[e];
+        for (int m = 0; m < nmodes; ++m) v = fma(amps[m], (double)pat[(size_t)m * nelem + e], v);
+        rec[e] = (PT)v;
+    }
+}
+
+}  // namespace adj
+
+gcb_status grad_project(const gcb_grid *g, const double *grad, const void *pat, int nmodes,
+                        double *out, cudaStream_t st)
+{
+    const int64_t nelem = g->n[0] * g->n[1] * g->n[2] * (int64_t)g->stride;
+    if (cudaMemsetAsync(out, 0, sizeof(double) * nmodes, st) != cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(cudaGetLastError()));
+        return GCB_ECUDA;
+    }
+    int64_t nb = (nelem + 255) / 256;
+    if (nb > 152 * 4) nb = 152 * 4;
+    const dim3 grid((unsigned)nb, (unsigned)nmodes);
+    if (g->dtype == GCB_F32)
+        adj::k_project<float><<<grid, 256, 0, st>>>(grad, (const float *)pat, nelem, out);
+    else
+        adj::k_project<double><<<grid, 256, 0, st>>>(grad, (const double *)pat, nelem, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error("k_project: %s", cudaGetErrorString(e)); return GCB_ECUDA; }
+    return GCB_OK;
+}
+
+gcb_status grid_combine(const gcb_grid *g, const void *base, const void *pat, const double *amps,
+                        int nmodes, cudaStream_t st)
+{
+    const int64_t nelem = g->n[0] * g->n[1] * g->n[2] * (int64_t)g->stride;
+    int64_t nb = (nelem + 255) / 256;
+    if (nb > 152 * 32) nb = 152 * 32;
+    if (g->dtype == GCB_F32)
+        adj::k_combine<float><<<(int)nb, 256, 0, st>>>((float *)g->rec, (const float *)base,
+                                                       (const float *)pat, amps, nelem, nmodes);
+    else
+        adj::k_combine<double><<<(int)nb, 256, 0, st>>>((double *)g->rec, (const double *)base,
+                                                        (const double *)pat, amps, nelem, nmodes);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error("k_combine: %s", cudaGetErrorString(e)); return GCB_ECUDA; }
+    return GCB_OK;
+}
+
+}  // namespace gcb

@@ -2,6 +2,8 @@
 // checks, the step loop, the workspace counters, and the small layout kernels
 // (node-record packing, FP32-pair position split/join).
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -417,6 +419,171 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
         if (s != GCB_OK) return s;
     }
     return read_stats(stats, st, out);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// adjoint driver: checkpoints, segment recomputation, backward sweep
+// ---------------------------------------------------------------------------
+namespace {
+
+size_t a256(size_t v) { return (v + 255) / 256 * 256; }
+
+// bytes of one state set and the view of a set carved at `base`
+size_t state_set_bytes(const gcb_particles *p, int nd)
+{
+    const size_t n = (size_t)p->n;
+    const size_t pe = p->pos_mode == GCB_POS_F64 ? 8 : 4, me = p->mom_dtype == GCB_F64 ? 8 : 4;
+    size_t b = nd * a256(n * pe) + 3 * a256(n * me) + nd * a256(n * me) + a256(n);
+    if (p->pos_mode == GCB_POS_F32PAIR) b += nd * a256(n * 4);
+    return b;
+}
+
+gcb_particles state_view(const gcb_particles *p, int nd, uint8_t *base)
+{
+    gcb_particles q = *p;
+    const size_t n = (size_t)p->n;
+    const size_t pe = p->pos_mode == GCB_POS_F64 ? 8 : 4, me = p->mom_dtype == GCB_F64 ? 8 : 4;
+    size_t off = 0;
+    for (int d = 0; d < 3; ++d) { q.x[d] = q.x_lo[d] = q.u[d] = q.dxp[d] = nullptr; }
+    for (int d = 0; d < nd; ++d) { q.x[d] = base + off; off += a256(n * pe); }
+    if (p->pos_mode == GCB_POS_F32PAIR)
+        for (int d = 0; d < nd; ++d) { q.x_lo[d] = base + off; off += a256(n * 4); }
+    for (int k = 0; k < 3; ++k) { q.u[k] = base + off; off += a256(n * me); }
+    for (int d = 0; d < nd; ++d) { q.dxp[d] = base + off; off += a256(n * me); }
+    q.flags = base + off;
+    q.pid = nullptr;
+    return q;
+}
+
+gcb_status copy_state(const gcb_particles *dst, const gcb_particles *src, int nd, cudaStream_t st)
+{
+    const size_t n = (size_t)src->n;
+    const size_t pe = src->pos_mode == GCB_POS_F64 ? 8 : 4, me = src->mom_dtype == GCB_F64 ? 8 : 4;
+    bool ok = true;
+    for (int d = 0; d < nd; ++d) {
+        ok = ok && cudaMemcpyAsync(dst->x[d], src->x[d], n * pe, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+        if (src->pos_mode == GCB_POS_F32PAIR)
+            ok = ok && cudaMemcpyAsync(dst->x_lo[d], src->x_lo[d], n * 4, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(dst->dxp[d], src->dxp[d], n * me, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    }
+    for (int k = 0; k < 3; ++k)
+        ok = ok && cudaMemcpyAsync(dst->u[k], src->u[k], n * me, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(dst->flags, src->flags, n, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    if (!ok) {
+        set_error("state copy: %s", cudaGetErrorString(cudaGetLastError()));
+        return GCB_ECUDA;
+    }
+    return GCB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, int n_steps,
+                                   int ckpt_every)
+{
+    if (!p || !g || n_steps < 1 || ckpt_every < 1 || p->n < 0) return 0;
+    const int nck = (n_steps + ckpt_every - 1) / ckpt_every;
+    const size_t S = state_set_bytes(p, g->ndim);
+    return kStatsBytes + (size_t)(nck + (ckpt_every - 1) + 2) * S;
+}
+
+gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_params *prm0,
+                          int n_steps, int ckpt_every, void *const *lam, double *grad_rec,
+                          void *cuda_stream, void *ws, size_t ws_bytes)
+{
+    g_err[0] = 0;
+    gcb_status s = check_problem(p0, g, prm0);
+    if (s != GCB_OK) return s;
+    if (g->ndim != 2 || !g->has_grad || prm0->grad_mode != GCB_GRAD_GRID) {
+        set_error("the adjoint supports 2D grids with gradient records (grad_mode GRID)");
+        return GCB_EUNSUPPORTED;
+    }
+    if (n_steps < 1 || ckpt_every < 1) { set_error("n_steps and ckpt_every must be >= 1"); return GCB_EINVAL; }
+    if (prm0->gca_max_iter > GCB_ADJOINT_MAX_ITER || prm0->gca_fixed_iters > GCB_ADJOINT_MAX_ITER) {
+        set_error("the adjoint records at most %d fixed-point iterations per step", GCB_ADJOINT_MAX_ITER);
+        return GCB_EUNSUPPORTED;
+    }
+    if (!lam || !grad_rec || !aligned(grad_rec, 8)) { set_error("lam or grad_rec NULL"); return GCB_EINVAL; }
+    const size_t me = p0->mom_dtype == GCB_F64 ? 8 : 4;
+    for (int k = 0; k < 7; ++k)
+        if (p0->n > 0 && (!lam[k] || !aligned(lam[k], me))) { set_error("lam[%d] NULL or misaligned", k); return GCB_EINVAL; }
+    const size_t need = gcb_adjoint_workspace_bytes(p0, g, n_steps, ckpt_every);
+    if (!ws || !aligned(ws, 256)) { set_error("workspace NULL or not 256-byte aligned"); return GCB_EINVAL; }
+    if (ws_bytes < need) { set_error("workspace too small (%zu < %zu bytes)", ws_bytes, need); return GCB_ENOMEM; }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    gcb_params prm = *prm0;
+    prm.sort_every = 0;
+    const int nd = g->ndim;
+    const int nck = (n_steps + ckpt_every - 1) / ckpt_every;
+    const size_t S = state_set_bytes(p0, nd);
+    uint8_t *w = (uint8_t *)ws;
+    unsigned long long *stats = (unsigned long long *)w;
+    uint8_t *ck = w + kStatsBytes;
+    uint8_t *seg = ck + (size_t)nck * S;
+    uint8_t *tmp = seg + (size_t)(ckpt_every - 1) * S;
+    const size_t nrec = (size_t)(g->n[0] * g->n[1] * g->n[2]) * 12;
+    if (cudaMemsetAsync(grad_rec, 0, nrec * sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(stats, 0, kStatsBytes, st) != cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(cudaGetLastError()));
+        return GCB_ECUDA;
+    }
+    if (p0->n == 0) return GCB_OK;
+    const bool fp64 = p0->mom_dtype == GCB_F64;
+    auto step = [&](const gcb_particles *out, const gcb_particles *in) {
+        return fp64 ? push_step_f64(out, in, g, &prm, st, stats) : push_step_f32(out, in, g, &prm, st, stats);
+    };
+    // forward: checkpoints every ckpt_every steps
+    gcb_particles c0 = state_view(p0, nd, ck);
+    if ((s = copy_state(&c0, p0, nd, st)) != GCB_OK) return s;
+    gcb_particles cur = c0;
+    gcb_particles tA = state_view(p0, nd, tmp), tB = state_view(p0, nd, tmp + S);
+    for (int k = 0; k + 1 < nck * ckpt_every && k < (nck - 1) * ckpt_every; ++k) {
+        const bool boundary = (k + 1) % ckpt_every == 0;
+        gcb_particles out = boundary ? state_view(p0, nd, ck + (size_t)((k + 1) / ckpt_every) * S)
+                                     : (cur.u[0] == tA.u[0] ? tB : tA);
+        if ((s = step(&out, &cur)) != GCB_OK) return s;
+        cur = out;
+    }
+    // backward over segments
+    for (int sg = nck - 1; sg >= 0; --sg) {
+        const int len = (n_steps - sg * ckpt_every) < ckpt_every ? n_steps - sg * ckpt_every : ckpt_every;
+        std::vector<gcb_particles> states((size_t)len);
+        states[0] = state_view(p0, nd, ck + (size_t)sg * S);
+        for (int j = 1; j < len; ++j) {
+            states[j] = state_view(p0, nd, seg + (size_t)(j - 1) * S);
+            if ((s = step(&states[j], &states[j - 1])) != GCB_OK) return s;
+        }
+        for (int j = len - 1; j >= 0; --j)
+            if ((s = adjoint_step(&states[j], g, &prm, lam, grad_rec, st)) != GCB_OK) return s;
+    }
+    return GCB_OK;
+}
+
+gcb_status gcb_grid_combine(const gcb_grid *g, const void *base, const void *pat,
+                            const double *amps, int n_modes, void *cuda_stream)
+{
+    g_err[0] = 0;
+    gcb_status s = check_grid(g);
+    if (s != GCB_OK) return s;
+    if (!base || !pat || !amps || n_modes < 0 || n_modes > 64) { set_error("gcb_grid_combine: bad arguments"); return GCB_EINVAL; }
+    return grid_combine(g, base, pat, amps, n_modes, (cudaStream_t)cuda_stream);
+}
+
+gcb_status gcb_grad_project(const gcb_grid *g, const double *grad_rec, const void *pat,
+                            int n_modes, double *out, void *cuda_stream)
+{
+    g_err[0] = 0;
+    gcb_status s = check_grid(g);
+    if (s != GCB_OK) return s;
+    if (g->stride != 12 || !grad_rec || !pat || !out || n_modes < 1 || n_modes > 64) {
+        set_error("gcb_grad_project: needs 12-element records and 1..64 modes");
+        return GCB_EINVAL;
+    }
+    return grad_project(g, grad_rec, pat, n_modes, out, (cudaStream_t)cuda_stream);
 }
 
 }  // extern "C"

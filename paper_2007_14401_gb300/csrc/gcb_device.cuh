@@ -431,8 +431,21 @@ __device__ __forceinline__ void boris(const R E[3], const R B[3], const StepPar<
 // u^{n-1/2}.  Returns
 // false when the step cannot be taken (B = 0 or v_E >= c on the path, or no
 // Lorentz factor >= 1 solves the quadratic); u and disp are then untouched.
+// The gather the step uses: any callable gth(ib, l, F).  PlainGather is the
+// kernels' (the grid's records in the arithmetic type); the adjoint kernel
+// passes one that also records weights and seeds tangents.
 template <typename R, int ND, int GM>
-__device__ __forceinline__ bool gca_step(const DevGrid<R> &g, const StepPar<R> &s, const int ib[ND],
+struct PlainGather {
+    DevGrid<R> g;
+    __device__ __forceinline__ void operator()(const int ib[ND], const R l[ND],
+                                               FieldPt<R, ND> &F) const
+    {
+        gather_any<R, ND, GM>(g, ib, l, F);
+    }
+};
+
+template <typename R, int ND, int GM, typename Gth>
+__device__ __forceinline__ bool gca_step(const Gth &gth, const StepPar<R> &s, const int ib[ND],
                                          const R ln[ND], const R dxp[ND], const FieldPt<R, ND> &F0,
                                          R u[3], R disp[ND], int &iters, bool &nonconv)
 {
@@ -444,7 +457,7 @@ __device__ __forceinline__ bool gca_step(const DevGrid<R> &g, const StepPar<R> &
     R pt[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) pt[d] = fma(R(-0.5), dxp[d], ln[d]);
-    gather_any<R, ND, GM>(g, ib, pt, F);
+    gth(ib, pt, F);
     make_frame<R, ND, (GM != 0)>(F, s.c, s.inv_c2, f);
     if (!(f0.ok && f.ok)) return false;
     R Gfull = sqrt(R(1) + dot3(u, u) * s.inv_c2);
@@ -524,7 +537,7 @@ __device__ __forceinline__ bool gca_step(const DevGrid<R> &g, const StepPar<R> &
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) pt[d] = ln[d] + dk[d];
-        gather_any<R, ND, GM>(g, ib, pt, F);
+        gth(ib, pt, F);
         make_frame<R, ND, (GM != 0)>(F, s.c, s.inv_c2, f);
         okall = okall && f.ok;   // a bad frame fails the step after the loop
         gc_vel(f, s, upn, mu, uperp, V);
@@ -534,7 +547,7 @@ __device__ __forceinline__ bool gca_step(const DevGrid<R> &g, const StepPar<R> &
     // reconstruction at R^{n+1/2} = (R^{n+1} + R^n)/2 (Sec. 3.1)
 #pragma unroll
     for (int d = 0; d < ND; ++d) pt[d] = fma(R(0.5), dk[d], ln[d]);
-    gather_any<R, ND, GM>(g, ib, pt, F);
+    gth(ib, pt, F);
     make_frame<R, ND, (GM != 0)>(F, s.c, s.inv_c2, f);
     if (!f.ok) return false;
     R Gp = gamma_gc(f, s, upn, mu, uperp);

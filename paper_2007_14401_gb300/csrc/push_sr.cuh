@@ -28,7 +28,7 @@ struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : GCB_TILE_F32; };
 
 // minimum resident blocks per SM requested from the register allocator
 #ifndef GCB_MIN_BLOCKS_F32
-#define GCB_MIN_BLOCKS_F32 2
+#define GCB_MIN_BLOCKS_F32 4
 #endif
 template <typename R, int ND>
 struct MinBlocks { static constexpr int n = (sizeof(R) == 8 || ND == 3) ? 1 : GCB_MIN_BLOCKS_F32; };
@@ -305,7 +305,8 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
 #pragma unroll
                         for (int j = 0; j < 3; ++j) F0.dB[ii][j] = s_F[6 + 3 * ii + j][sl];
                 }
-                done = gca_step<R, ND, GM>(a.g, sp, ibs, ls, ds, F0, us, disp, it, ncv);
+                done = gca_step<R, ND, GM>(PlainGather<R, ND, GM>{a.g}, sp, ibs, ls, ds, F0, us,
+                                           disp, it, ncv);
                 if (!done) {
                     fail = true;
                     it = 0;

@@ -64,7 +64,8 @@ class GcbKsParams(C.Structure):
 
 EXPORTS = ["gcb_version", "gcb_status_string", "gcb_last_error", "gcb_grid_stride",
            "gcb_grid_pack", "gcb_pos_split", "gcb_pos_join", "gcb_workspace_bytes",
-           "gcb_sort_sr", "gcb_push_sr", "gcb_push_sr_noalloc", "gcb_ks_cell_size",
+           "gcb_sort_sr", "gcb_push_sr", "gcb_push_sr_noalloc", "gcb_adjoint_workspace_bytes",
+           "gcb_adjoint_sr", "gcb_grid_combine", "gcb_grad_project", "gcb_ks_cell_size",
            "gcb_push_ks"]
 
 
@@ -98,6 +99,17 @@ def load_library(path: str | None = None):
     lib.gcb_push_sr_noalloc.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int,
                                         C.c_void_p, P(GcbStats)]
     lib.gcb_push_sr_noalloc.restype = C.c_int
+    lib.gcb_adjoint_workspace_bytes.argtypes = [P(GcbParticles), P(GcbGrid), C.c_int, C.c_int]
+    lib.gcb_adjoint_workspace_bytes.restype = C.c_size_t
+    lib.gcb_adjoint_sr.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int, C.c_int,
+                                   P(C.c_void_p), C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t]
+    lib.gcb_adjoint_sr.restype = C.c_int
+    lib.gcb_grid_combine.argtypes = [P(GcbGrid), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                     C.c_void_p]
+    lib.gcb_grid_combine.restype = C.c_int
+    lib.gcb_grad_project.argtypes = [P(GcbGrid), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                     C.c_void_p]
+    lib.gcb_grad_project.restype = C.c_int
     lib.gcb_ks_cell_size.argtypes = [P(GcbGridKs), P(GcbKsParams), C.c_void_p, C.c_void_p]
     lib.gcb_ks_cell_size.restype = C.c_int
     lib.gcb_push_ks.argtypes = [P(GcbParticles), P(GcbGridKs), P(GcbKsParams), P(GcbParams),
@@ -235,6 +247,45 @@ class State:
         self.flags.copy_(torch.as_tensor(np.asarray(st["flags"], dtype=np.uint8)))
         torch.cuda.synchronize()
 
+    def set_tensors(self, x64: torch.Tensor, u: torch.Tensor, dxp: torch.Tensor,
+                    flags: torch.Tensor, stream=None):
+        """Fill from device tensors: x float64 (ndim, n), u (3, n), dxp (ndim, n)."""
+        x64 = x64.to(torch.float64).contiguous()
+        if self.pos_mode == POS_F64:
+            self.x.copy_(x64)
+        elif self.n:
+            for d in range(self.ndim):
+                _check(_lib.gcb_pos_split(self.n, C.c_void_p(x64[d].data_ptr()),
+                                          C.c_void_p(self.x[d].data_ptr()),
+                                          C.c_void_p(self.x_lo[d].data_ptr()), _stream_ptr(stream)),
+                       "gcb_pos_split")
+        self.u.copy_(u)
+        self.dxp.copy_(dxp)
+        self.flags.copy_(flags)
+
+    def clone(self) -> "State":
+        c = State.__new__(State)
+        c.n, c.ndim, c.precision = self.n, self.ndim, self.precision
+        c.pos_mode, c.mom_dtype = self.pos_mode, self.mom_dtype
+        c.x, c.u, c.dxp, c.flags = (self.x.clone(), self.u.clone(), self.dxp.clone(),
+                                    self.flags.clone())
+        c.x_lo = self.x_lo.clone() if self.x_lo is not None else None
+        c.pid = self.pid.clone() if self.pid is not None else None
+        c._make_struct()
+        return c
+
+    def x_f64(self, stream=None) -> torch.Tensor:
+        """Positions as a float64 (ndim, n) device tensor (pairs joined)."""
+        if self.pos_mode == POS_F64:
+            return self.x.clone()
+        x = torch.empty((self.ndim, self.n), dtype=torch.float64, device=self.x.device)
+        for d in range(self.ndim if self.n else 0):
+            _check(_lib.gcb_pos_join(self.n, C.c_void_p(self.x[d].data_ptr()),
+                                     C.c_void_p(self.x_lo[d].data_ptr()),
+                                     C.c_void_p(x[d].data_ptr()), _stream_ptr(stream)),
+                   "gcb_pos_join")
+        return x
+
     def to_numpy(self, stream=None) -> dict:
         """The state as plain float64 arrays (positions joined from pairs)."""
         if self.pos_mode == POS_F64:
@@ -303,6 +354,90 @@ def push(state: State, grid: Grid, params: GcbParams, n_steps: int = 1, stream=N
     if stats:
         return {k: getattr(out, k) for k, _ in GcbStats._fields_}
     return None
+
+
+# --------------------------------------------------------------------------
+# adjoint
+# --------------------------------------------------------------------------
+LAM_ORDER = ("x0", "x1", "u0", "u1", "u2", "dxp0", "dxp1")
+
+
+def adjoint(state: State, grid: Grid, params: GcbParams, n_steps: int, lam: torch.Tensor,
+            ckpt_every: int = 16, stream=None) -> torch.Tensor:
+    """Reverse sweep of n_steps pushes from the initial ``state`` (left
+    unchanged).  ``lam`` (7, n) in the momentum dtype holds dL/d(final x0, x1,
+    u0, u1, u2, dxp0, dxp1) and is overwritten with dL/d(initial state).
+    Returns dL/d(record values) as a float64 tensor (nodes, 12)."""
+    nb = _lib.gcb_adjoint_workspace_bytes(C.byref(state.s), C.byref(grid.s), int(n_steps),
+                                          int(ckpt_every))
+    if nb == 0:
+        raise GcbError("gcb_adjoint_workspace_bytes: invalid arguments")
+    ws = torch.empty(nb, dtype=torch.uint8, device=state.u.device)
+    nn = grid.n[0] * grid.n[1] * grid.n[2]
+    grad = torch.empty((nn, 12), dtype=torch.float64, device=state.u.device)
+    if lam.shape != (7, state.n) or lam.dtype != state.u.dtype or not lam.is_contiguous():
+        raise GcbError("lam must be a contiguous (7, n) tensor of the momentum dtype")
+    ptrs = (C.c_void_p * 7)(*[lam[k].data_ptr() for k in range(7)])
+    rc = _lib.gcb_adjoint_sr(C.byref(state.s), C.byref(grid.s), C.byref(params), int(n_steps),
+                             int(ckpt_every), ptrs, C.c_void_p(grad.data_ptr()),
+                             _stream_ptr(stream), C.c_void_p(ws.data_ptr()), nb)
+    _check(rc, "gcb_adjoint_sr")
+    return grad
+
+
+def grid_combine(grid: Grid, base: torch.Tensor, pat: torch.Tensor, amps: torch.Tensor,
+                 stream=None):
+    """grid.rec = base + sum_m amps[m] pat[m] (records in grid's layout)."""
+    amps = amps.to(device=grid.rec.device, dtype=torch.float64).contiguous()
+    rc = _lib.gcb_grid_combine(C.byref(grid.s), C.c_void_p(base.data_ptr()),
+                               C.c_void_p(pat.data_ptr()), C.c_void_p(amps.data_ptr()),
+                               int(amps.numel()), _stream_ptr(stream))
+    _check(rc, "gcb_grid_combine")
+
+
+def grad_project(grid: Grid, grad: torch.Tensor, pat: torch.Tensor, stream=None) -> torch.Tensor:
+    """dL/da_m = <grad, pat[m]> for fields linear in the amplitudes."""
+    out = torch.empty(pat.shape[0], dtype=torch.float64, device=grad.device)
+    rc = _lib.gcb_grad_project(C.byref(grid.s), C.c_void_p(grad.data_ptr()),
+                               C.c_void_p(pat.data_ptr()), int(pat.shape[0]),
+                               C.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    _check(rc, "gcb_grad_project")
+    return out
+
+
+class ModePush(torch.autograd.Function):
+    """Differentiable n-step push: (x0, u0, dxp0, amps) -> (x, u, dxp), the
+    field records being base + sum_m amps[m] pat[m].  ``ctx_cfg`` is a dict
+    with grid, base, pat, params, n_steps, ckpt_every, flags, precision,
+    pos_mode.  x as float64 (2, n); u (3, n) and dxp (2, n) in the momentum
+    dtype."""
+
+    @staticmethod
+    def forward(ctx, x0, u0, dxp0, amps, cfg):
+        grid = cfg["grid"]
+        grid_combine(grid, cfg["base"], cfg["pat"], amps)
+        st = State(x0.shape[1], 2, cfg.get("precision", "fp64"), cfg.get("pos_mode", "f64"),
+                   device=x0.device)
+        st.set_tensors(x0, u0, dxp0, cfg["flags"])
+        ctx.cfg, ctx.init = cfg, st.clone()
+        push(st, grid, cfg["params"], cfg["n_steps"], stats=False)
+        return st.x_f64(), st.u.clone(), st.dxp.clone()
+
+    @staticmethod
+    def backward(ctx, gx, gu, gdxp):
+        cfg, st = ctx.cfg, ctx.init
+        n = st.n
+        lam = torch.zeros((7, n), dtype=st.u.dtype, device=st.u.device)
+        if gx is not None:
+            lam[0:2] = gx.to(lam.dtype)
+        if gu is not None:
+            lam[2:5] = gu.to(lam.dtype)
+        if gdxp is not None:
+            lam[5:7] = gdxp.to(lam.dtype)
+        grad = adjoint(st, cfg["grid"], cfg["params"], cfg["n_steps"], lam,
+                       cfg.get("ckpt_every", 16))
+        ga = grad_project(cfg["grid"], grad, cfg["pat"])
+        return lam[0:2].to(torch.float64), lam[2:5].clone(), lam[5:7].clone(), ga, None
 
 
 # --------------------------------------------------------------------------

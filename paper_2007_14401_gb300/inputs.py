@@ -169,6 +169,50 @@ def reconnection_2d(nx=2048, ny=1024, dx=1.0, B0=1.0, delta=8.0, psi0=0.1,
     return fields, state, params
 
 
+def reconnection_2d_modes(**kw):
+    """The reconnection workload split for differentiation with respect to the
+    Fourier-mode amplitudes a_m: its fields are base + sum_m a_m pattern_m
+    (B, E = -v_in x B and the central-difference gradients are all linear in
+    the a_m).  Returns (base, patterns, amps, state, params): base and each
+    pattern are field dicts (E, B, dB, dx) without particles; amps, state and
+    params are those of reconnection_2d(**kw), so |q/m| stays fixed when the
+    amplitudes move."""
+    fields, state, params = reconnection_2d(**kw)
+    md = fields["modes"]
+    kz = dict(kw, n_particles=1, mode_amps=np.zeros(len(md["amp"])))
+    base, _, _ = reconnection_2d(**kz)
+    base.pop("modes")
+    ny, nx = np.asarray(fields["B"][0]).shape
+    dx = fields["dx"][0]
+    Lx, Ly = nx * dx, ny * dx
+    X = (np.arange(nx) * dx)[None, :] * np.ones((ny, 1))
+    Y = (np.arange(ny) * dx - 0.5 * Ly)[:, None] * np.ones((1, nx))
+    v = kw.get("vin", 0.1) * np.sin(4 * math.pi * Y / Ly)
+    patterns = []
+    for m in range(len(md["amp"])):
+        kx, ky = 2 * math.pi * md["nx"][m] / Lx, 2 * math.pi * md["ny"][m] / Ly
+        k = math.hypot(kx, ky)
+        sn = np.sin(kx * X + ky * Y + md["phase"][m])
+        Bx, By, Bz = ky / k * sn, -kx / k * sn, np.zeros_like(sn)
+        B = [Bx, By, Bz]
+        patterns.append(dict(E=[np.zeros_like(sn), np.zeros_like(sn), v * Bx], B=B,
+                             dB=central_gradients(B, (dx, dx)), dx=(dx, dx)))
+    return base, patterns, np.asarray(md["amp"], float), state, params
+
+
+def combine_fields(base: dict, patterns: list, amps) -> dict:
+    """base + sum_m amps[m] patterns[m], component by component."""
+    def comb(key):
+        out = []
+        for c in range(len(base[key])):
+            acc = np.array(base[key][c], dtype=np.float64, copy=True)
+            for a, p in zip(amps, patterns):
+                acc = acc + a * np.asarray(p[key][c])
+            out.append(acc)
+        return out
+    return dict(E=comb("E"), B=comb("B"), dB=comb("dB"), dx=base["dx"])
+
+
 # --------------------------------------------------------------------------
 # 3D kinked current sheet, mixed precision
 # --------------------------------------------------------------------------
