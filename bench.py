@@ -10,7 +10,7 @@ one pass of the whole push over all particles, state resident in HBM; the
 particles are re-sorted by cell every 8 steps inside the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload reconnection2d|harris2d_fp64|sheet3d|kerr_wald]
+                  [--workload reconnection2d|harris2d_fp64|sheet3d|kerr_wald|adjoint2d]
 
 Under torchrun every rank pushes its own particles (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.  --impl reference
@@ -86,6 +86,24 @@ WORKLOADS = {
              "power law in the sheet), |q/m| = 20, mixed FP32 (FP32-pair positions)",
         extra=dict(grid=[256, 256, 256], dt=0.45, curvature=1, grad_mode="dw", gca_tol=1e-7)),
 }
+
+
+def _gen_adjoint(n, seed):
+    from paper_2007_14401_gb300 import inputs
+    return inputs.reconnection_2d_modes(nx=512, ny=256, n_particles=n, seed=seed)
+
+
+# The adjoint workload: the reconnection field at 512 x 256 written as base +
+# sum_m a_m pattern_m over its 64 modes; one step of the timed loop is the
+# forward run of ADJ_STEPS pushes plus the reverse sweep for L = mean final
+# kinetic energy, which yields dL/d(initial state) of every particle and
+# dL/da_m.
+ADJ_STEPS, ADJ_CKPT, ADJ_FIXED_ITERS = 256, 16, 4
+ADJOINT = dict(gen=_gen_adjoint, n=1 << 20,
+               desc="adjoint: 2D double Harris + GEM + 64 modes at 512x256, {n} particles, "
+                    f"{ADJ_STEPS} steps, checkpoints every {ADJ_CKPT}, mixed FP32 forward + "
+                    "FP32 adjoint, FP64 node accumulators; L = mean final kinetic energy, "
+                    "gradients w.r.t. the 64 mode amplitudes and all initial states")
 
 
 def workload_config(w, n_total, ngpu, sort_every, sort_tile):
@@ -231,7 +249,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gcb", choices=["gcb", "reference"])
-    ap.add_argument("--workload", default="reconnection2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="reconnection2d",
+                    choices=sorted(WORKLOADS) + ["adjoint2d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -241,6 +260,8 @@ def main():
                     help="particles per GPU (smaller cases for profiling only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "adjoint2d":
+        return run_adjoint(args)
     w = WORKLOADS[args.workload]
     sort_every = w["sort_every"] if args.sort_every is None else args.sort_every
     tile = w["tile"] if args.sort_tile is None else tuple(int(v) for v in args.sort_tile.split(","))
@@ -410,6 +431,100 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+def adjoint_launches():
+    """Kernels of one forward + reverse sweep: ADJ_STEPS pushes; in the sweep
+    the pushes up to the last checkpoint, per segment its recomputed pushes
+    and its adjoint steps, and the mode projection."""
+    nck = (ADJ_STEPS + ADJ_CKPT - 1) // ADJ_CKPT
+    seg = [min(ADJ_CKPT, ADJ_STEPS - s * ADJ_CKPT) for s in range(nck)]
+    return ADJ_STEPS + (nck - 1) * ADJ_CKPT + sum(2 * L - 1 for L in seg) + 1
+
+
+def run_adjoint(args):
+    """Forward ADJ_STEPS pushes + reverse sweep on one GPU (replicas only under
+    torchrun: each rank differentiates its own particles, and the 64 mode
+    gradients would be summed once after the sweep)."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    from paper_2007_14401_gb300 import gcb as G
+    n_req = ADJOINT["n"] if args.particles is None else args.particles
+    base, pats, amps, st, p = ADJOINT["gen"](n_req, 1 + rank)
+    grid = G.Grid(base, dtype="f32")
+    base_rec = grid.rec.clone()
+    pat_rec = torch.stack([G.Grid(q, dtype="f32").rec for q in pats]).contiguous()
+    amps_d = torch.tensor(amps, dtype=torch.float64, device="cuda")
+    G.grid_combine(grid, base_rec, pat_rec, amps_d)
+    init = G.State.from_numpy(st, precision="mixed", pos_mode="pair")
+    gp = G.make_params(p, gca_fixed_iters=ADJ_FIXED_ITERS)
+    n = init.n
+    cur = init.clone()
+    ws = G.Workspace(cur, grid, gp)
+    lam = torch.empty((7, n), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def forward():
+        for t_, s_ in zip(cur.tensors(), init.tensors()):
+            t_.copy_(s_)
+        G.push(cur, grid, gp, ADJ_STEPS, workspace=ws, stats=False)
+
+    def backward():
+        # dL/du_final for L = mean (Gamma - 1) c^2: u / (Gamma n)
+        Gm = torch.sqrt(1.0 + (cur.u * cur.u).sum(0))
+        lam.zero_()
+        lam[2:5] = cur.u / (Gm * n)
+        grad = G.adjoint(init, grid, gp, ADJ_STEPS, lam, ADJ_CKPT)
+        return G.grad_project(grid, grad, pat_rec)
+
+    for _ in range(args.warmup if args.steps > 1 else 1):
+        forward()
+        backward()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    k = max(1, args.steps)
+    ef = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(k)]
+    eb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(k)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(k):
+        ef[i][0].record(stream)
+        forward()
+        ef[i][1].record(stream)
+        eb[i][0].record(stream)
+        ga = backward()
+        eb[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1)
+    ms_f = statistics.median(a.elapsed_time(b) for a, b in ef)
+    ms_b = statistics.median(a.elapsed_time(b) for a, b in eb)
+    value = n * ADJ_STEPS * k / (ms * 1e-3)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+                "steps": k, "warmup": args.warmup, "ms_per_step": ms / k,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": ADJOINT["desc"].format(n=n), "particles": n,
+                           "push_steps_per_step": ADJ_STEPS, "ckpt_every": ADJ_CKPT,
+                           "gca_fixed_iters": ADJ_FIXED_ITERS, "grid": [512, 256],
+                           "modes": len(amps),
+                           "l2": "particle state 39 MB fits L2; checkpoints 620 MB do not"},
+                "adjoint": {"ms_forward": ms_f, "ms_reverse": ms_b,
+                            "reverse_over_forward": ms_b / ms_f,
+                            "dL_da_rms": float(ga.pow(2).mean().sqrt())},
+                "gpu_launches": k * adjoint_launches(), "clocks": clocks, "e2e": None}
+        print(json.dumps(line), flush=True)
     return 0
 
 

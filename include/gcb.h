@@ -221,12 +221,19 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
  */
 #define GCB_ADJOINT_MAX_ITER 22   /* gca_max_iter / gca_fixed_iters limit */
 
+/* How the transposed step is formed: REVERSE, the step's derivative written
+ * out backwards (the fast default); TANGENT, columns of the step's Jacobian
+ * from dual-number replays contracted with the adjoint (a slower second
+ * construction of the same quantity, for cross-checks). */
+enum { GCB_ADJ_REVERSE = 0, GCB_ADJ_TANGENT = 1 };
+
 size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, int n_steps,
                                    int ckpt_every);
 
 /*
  *   p0         : initial state (device arrays, read only; FP64 or mixed
  *                layout as for gcb_push_sr, ndim 2).
+ *   method     : GCB_ADJ_REVERSE or GCB_ADJ_TANGENT.
  *   g, prm     : as for gcb_push_sr; needs g->has_grad and grad_mode GRID;
  *                sorting is not applied.  Use gca_fixed_iters > 0 so every
  *                particle-step has the same iteration count as the forward.
@@ -238,8 +245,8 @@ size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, in
  * Errors: GCB_EINVAL / GCB_EUNSUPPORTED / GCB_ENOMEM as for gcb_push_sr.
  */
 gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_params *prm,
-                          int n_steps, int ckpt_every, void *const *lam, double *grad_rec,
-                          void *cuda_stream, void *ws, size_t ws_bytes);
+                          int n_steps, int ckpt_every, int method, void *const *lam,
+                          double *grad_rec, void *cuda_stream, void *ws, size_t ws_bytes);
 
 /*
  * Fields linear in n_modes amplitudes a_m: rec = base + sum_m a_m pat_m

@@ -19,6 +19,7 @@
 
 #include "dual.cuh"
 #include "gcb_internal.h"
+#include "adjoint_rev.cuh"
 #include "push_sr.cuh"
 
 namespace gcb {
@@ -243,13 +244,275 @@ __global__ void __launch_bounds__(TPB) k_adjoint_sr(const AdjArgs<T> a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// reverse mode: replay the step recording its gather points, then run the
+// transposed step backwards (adjoint_rev.cuh), re-gathering at each point.
+// ---------------------------------------------------------------------------
+
+// Plain gather that records where it was called (R^{n-1/2}, the iterates,
+// R^{n+1/2}, in that order).
 template <typename T>
-static gcb_status launch(const AdjArgs<T> &a, cudaStream_t st)
+struct RecGather {
+    DevGrid<T> g;
+    T (*pts)[2];
+    int *count;
+    __device__ __forceinline__ void operator()(const int ib[2], const T l[2], FieldPt<T, 2> &F) const
+    {
+        const int k = (*count)++;
+        if (k < MAXG) {
+            pts[k][0] = l[0];
+            pts[k][1] = l[1];
+        }
+        gather<T, 2, 2>(g, ib, l, F);
+    }
+};
+
+// Transpose of F = sum_o W_o(p) rec_o: node records receive W_o aF (FP64
+// atomics; components whose adjoint is zero are skipped) and the position
+// adjoint sum_o grad W_o (rec_o . aF) is returned.
+template <typename T>
+__device__ __forceinline__ void gather_bwd(const DevGrid<T> &g, double *grad, const int ib[2],
+                                           const T p[2], const FieldPt<T, 2> &aF, T ap[2])
+{
+    int i0[2], i1[2];
+    T t[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) cell_of(g, d, ib[d], p[d], t[d], i0[d], i1[d]);
+    T av[NF];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { av[c] = aF.E[c]; av[3 + c] = aF.B[c]; }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) av[6 + 3 * i + j] = aF.dB[i][j];
+    ap[0] = ap[1] = T(0);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const int ix = (o & 1) ? i1[0] : i0[0];
+        const int iy = (o & 2) ? i1[1] : i0[1];
+        const int node = iy * g.n[0] + ix;
+        const T wx = (o & 1) ? t[0] : T(1) - t[0];
+        const T wy = (o & 2) ? t[1] : T(1) - t[1];
+        const T dwx = (o & 1) ? g.inv_dx[0] : -g.inv_dx[0];
+        const T dwy = (o & 2) ? g.inv_dx[1] : -g.inv_dx[1];
+        const T *rp = g.rec + (size_t)node * g.stride;
+        T dv = T(0);
+#pragma unroll
+        for (int c = 0; c < NF; ++c) dv = fma(__ldg(rp + c), av[c], dv);
+        ap[0] = fma(dwx * wy, dv, ap[0]);
+        ap[1] = fma(wx * dwy, dv, ap[1]);
+        const T W = wx * wy;
+        double *gp = grad + (size_t)node * NF;
+#pragma unroll
+        for (int c = 0; c < NF; ++c)
+            if (av[c] != T(0)) atomicAdd(gp + c, (double)(W * av[c]));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void gather_frame(const DevGrid<T> &g, const int ib[2], const T p[2],
+                                             const StepPar<T> &s, FieldPt<T, 2> &F, Frame<T> &f)
+{
+    gather<T, 2, 2>(g, ib, p, F);
+    make_frame<T, 2, true>(F, s.c, s.inv_c2, f);
+}
+
+// frame adjoint at gather point p -> node records and position adjoint
+template <typename T>
+__device__ __forceinline__ void frame_gather_bwd(const DevGrid<T> &g, double *grad, const int ib[2],
+                                                 const T p[2], const FieldPt<T, 2> &F,
+                                                 const StepPar<T> &s, const rev::FrameAdj<T> &af,
+                                                 T ap[2])
+{
+    FieldPt<T, 2> aF;
+    rev::frame_bwd<T, 2>(F, s.c, s.inv_c2, af, aF);
+    gather_bwd(g, grad, ib, p, aF, ap);
+}
+
+// Reverse sweep of a guiding-center step taken with K iterations whose gather
+// points (R^{n-1/2}, x^n + d^1 .. x^n + d^{K-1}, R^{n+1/2}) are pts[0..K].
+template <typename T>
+__device__ __forceinline__ void gca_rev(const DevGrid<T> &g, double *grad, const StepPar<T> &s,
+                                        const int ib[2], const T l[2], const T u[3], int K,
+                                        const T (*pts)[2], const T lo[NS], T li[NS])
+{
+    using rev::FrameAdj;
+    FieldPt<T, 2> F0, F;
+    Frame<T> f0, f;
+    gather_frame(g, ib, l, s, F0, f0);
+    // conversion quantities (recomputed at R^{n-1/2})
+    gather_frame(g, ib, pts[0], s, F, f);
+    T Gf, upar, vcm[3], uperp, mu, bpg[3];
+    rev::conv_fwd(f, s, u, Gf, upar, vcm, uperp, mu, bpg);
+    // u_par^{n+1/2}
+    T upn;
+    {
+        if (!s.curvature) {
+            upn = fma(s.qm * s.dt, f0.Epar, upar);
+        } else {
+            const T A = dot3(f0.vE, f0.bgb);
+            const T gg = dot3(f0.vE, f0.vgb);
+            const T D = fma(-s.half_dt, A, T(1));
+            const T G0 = gamma_gc(f0, s, upar, mu, uperp);
+            const T upr = fma(upar, fma(s.half_dt, A, T(1)), fma(s.qm * s.dt, f0.Epar, s.half_dt * G0 * gg));
+            const T c2 = s.c * s.c;
+            const T kap2 = f0.kappa * f0.kappa;
+            const T k1 = T(0.25) * s.dt * s.dt * gg * gg - c2 * D * D / kap2;
+            const T k2 = upr * s.dt * gg;
+            const T k3 = fma(upr, upr, (c2 + perp2(f0, s, mu, uperp)) * D * D);
+            const T disc = fma(k2, k2, T(-4) * k1 * k3);
+            const T sq = sqrt(disc);
+            const T q = T(-0.5) * (k2 + (k2 >= T(0) ? sq : -sq));
+            const T r1 = q / k1;
+            const T r2 = (q != T(0)) ? k3 / q : T(-1);
+            const T G1 = r1 >= r2 ? r1 : r2;
+            upn = fma(s.half_dt * G1, gg, upr) / D;
+        }
+    }
+    T aupn = T(0), amu = T(0), auperp = T(0), abpg[3] = {T(0), T(0), T(0)};
+    T al[2], ad[2], ap[2];
+    // reconstruction at R^{n+1/2} = x^n + d^K/2
+    {
+        gather_frame(g, ib, pts[K], s, F, f);
+        FrameAdj<T> af;
+        af.zero();
+        const T lu[3] = {lo[2], lo[3], lo[4]};
+        rev::recon_bwd(f, s, upn, mu, uperp, bpg, lu, af, aupn, amu, auperp, abpg);
+        frame_gather_bwd(g, grad, ib, pts[K], F, s, af, ap);
+    }
+    // x^{n+1} = x^n + d^K, dxp = d^K
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+        al[d] = lo[d] + ap[d];
+        ad[d] = lo[d] + lo[5 + d] + T(0.5) * ap[d];
+    }
+    // iterates: d^k = dt/2 (V^n + V^{k-1}), V^0 = V^n
+    T aVn[3] = {T(0), T(0), T(0)};
+    for (int k = K; k >= 2; --k) {
+        T aV[3] = {s.half_dt * ad[0], s.half_dt * ad[1], T(0)};
+        aVn[0] += aV[0];
+        aVn[1] += aV[1];
+        gather_frame(g, ib, pts[k - 1], s, F, f);
+        FrameAdj<T> af;
+        af.zero();
+        rev::gc_vel_bwd(f, s, upn, mu, uperp, aV, af, aupn, amu, auperp);
+        frame_gather_bwd(g, grad, ib, pts[k - 1], F, s, af, ap);
+        al[0] += ap[0];
+        al[1] += ap[1];
+        ad[0] = ap[0];
+        ad[1] = ap[1];
+    }
+    aVn[0] += s.dt * ad[0];
+    aVn[1] += s.dt * ad[1];
+    // V^n at x^n, then the u_par update there
+    FrameAdj<T> af0;
+    af0.zero();
+    rev::gc_vel_bwd(f0, s, upn, mu, uperp, aVn, af0, aupn, amu, auperp);
+    T aupar = T(0);
+    rev::upar_bwd(f0, s, upar, mu, uperp, aupn, af0, aupar, amu, auperp);
+    // conversion at R^{n-1/2} = x^n - dxp/2
+    T au[3] = {T(0), T(0), T(0)};
+    {
+        gather_frame(g, ib, pts[0], s, F, f);
+        FrameAdj<T> afm;
+        afm.zero();
+        rev::conv_bwd(f, s, u, Gf, upar, vcm, uperp, mu, bpg, aupar, amu, auperp, abpg, afm, au);
+        frame_gather_bwd(g, grad, ib, pts[0], F, s, afm, ap);
+        al[0] += ap[0];
+        al[1] += ap[1];
+        li[5] = T(-0.5) * ap[0];
+        li[6] = T(-0.5) * ap[1];
+    }
+    frame_gather_bwd(g, grad, ib, l, F0, s, af0, ap);
+    li[0] = al[0] + ap[0];
+    li[1] = al[1] + ap[1];
+    li[2] = au[0];
+    li[3] = au[1];
+    li[4] = au[2];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_adjoint_rev(const AdjArgs<T> a)
+{
+    T pts[MAXG][2];
+    for (int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x; i < a.np;
+         i += (int64_t)gridDim.x * TPB) {
+        const uint8_t fl = a.flags[i];
+        bool fin = true;
+        int ib[2];
+        T l[2], u[3], dxp[2], lo[NS];
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            load_pos(a, i, d, ib[d], l[d], fin);
+            dxp[d] = a.dxp[d][i];
+            fin = fin && isfinite(dxp[d]);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { u[k] = a.u[k][i]; fin = fin && isfinite(u[k]); }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) lo[k] = a.lam[k][i];
+        if (!fin) continue;          // a frozen particle's step is the identity
+
+        StepPar<T> sp = a.sp;
+        sp.qm = a.qm[(fl >> GCB_SPECIES_SHIFT) & 3];
+        FieldPt<T, 2> F0;
+        gather<T, 2, 2>(a.g, ib, l, F0);
+        const T Q = fabs(sp.qm);
+        const T G = sqrt(T(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * sp.inv_c2);
+        const T Bm = sqrt(F0.B[0] * F0.B[0] + F0.B[1] * F0.B[1] + F0.B[2] * F0.B[2]);
+        const T Em = sqrt(F0.E[0] * F0.E[0] + F0.E[1] * F0.E[1] + F0.E[2] * F0.E[2]);
+        int S = (a.c2 * G < a.rho_thr * Q * Bm && Em < a.f_E * Bm) ? 0 : 1;
+        if (a.force == GCB_FORCE_BORIS) S = 1;
+        if (a.force == GCB_FORCE_GCA) S = 0;
+        int K = 0;
+        bool gca = false;
+        if (S == 0) {
+            T uu[3] = {u[0], u[1], u[2]}, disp[2];
+            bool ncv;
+            int cnt = 0;
+            gca = gca_step<T, 2, 2>(RecGather<T>{a.g, pts, &cnt}, sp, ib, l, dxp, F0, uu, disp, K, ncv);
+            gca = gca && cnt == K + 1 && cnt <= MAXG;
+        }
+        T li[NS];
+        if (gca) {
+            gca_rev(a.g, a.grad, sp, ib, l, u, K, pts, lo, li);
+        } else {
+            T lu[3] = {lo[2], lo[3], lo[4]};
+            T ldisp[2] = {lo[0] + lo[5], lo[1] + lo[6]};
+            T au[3], aE[3], aB[3];
+            rev::boris_bwd<T, 2>(F0.E, F0.B, sp, u, lu, ldisp, au, aE, aB);
+            FieldPt<T, 2> aF;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { aF.E[c] = aE[c]; aF.B[c] = aB[c]; }
+#pragma unroll
+            for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) aF.dB[ii][j] = T(0);
+            T ap[2];
+            gather_bwd(a.g, a.grad, ib, l, aF, ap);
+            li[0] = lo[0] + ap[0];
+            li[1] = lo[1] + ap[1];
+            li[2] = au[0];
+            li[3] = au[1];
+            li[4] = au[2];
+            li[5] = T(0);
+            li[6] = T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) a.lam[k][i] = li[k];
+    }
+}
+
+template <typename T>
+static gcb_status launch(const AdjArgs<T> &a, int method, cudaStream_t st)
 {
     if (a.np == 0) return GCB_OK;
     int64_t nb = (a.np + TPB - 1) / TPB;
     if (nb > 152 * 64) nb = 152 * 64;
-    k_adjoint_sr<T, NDIR><<<(int)nb, TPB, 0, st>>>(a);
+    if (method == GCB_ADJ_REVERSE)
+        k_adjoint_rev<T><<<(int)nb, TPB, 0, st>>>(a);
+    else
+        k_adjoint_sr<T, NDIR><<<(int)nb, TPB, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("k_adjoint_sr launch: %s", cudaGetErrorString(e));
@@ -262,7 +525,7 @@ static gcb_status launch(const AdjArgs<T> &a, cudaStream_t st)
 
 // The adjoint of one step for all particles whose pre-step state is `s`.
 gcb_status adjoint_step(const gcb_particles *s, const gcb_grid *g, const gcb_params *prm,
-                        void *const lam[7], double *grad, cudaStream_t st)
+                        void *const lam[7], double *grad, int method, cudaStream_t st)
 {
     auto fill = [&](auto &a, auto tag) {
         using T = decltype(tag);
@@ -304,11 +567,11 @@ gcb_status adjoint_step(const gcb_particles *s, const gcb_grid *g, const gcb_par
     if (s->mom_dtype == GCB_F64) {
         adj::AdjArgs<double> a;
         fill(a, 0.0);
-        return adj::launch(a, st);
+        return adj::launch(a, method, st);
     }
     adj::AdjArgs<float> a;
     fill(a, 0.0f);
-    return adj::launch(a, st);
+    return adj::launch(a, method, st);
 }
 
 }  // namespace gcb

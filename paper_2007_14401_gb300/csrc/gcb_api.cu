@@ -492,8 +492,8 @@ size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, in
 }
 
 gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_params *prm0,
-                          int n_steps, int ckpt_every, void *const *lam, double *grad_rec,
-                          void *cuda_stream, void *ws, size_t ws_bytes)
+                          int n_steps, int ckpt_every, int method, void *const *lam,
+                          double *grad_rec, void *cuda_stream, void *ws, size_t ws_bytes)
 {
     g_err[0] = 0;
     gcb_status s = check_problem(p0, g, prm0);
@@ -503,6 +503,7 @@ gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_
         return GCB_EUNSUPPORTED;
     }
     if (n_steps < 1 || ckpt_every < 1) { set_error("n_steps and ckpt_every must be >= 1"); return GCB_EINVAL; }
+    if (method != GCB_ADJ_REVERSE && method != GCB_ADJ_TANGENT) { set_error("unknown adjoint method %d", method); return GCB_EINVAL; }
     if (prm0->gca_max_iter > GCB_ADJOINT_MAX_ITER || prm0->gca_fixed_iters > GCB_ADJOINT_MAX_ITER) {
         set_error("the adjoint records at most %d fixed-point iterations per step", GCB_ADJOINT_MAX_ITER);
         return GCB_EUNSUPPORTED;
@@ -558,7 +559,7 @@ gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_
             if ((s = step(&states[j], &states[j - 1])) != GCB_OK) return s;
         }
         for (int j = len - 1; j >= 0; --j)
-            if ((s = adjoint_step(&states[j], g, &prm, lam, grad_rec, st)) != GCB_OK) return s;
+            if ((s = adjoint_step(&states[j], g, &prm, lam, grad_rec, method, st)) != GCB_OK) return s;
     }
     return GCB_OK;
 }

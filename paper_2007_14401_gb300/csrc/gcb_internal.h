@@ -30,7 +30,7 @@ gcb_status push_step_f32(const gcb_particles *p, const gcb_particles *in, const 
 // pre-step state is `s`; lam[7] (x0 x1 u0 u1 u2 dxp0 dxp1) is updated in
 // place, node-record adjoints are added to grad (12 doubles per node).
 gcb_status adjoint_step(const gcb_particles *s, const gcb_grid *g, const gcb_params *prm,
-                        void *const lam[7], double *grad, cudaStream_t st);
+                        void *const lam[7], double *grad, int method, cudaStream_t st);
 gcb_status grad_project(const gcb_grid *g, const double *grad, const void *pat, int nmodes,
                         double *out, cudaStream_t st);
 gcb_status grid_combine(const gcb_grid *g, const void *base, const void *pat, const double *amps,

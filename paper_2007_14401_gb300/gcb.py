@@ -102,7 +102,8 @@ def load_library(path: str | None = None):
     lib.gcb_adjoint_workspace_bytes.argtypes = [P(GcbParticles), P(GcbGrid), C.c_int, C.c_int]
     lib.gcb_adjoint_workspace_bytes.restype = C.c_size_t
     lib.gcb_adjoint_sr.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int, C.c_int,
-                                   P(C.c_void_p), C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t]
+                                   C.c_int, P(C.c_void_p), C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_size_t]
     lib.gcb_adjoint_sr.restype = C.c_int
     lib.gcb_grid_combine.argtypes = [P(GcbGrid), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                      C.c_void_p]
@@ -362,12 +363,16 @@ def push(state: State, grid: Grid, params: GcbParams, n_steps: int = 1, stream=N
 LAM_ORDER = ("x0", "x1", "u0", "u1", "u2", "dxp0", "dxp1")
 
 
+ADJ_METHODS = {"reverse": 0, "tangent": 1}
+
+
 def adjoint(state: State, grid: Grid, params: GcbParams, n_steps: int, lam: torch.Tensor,
-            ckpt_every: int = 16, stream=None) -> torch.Tensor:
+            ckpt_every: int = 16, stream=None, method: str = "reverse") -> torch.Tensor:
     """Reverse sweep of n_steps pushes from the initial ``state`` (left
     unchanged).  ``lam`` (7, n) in the momentum dtype holds dL/d(final x0, x1,
     u0, u1, u2, dxp0, dxp1) and is overwritten with dL/d(initial state).
-    Returns dL/d(record values) as a float64 tensor (nodes, 12)."""
+    Returns dL/d(record values) as a float64 tensor (nodes, 12).  method
+    "reverse" (default) or "tangent" (dual-number Jacobian columns, slower)."""
     nb = _lib.gcb_adjoint_workspace_bytes(C.byref(state.s), C.byref(grid.s), int(n_steps),
                                           int(ckpt_every))
     if nb == 0:
@@ -379,7 +384,8 @@ def adjoint(state: State, grid: Grid, params: GcbParams, n_steps: int, lam: torc
         raise GcbError("lam must be a contiguous (7, n) tensor of the momentum dtype")
     ptrs = (C.c_void_p * 7)(*[lam[k].data_ptr() for k in range(7)])
     rc = _lib.gcb_adjoint_sr(C.byref(state.s), C.byref(grid.s), C.byref(params), int(n_steps),
-                             int(ckpt_every), ptrs, C.c_void_p(grad.data_ptr()),
+                             int(ckpt_every), ADJ_METHODS[method], ptrs,
+                             C.c_void_p(grad.data_ptr()),
                              _stream_ptr(stream), C.c_void_p(ws.data_ptr()), nb)
     _check(rc, "gcb_adjoint_sr")
     return grad
@@ -435,7 +441,7 @@ class ModePush(torch.autograd.Function):
         if gdxp is not None:
             lam[5:7] = gdxp.to(lam.dtype)
         grad = adjoint(st, cfg["grid"], cfg["params"], cfg["n_steps"], lam,
-                       cfg.get("ckpt_every", 16))
+                       cfg.get("ckpt_every", 16), method=cfg.get("method", "reverse"))
         ga = grad_project(cfg["grid"], grad, cfg["pat"])
         return lam[0:2].to(torch.float64), lam[2:5].clone(), lam[5:7].clone(), ga, None
 

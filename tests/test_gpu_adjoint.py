@@ -115,7 +115,7 @@ def rel_err(got, ref, scale):
     return np.maximum(np.abs(got - ref) - FD_FLOOR, 0.0) / (np.abs(ref) + scale)
 
 
-def run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5):
+def run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5, method="reverse"):
     """Forward + adjoint through ModePush; returns (state grads (7, n), mode grads)."""
     import torch
     base, pats, amps, st0, params, w = case
@@ -131,7 +131,7 @@ def run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5):
     cfg = dict(grid=grid, base=base_rec, pat=pat_rec,
                params=G.make_params(params, **FIXED), n_steps=N_STEPS, ckpt_every=ckpt_every,
                flags=torch.tensor(st0["flags"], device=dev), precision=precision,
-               pos_mode=pos_mode)
+               pos_mode=pos_mode, method=method)
     x, u, dxp = G.ModePush.apply(x0, u0, d0, a, cfg)
     n = u.shape[1]
     Gm = torch.sqrt(1.0 + (u.double() ** 2).sum(0))
@@ -169,8 +169,20 @@ def test_branch_mix(G, case):
     assert 0.1 * tot < s["n_gca"] < 0.9 * tot, s
 
 
-def test_adjoint_fp64_matches_oracle_fd(G, case, fd):
-    compare(run_gpu(G, case, "fp64", "f64", "f64"), fd, 1e-6, 0.97)
+@pytest.mark.parametrize("method", ["reverse", "tangent"])
+def test_adjoint_fp64_matches_oracle_fd(G, case, fd, method):
+    compare(run_gpu(G, case, "fp64", "f64", "f64", method=method), fd, 1e-6, 0.97)
+
+
+def test_reverse_and_tangent_agree(G, case):
+    """Two constructions of the same transposed step (written-out reverse
+    sweep; dual-number Jacobian columns): equal to FP64 rounding."""
+    r = run_gpu(G, case, "fp64", "f64", "f64", method="reverse")
+    t = run_gpu(G, case, "fp64", "f64", "f64", method="tangent")
+    for k in range(7):
+        sc = np.abs(t[0][k]).max()
+        np.testing.assert_allclose(r[0][k], t[0][k], rtol=0, atol=1e-11 * sc)
+    np.testing.assert_allclose(r[1], t[1], rtol=1e-10, atol=0)
 
 
 def test_adjoint_checkpoint_interval_invariance(G, case):
@@ -183,10 +195,11 @@ def test_adjoint_checkpoint_interval_invariance(G, case):
         np.testing.assert_allclose(got[1], ref[1], rtol=1e-12, atol=1e-14)
 
 
-def test_adjoint_mixed_close_to_fp64(G, case, fd):
+@pytest.mark.parametrize("method", ["reverse", "tangent"])
+def test_adjoint_mixed_close_to_fp64(G, case, fd, method):
     """FP32 forward + FP32 adjoint (FP32-pair positions, FP32 records) against
     the oracle's FP64 differences: FP32 tangent arithmetic."""
-    compare(run_gpu(G, case, "mixed", "pair", "f32"), fd, 2e-2, 0.97)
+    compare(run_gpu(G, case, "mixed", "pair", "f32", method=method), fd, 2e-2, 0.97)
 
 
 def test_grid_combine_and_project(G, case):
