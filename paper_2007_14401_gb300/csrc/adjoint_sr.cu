@@ -22,6 +22,33 @@
 #include "adjoint_rev.cuh"
 #include "push_sr.cuh"
 
+// Code size of the reverse kernel: its per-point pieces (gather + frame,
+// frame transpose + scatter, and at level 2 the guiding-center velocity
+// transpose and the replay's gather) are called out of line instead of being
+// inlined at every gather point, which keeps the kernel's instruction
+// footprint within the instruction caches.
+#ifndef GCB_ADJ_OUTLINE
+#define GCB_ADJ_OUTLINE 0
+#endif
+// GCB_ADJ_CACHE: accumulate a particle-step's node adjoints per thread in
+// shared memory (1) or add every gather's contributions directly (0).
+#ifndef GCB_ADJ_CACHE
+#define GCB_ADJ_CACHE 1
+#endif
+#ifndef GCB_ADJ_BLOCKS_F32
+#define GCB_ADJ_BLOCKS_F32 4
+#endif
+#if GCB_ADJ_OUTLINE >= 1
+#define GCB_ADJ_FN1 __device__ __noinline__
+#else
+#define GCB_ADJ_FN1 __device__ __forceinline__
+#endif
+#if GCB_ADJ_OUTLINE >= 2
+#define GCB_ADJ_FN2 __device__ __noinline__
+#else
+#define GCB_ADJ_FN2 __device__ __forceinline__
+#endif
+
 namespace gcb {
 namespace adj {
 
@@ -249,6 +276,12 @@ __global__ void __launch_bounds__(TPB) k_adjoint_sr(const AdjArgs<T> a)
 // transposed step backwards (adjoint_rev.cuh), re-gathering at each point.
 // ---------------------------------------------------------------------------
 
+template <typename T>
+GCB_ADJ_FN2 void plain_gather2(const DevGrid<T> &g, const int ib[2], const T l[2], FieldPt<T, 2> &F)
+{
+    gather<T, 2, 2>(g, ib, l, F);
+}
+
 // Plain gather that records where it was called (R^{n-1/2}, the iterates,
 // R^{n+1/2}, in that order).
 template <typename T>
@@ -263,15 +296,77 @@ struct RecGather {
             pts[k][0] = l[0];
             pts[k][1] = l[1];
         }
-        gather<T, 2, 2>(g, ib, l, F);
+        plain_gather2(g, ib, l, F);
     }
 };
 
-// Transpose of F = sum_o W_o(p) rec_o: node records receive W_o aF (FP64
-// atomics; components whose adjoint is zero are skipped) and the position
-// adjoint sum_o grad W_o (rec_o . aF) is returned.
+// Node-record adjoints of one particle-step, accumulated per thread for up
+// to two cells (4 nodes x 12 components each) in shared memory laid out
+// thread-fastest, and added to the FP64 node accumulators when a cell is
+// evicted and at the end of the step: the step's gathers (x^n, R^{n-1/2},
+// the iterates, R^{n+1/2}) mostly share one or two cells, so this replaces
+// most of the per-gather atomics.
 template <typename T>
-__device__ __forceinline__ void gather_bwd(const DevGrid<T> &g, double *grad, const int ib[2],
+struct NodeCache {
+    T *acc;          // this thread's slot 0 element; element (s, o, c) at acc[((s*4+o)*NF+c)*TPB]
+    double *grad;
+    int nx, ny;
+    int key[2];      // lower-left node of the cached cell, -1 when empty
+    int mru;         // most recently used slot
+
+    __device__ __forceinline__ T &at(int sl, int o, int c) const
+    {
+        return acc[((sl * 4 + o) * NF + c) * TPB];
+    }
+    __device__ __forceinline__ void flush(int sl)
+    {
+        const int k = sl ? key[1] : key[0];
+        if (k < 0) return;
+        const int ix = k % nx, iy = k / nx;
+        const int jx = ix + 1 == nx ? 0 : ix + 1, jy = iy + 1 == ny ? 0 : iy + 1;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const int node = ((o & 2) ? jy : iy) * nx + ((o & 1) ? jx : ix);
+            double *gp = grad + (size_t)node * NF;
+#pragma unroll
+            for (int c = 0; c < NF; ++c) {
+                const T v = at(sl, o, c);
+                if (v != T(0)) atomicAdd(gp + c, (double)v);
+            }
+        }
+    }
+    // slot holding cell `k` (evicting the least recently used one if needed)
+    __device__ __forceinline__ int slot(int k)
+    {
+        int sl;
+        if (k == key[0]) {
+            sl = 0;
+        } else if (k == key[1]) {
+            sl = 1;
+        } else {
+            sl = 1 - mru;
+            flush(sl);
+            if (sl) key[1] = k; else key[0] = k;
+#pragma unroll
+            for (int o = 0; o < 4; ++o)
+#pragma unroll
+                for (int c = 0; c < NF; ++c) at(sl, o, c) = T(0);
+        }
+        mru = sl;
+        return sl;
+    }
+    __device__ __forceinline__ void finish()
+    {
+        flush(0);
+        flush(1);
+        key[0] = key[1] = -1;
+    }
+};
+
+// Transpose of F = sum_o W_o(p) rec_o: the node records receive W_o aF (via
+// the cache) and the position adjoint sum_o grad W_o (rec_o . aF) is returned.
+template <typename T>
+__device__ __forceinline__ void gather_bwd(const DevGrid<T> &g, NodeCache<T> &nc, const int ib[2],
                                            const T p[2], const FieldPt<T, 2> &aF, T ap[2])
 {
     int i0[2], i1[2];
@@ -285,6 +380,9 @@ __device__ __forceinline__ void gather_bwd(const DevGrid<T> &g, double *grad, co
     for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) av[6 + 3 * i + j] = aF.dB[i][j];
+#if GCB_ADJ_CACHE
+    const int sl = nc.slot(i0[1] * g.n[0] + i0[0]);
+#endif
     ap[0] = ap[1] = T(0);
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
@@ -302,15 +400,20 @@ __device__ __forceinline__ void gather_bwd(const DevGrid<T> &g, double *grad, co
         ap[0] = fma(dwx * wy, dv, ap[0]);
         ap[1] = fma(wx * dwy, dv, ap[1]);
         const T W = wx * wy;
-        double *gp = grad + (size_t)node * NF;
+#if GCB_ADJ_CACHE
+#pragma unroll
+        for (int c = 0; c < NF; ++c) nc.at(sl, o, c) = fma(W, av[c], nc.at(sl, o, c));
+#else
+        double *gp = nc.grad + (size_t)node * NF;
 #pragma unroll
         for (int c = 0; c < NF; ++c)
             if (av[c] != T(0)) atomicAdd(gp + c, (double)(W * av[c]));
+#endif
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void gather_frame(const DevGrid<T> &g, const int ib[2], const T p[2],
+GCB_ADJ_FN1 void gather_frame(const DevGrid<T> &g, const int ib[2], const T p[2],
                                              const StepPar<T> &s, FieldPt<T, 2> &F, Frame<T> &f)
 {
     gather<T, 2, 2>(g, ib, p, F);
@@ -319,7 +422,7 @@ __device__ __forceinline__ void gather_frame(const DevGrid<T> &g, const int ib[2
 
 // frame adjoint at gather point p -> node records and position adjoint
 template <typename T>
-__device__ __forceinline__ void frame_gather_bwd(const DevGrid<T> &g, double *grad, const int ib[2],
+GCB_ADJ_FN1 void frame_gather_bwd(const DevGrid<T> &g, NodeCache<T> &grad, const int ib[2],
                                                  const T p[2], const FieldPt<T, 2> &F,
                                                  const StepPar<T> &s, const rev::FrameAdj<T> &af,
                                                  T ap[2])
@@ -332,109 +435,130 @@ __device__ __forceinline__ void frame_gather_bwd(const DevGrid<T> &g, double *gr
 // Reverse sweep of a guiding-center step taken with K iterations whose gather
 // points (R^{n-1/2}, x^n + d^1 .. x^n + d^{K-1}, R^{n+1/2}) are pts[0..K].
 template <typename T>
-__device__ __forceinline__ void gca_rev(const DevGrid<T> &g, double *grad, const StepPar<T> &s,
+GCB_ADJ_FN2 void vel_bwd(const Frame<T> &f, const StepPar<T> &s, T upn, T mu, T uperp,
+                         const T aV[3], rev::FrameAdj<T> &af, T &aupn, T &amu, T &auperp)
+{
+    rev::gc_vel_bwd(f, s, upn, mu, uperp, aV, af, aupn, amu, auperp);
+}
+
+// u_par^{n+1/2} from the frame at x^n (the forward update of Sec. 2.2.1 / 2.2.2)
+template <typename T>
+__device__ __forceinline__ T upar_new(const Frame<T> &f0, const StepPar<T> &s, T upar, T mu, T uperp)
+{
+    if (!s.curvature) return fma(s.qm * s.dt, f0.Epar, upar);
+    const T A = dot3(f0.vE, f0.bgb);
+    const T gg = dot3(f0.vE, f0.vgb);
+    const T D = fma(-s.half_dt, A, T(1));
+    const T G0 = gamma_gc(f0, s, upar, mu, uperp);
+    const T upr = fma(upar, fma(s.half_dt, A, T(1)), fma(s.qm * s.dt, f0.Epar, s.half_dt * G0 * gg));
+    const T c2 = s.c * s.c;
+    const T kap2 = f0.kappa * f0.kappa;
+    const T k1 = T(0.25) * s.dt * s.dt * gg * gg - c2 * D * D / kap2;
+    const T k2 = upr * s.dt * gg;
+    const T k3 = fma(upr, upr, (c2 + perp2(f0, s, mu, uperp)) * D * D);
+    const T disc = fma(k2, k2, T(-4) * k1 * k3);
+    const T sq = sqrt(disc);
+    const T q = T(-0.5) * (k2 + (k2 >= T(0) ? sq : -sq));
+    const T r1 = q / k1;
+    const T r2 = (q != T(0)) ? k3 / q : T(-1);
+    const T G1 = r1 >= r2 ? r1 : r2;
+    return fma(s.half_dt * G1, gg, upr) / D;
+}
+
+// Reverse sweep of a guiding-center step taken with K iterations whose gather
+// points (R^{n-1/2}, x^n + d^1 .. x^n + d^{K-1}, R^{n+1/2}) are pts[0..K].
+// One loop over the step's gather points in reverse order of their use:
+//   stage 0        R^{n+1/2}: reconstruction of u
+//   stage 1..K-1   x^n + d^{K-stage}: the iterate's velocity V^{K-stage}
+//   stage K        x^n: V^n and the u_par update
+//   stage K+1      R^{n-1/2}: conversion of u
+// so that the gather, frame and scatter code is present once.
+template <typename T>
+__device__ __forceinline__ void gca_rev(const DevGrid<T> &g, NodeCache<T> &grad, const StepPar<T> &s,
                                         const int ib[2], const T l[2], const T u[3], int K,
                                         const T (*pts)[2], const T lo[NS], T li[NS])
 {
     using rev::FrameAdj;
-    FieldPt<T, 2> F0, F;
-    Frame<T> f0, f;
-    gather_frame(g, ib, l, s, F0, f0);
-    // conversion quantities (recomputed at R^{n-1/2})
-    gather_frame(g, ib, pts[0], s, F, f);
-    T Gf, upar, vcm[3], uperp, mu, bpg[3];
-    rev::conv_fwd(f, s, u, Gf, upar, vcm, uperp, mu, bpg);
-    // u_par^{n+1/2}
-    T upn;
-    {
-        if (!s.curvature) {
-            upn = fma(s.qm * s.dt, f0.Epar, upar);
+    FieldPt<T, 2> F;
+    Frame<T> f;
+    // forward quantities of the conversion (at R^{n-1/2}) and of the u_par update (at x^n)
+    T Gf, upar, vcm[3], uperp, mu, bpg[3], upn;
+    for (int j = 0; j < 2; ++j) {
+        gather_frame(g, ib, j == 0 ? pts[0] : l, s, F, f);
+        if (j == 0) rev::conv_fwd(f, s, u, Gf, upar, vcm, uperp, mu, bpg);
+        else upn = upar_new(f, s, upar, mu, uperp);
+    }
+    T aupn = T(0), amu = T(0), auperp = T(0), aupar = T(0);
+    T abpg[3] = {T(0), T(0), T(0)}, au[3] = {T(0), T(0), T(0)};
+    T al[2] = {lo[0], lo[1]};
+    T ad[2] = {lo[0] + lo[5], lo[1] + lo[6]};      // x^{n+1} = x^n + d^K, dxp = d^K
+    T aVn[3] = {T(0), T(0), T(0)};
+    for (int st = 0; st <= K + 1; ++st) {
+        const T *p = st == 0 ? pts[K] : (st < K ? pts[K - st] : (st == K ? l : pts[0]));
+        gather_frame(g, ib, p, s, F, f);
+        FrameAdj<T> af;
+        af.zero();
+        if (st == 0) {
+            const T lu[3] = {lo[2], lo[3], lo[4]};
+            rev::recon_bwd(f, s, upn, mu, uperp, bpg, lu, af, aupn, amu, auperp, abpg);
+        } else if (st <= K) {
+            // d^k = dt/2 (V^n + V^{k-1}) with V^0 = V^n: stage st < K carries
+            // V^{K-st}; stage K carries V^n with every term collected
+            T aV[3];
+            if (st < K) {
+                aV[0] = s.half_dt * ad[0];
+                aV[1] = s.half_dt * ad[1];
+                aVn[0] += aV[0];
+                aVn[1] += aV[1];
+            } else {
+                aV[0] = aVn[0] + s.dt * ad[0];
+                aV[1] = aVn[1] + s.dt * ad[1];
+            }
+            aV[2] = T(0);
+            vel_bwd(f, s, upn, mu, uperp, aV, af, aupn, amu, auperp);
+            if (st == K) rev::upar_bwd(f, s, upar, mu, uperp, aupn, af, aupar, amu, auperp);
         } else {
-            const T A = dot3(f0.vE, f0.bgb);
-            const T gg = dot3(f0.vE, f0.vgb);
-            const T D = fma(-s.half_dt, A, T(1));
-            const T G0 = gamma_gc(f0, s, upar, mu, uperp);
-            const T upr = fma(upar, fma(s.half_dt, A, T(1)), fma(s.qm * s.dt, f0.Epar, s.half_dt * G0 * gg));
-            const T c2 = s.c * s.c;
-            const T kap2 = f0.kappa * f0.kappa;
-            const T k1 = T(0.25) * s.dt * s.dt * gg * gg - c2 * D * D / kap2;
-            const T k2 = upr * s.dt * gg;
-            const T k3 = fma(upr, upr, (c2 + perp2(f0, s, mu, uperp)) * D * D);
-            const T disc = fma(k2, k2, T(-4) * k1 * k3);
-            const T sq = sqrt(disc);
-            const T q = T(-0.5) * (k2 + (k2 >= T(0) ? sq : -sq));
-            const T r1 = q / k1;
-            const T r2 = (q != T(0)) ? k3 / q : T(-1);
-            const T G1 = r1 >= r2 ? r1 : r2;
-            upn = fma(s.half_dt * G1, gg, upr) / D;
+            rev::conv_bwd(f, s, u, Gf, upar, vcm, uperp, mu, bpg, aupar, amu, auperp, abpg, af, au);
+        }
+        T ap[2];
+        frame_gather_bwd(g, grad, ib, p, F, s, af, ap);
+        al[0] += ap[0];
+        al[1] += ap[1];
+        if (st == 0) {                 // R^{n+1/2} = x^n + d^K / 2
+            ad[0] += T(0.5) * ap[0];
+            ad[1] += T(0.5) * ap[1];
+        } else if (st < K) {           // x^n + d^{K-st}
+            ad[0] = ap[0];
+            ad[1] = ap[1];
+        } else if (st == K + 1) {      // R^{n-1/2} = x^n - dxp / 2
+            li[5] = T(-0.5) * ap[0];
+            li[6] = T(-0.5) * ap[1];
         }
     }
-    T aupn = T(0), amu = T(0), auperp = T(0), abpg[3] = {T(0), T(0), T(0)};
-    T al[2], ad[2], ap[2];
-    // reconstruction at R^{n+1/2} = x^n + d^K/2
-    {
-        gather_frame(g, ib, pts[K], s, F, f);
-        FrameAdj<T> af;
-        af.zero();
-        const T lu[3] = {lo[2], lo[3], lo[4]};
-        rev::recon_bwd(f, s, upn, mu, uperp, bpg, lu, af, aupn, amu, auperp, abpg);
-        frame_gather_bwd(g, grad, ib, pts[K], F, s, af, ap);
-    }
-    // x^{n+1} = x^n + d^K, dxp = d^K
-#pragma unroll
-    for (int d = 0; d < 2; ++d) {
-        al[d] = lo[d] + ap[d];
-        ad[d] = lo[d] + lo[5 + d] + T(0.5) * ap[d];
-    }
-    // iterates: d^k = dt/2 (V^n + V^{k-1}), V^0 = V^n
-    T aVn[3] = {T(0), T(0), T(0)};
-    for (int k = K; k >= 2; --k) {
-        T aV[3] = {s.half_dt * ad[0], s.half_dt * ad[1], T(0)};
-        aVn[0] += aV[0];
-        aVn[1] += aV[1];
-        gather_frame(g, ib, pts[k - 1], s, F, f);
-        FrameAdj<T> af;
-        af.zero();
-        rev::gc_vel_bwd(f, s, upn, mu, uperp, aV, af, aupn, amu, auperp);
-        frame_gather_bwd(g, grad, ib, pts[k - 1], F, s, af, ap);
-        al[0] += ap[0];
-        al[1] += ap[1];
-        ad[0] = ap[0];
-        ad[1] = ap[1];
-    }
-    aVn[0] += s.dt * ad[0];
-    aVn[1] += s.dt * ad[1];
-    // V^n at x^n, then the u_par update there
-    FrameAdj<T> af0;
-    af0.zero();
-    rev::gc_vel_bwd(f0, s, upn, mu, uperp, aVn, af0, aupn, amu, auperp);
-    T aupar = T(0);
-    rev::upar_bwd(f0, s, upar, mu, uperp, aupn, af0, aupar, amu, auperp);
-    // conversion at R^{n-1/2} = x^n - dxp/2
-    T au[3] = {T(0), T(0), T(0)};
-    {
-        gather_frame(g, ib, pts[0], s, F, f);
-        FrameAdj<T> afm;
-        afm.zero();
-        rev::conv_bwd(f, s, u, Gf, upar, vcm, uperp, mu, bpg, aupar, amu, auperp, abpg, afm, au);
-        frame_gather_bwd(g, grad, ib, pts[0], F, s, afm, ap);
-        al[0] += ap[0];
-        al[1] += ap[1];
-        li[5] = T(-0.5) * ap[0];
-        li[6] = T(-0.5) * ap[1];
-    }
-    frame_gather_bwd(g, grad, ib, l, F0, s, af0, ap);
-    li[0] = al[0] + ap[0];
-    li[1] = al[1] + ap[1];
+    li[0] = al[0];
+    li[1] = al[1];
     li[2] = au[0];
     li[3] = au[1];
     li[4] = au[2];
 }
 
+// resident blocks per SM the reverse kernel is compiled for (FP32: 4, i.e.
+// at most 128 registers; FP64 kernels need more registers than that allows)
+template <typename T> struct RevBlocks { static constexpr int n = GCB_ADJ_BLOCKS_F32; };
+template <> struct RevBlocks<double> { static constexpr int n = 1; };
+
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_adjoint_rev(const AdjArgs<T> a)
+__global__ void __launch_bounds__(TPB, RevBlocks<T>::n) k_adjoint_rev(const AdjArgs<T> a)
 {
+    extern __shared__ __align__(16) unsigned char s_raw[];
     T pts[MAXG][2];
+    NodeCache<T> nc;
+    nc.acc = reinterpret_cast<T *>(s_raw) + threadIdx.x;
+    nc.grad = a.grad;
+    nc.nx = a.g.n[0];
+    nc.ny = a.g.n[1];
+    nc.key[0] = nc.key[1] = -1;
+    nc.mru = 1;
     for (int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x; i < a.np;
          i += (int64_t)gridDim.x * TPB) {
         const uint8_t fl = a.flags[i];
@@ -475,7 +599,7 @@ __global__ void __launch_bounds__(TPB) k_adjoint_rev(const AdjArgs<T> a)
         }
         T li[NS];
         if (gca) {
-            gca_rev(a.g, a.grad, sp, ib, l, u, K, pts, lo, li);
+            gca_rev(a.g, nc, sp, ib, l, u, K, pts, lo, li);
         } else {
             T lu[3] = {lo[2], lo[3], lo[4]};
             T ldisp[2] = {lo[0] + lo[5], lo[1] + lo[6]};
@@ -489,7 +613,7 @@ __global__ void __launch_bounds__(TPB) k_adjoint_rev(const AdjArgs<T> a)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) aF.dB[ii][j] = T(0);
             T ap[2];
-            gather_bwd(a.g, a.grad, ib, l, aF, ap);
+            gather_bwd(a.g, nc, ib, l, aF, ap);
             li[0] = lo[0] + ap[0];
             li[1] = lo[1] + ap[1];
             li[2] = au[0];
@@ -498,10 +622,16 @@ __global__ void __launch_bounds__(TPB) k_adjoint_rev(const AdjArgs<T> a)
             li[5] = T(0);
             li[6] = T(0);
         }
+#if GCB_ADJ_CACHE
+        nc.finish();
+#endif
 #pragma unroll
         for (int k = 0; k < NS; ++k) a.lam[k][i] = li[k];
     }
 }
+
+template <typename T>
+constexpr int rev_smem() { return GCB_ADJ_CACHE ? 2 * 4 * NF * TPB * (int)sizeof(T) : 0; }
 
 template <typename T>
 static gcb_status launch(const AdjArgs<T> &a, int method, cudaStream_t st)
@@ -509,8 +639,16 @@ static gcb_status launch(const AdjArgs<T> &a, int method, cudaStream_t st)
     if (a.np == 0) return GCB_OK;
     int64_t nb = (a.np + TPB - 1) / TPB;
     if (nb > 152 * 64) nb = 152 * 64;
-    if (method == GCB_ADJ_REVERSE)
-        k_adjoint_rev<T><<<(int)nb, TPB, 0, st>>>(a);
+    if (method == GCB_ADJ_REVERSE) {
+        cudaError_t e = cudaFuncSetAttribute(k_adjoint_rev<T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             rev_smem<T>());
+        if (e != cudaSuccess) {
+            set_error("k_adjoint_rev smem attribute: %s", cudaGetErrorString(e));
+            return GCB_ECUDA;
+        }
+        k_adjoint_rev<T><<<(int)nb, TPB, rev_smem<T>(), st>>>(a);
+    }
     else
         k_adjoint_sr<T, NDIR><<<(int)nb, TPB, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
