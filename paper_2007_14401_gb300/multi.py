@@ -1,0 +1,44 @@
+"""Multi-rank bookkeeping: one process per GPU, particles sharded by rank.
+
+Test particles in static fields do not interact, so the push exchanges
+nothing between ranks.  What crosses ranks is bookkeeping: the step time (the
+whole job is as slow as its slowest rank: max), the particle count (sum),
+and, after an adjoint sweep, the gradients with respect to shared inputs such
+as the field-mode amplitudes (sum).  Each function is a no-op reduction when
+no process group is initialised.
+"""
+from __future__ import annotations
+
+import torch
+import torch.distributed as dist
+
+
+def _group_size() -> int:
+    if dist.is_available() and dist.is_initialized():
+        return dist.get_world_size()
+    return 1
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of rank's synthetic particles (distinct per rank, 1 on rank 0)."""
+    return 1 + int(rank)
+
+
+def whole_job_rate(n_local: int, steps: int, ms_local: float, device="cpu"):
+    """Units processed by all ranks per second over the slowest rank's time.
+    Returns (rate, max ms, total units)."""
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(n_local)], dtype=torch.float64, device=device)
+    if _group_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    total = int(round(n.item()))
+    return total * steps / (ms * 1e-3), ms, total
+
+
+def sum_over_ranks(x: torch.Tensor) -> torch.Tensor:
+    """In-place sum over ranks (e.g. dL/da_m of each rank's particles)."""
+    if _group_size() > 1:
+        dist.all_reduce(x, op=dist.ReduceOp.SUM)
+    return x
