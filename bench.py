@@ -67,7 +67,11 @@ WORKLOADS = {
         desc="2D double Harris + GEM + 64 modes, 2048x1024 grid, {n} particles, mixed FP32 "
              "(FP32-pair positions)",
         extra=dict(grid=[2048, 1024], dt=0.45, omega_c_dt_max=1e5, curvature=1,
-                   grad_mode="grid", gca_tol=1e-7)),
+                   grad_mode="grid", gca_tol=1e-7),
+        # DRAM bytes (read + write) of one push launch at 2^24 particles, from
+        # an ncu capture of this kernel (1 pass: dram__bytes_read.sum +
+        # dram__bytes_write.sum = 722.54 MB + 562.97 MB)
+        traffic_b=1285.51e6),
     "harris2d_fp64": dict(
         gen=_gen_harris, n=16384, precision="fp64", grid="f64", sort_every=0, tile=(1, 1),
         state_b=57, field_b=128 * 128 * 48, fp64_b=None,
@@ -78,7 +82,13 @@ WORKLOADS = {
         state_b=49, field_b=512 * 512 * 32, fp64_b=None,
         desc="Kerr-Schild a=0.9, Wald field + split monopole, 512x512 (log r, theta) grid, "
              "{n} electrons, |q/m| = 1e3, FP32 field records, FP64 metric and state",
-        extra=dict(grid=[512, 512], dt=0.02, spin=0.9)),
+        extra=dict(grid=[512, 512], dt=0.02, spin=0.9),
+        # FP64-issue bound: FP64 flops per particle-step as executed (2 DFMA
+        # + DMUL + DADD, ncu thread-instruction counts of this kernel at 2^18
+        # particles) against the FP64 FMA peak 152 SMs x 2 DFMA/clk x 2 flops
+        # x 2.07 GHz = 1.2586 TFLOP/s
+        alu=dict(flops=2948.0, peak=1.2586, peak_source="derived: 152 SMs x 2 DFMA/clk "
+                 "x 2 flop x 2.07 GHz (ncu peak_sustained dfma 304 inst/clk)")),
     "sheet3d": dict(
         gen=_gen_sheet3d, n=1 << 26, precision="mixed", grid="f32", sort_every=8,
         tile=(1, 1, 1), state_b=49, field_b=256 ** 3 * 32, fp64_b=(73, 256 ** 3 * 48),
@@ -401,16 +411,25 @@ def main():
         else:
             kname = "k_push_sr<float,{},1,{}>".format(
                 len(w["extra"]["grid"]), 2 if w["extra"]["grad_mode"] == "grid" else 1)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                    "traffic": (w["traffic_b"] if "traffic_b" in w and n == w["n"] else None),
+                    "kernel": kname, "alg_bytes_per_particle_step": alg / n,
+                    "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+        if "alu" in w:
+            a_ = w["alu"]
+            tf = a_["flops"] * n / (avg_launch * 1e-3) / 1e12
+            roofline = {"bound": "alu", "achieved": tf, "peak": a_["peak"], "unit": "TFLOP/s",
+                        "frac": tf / a_["peak"], "traffic": None, "kernel": kname,
+                        "fp64_flops_per_particle_step": a_["flops"],
+                        "peak_source": a_["peak_source"],
+                        "hbm": {"achieved_gbs": achieved, "frac": achieved / pk["hbm_gbs"]}}
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if w["precision"] == "mixed" else "f64", "data": "synthetic",
                 "config": workload_config(w, n_all, world, sort_every, tile),
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                             "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                             "traffic": None, "kernel": kname,
-                             "alg_bytes_per_particle_step": alg / n,
-                             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
+                "roofline": roofline,
                 "e2e": e2e,
                 "gpu_launches": args.steps + 6 * n_sorts,
                 "sort": {"every": sort_every, "sorts_in_timed_region": n_sorts,

@@ -226,6 +226,8 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
  * from dual-number replays contracted with the adjoint (a slower second
  * construction of the same quantity, for cross-checks). */
 enum { GCB_ADJ_REVERSE = 0, GCB_ADJ_TANGENT = 1 };
+/* or-ed into method: the checkpoints are already in ws (gcb_push_sr_ckpt) */
+#define GCB_ADJ_HAVE_CKPT 0x100
 
 size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, int n_steps,
                                    int ckpt_every);
@@ -233,7 +235,8 @@ size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, in
 /*
  *   p0         : initial state (device arrays, read only; FP64 or mixed
  *                layout as for gcb_push_sr, ndim 2).
- *   method     : GCB_ADJ_REVERSE or GCB_ADJ_TANGENT.
+ *   method     : GCB_ADJ_REVERSE or GCB_ADJ_TANGENT, optionally or-ed with
+ *                GCB_ADJ_HAVE_CKPT (see gcb_push_sr_ckpt).
  *   g, prm     : as for gcb_push_sr; needs g->has_grad and grad_mode GRID;
  *                sorting is not applied.  Use gca_fixed_iters > 0 so every
  *                particle-step has the same iteration count as the forward.
@@ -247,6 +250,20 @@ size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, in
 gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_params *prm,
                           int n_steps, int ckpt_every, int method, void *const *lam,
                           double *grad_rec, void *cuda_stream, void *ws, size_t ws_bytes);
+
+/*
+ * The forward pass for a later gcb_adjoint_sr: n_steps pushes of p in place
+ * (as gcb_push_sr without sorting) that also store, in the adjoint workspace
+ * ws, the initial state and every ckpt_every-th state.  gcb_adjoint_sr with
+ * method | GCB_ADJ_HAVE_CKPT on the same ws, the same n, layout, n_steps and
+ * ckpt_every then starts from those checkpoints instead of running its own
+ * forward pass (its p0 argument then only describes the layout; the caller
+ * keeps ws untouched in between).  out: the forward's statistics, or NULL.
+ * Errors as gcb_adjoint_sr.
+ */
+gcb_status gcb_push_sr_ckpt(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                            int n_steps, int ckpt_every, void *cuda_stream, void *ws,
+                            size_t ws_bytes, gcb_stats *out);
 
 /*
  * Fields linear in n_modes amplitudes a_m: rec = base + sum_m a_m pat_m

@@ -30,10 +30,17 @@
 #ifndef GCB_ADJ_OUTLINE
 #define GCB_ADJ_OUTLINE 0
 #endif
-// GCB_ADJ_CACHE: accumulate a particle-step's node adjoints per thread in
-// shared memory (1) or add every gather's contributions directly (0).
+// GCB_ADJ_CACHE: cells (0, 1 or 2) whose node adjoints a thread accumulates
+// in shared memory over a particle-step before adding them to the FP64 node
+// accumulators (0: every gather's contributions are added directly).
 #ifndef GCB_ADJ_CACHE
 #define GCB_ADJ_CACHE 1
+#endif
+// GCB_ADJ_FCACHE: gather points (x^n first, then the step's gathers in order)
+// whose interpolated field the replay keeps in shared memory for the reverse
+// loop, which otherwise gathers again; points past it are re-gathered.
+#ifndef GCB_ADJ_FCACHE
+#define GCB_ADJ_FCACHE 6
 #endif
 #ifndef GCB_ADJ_BLOCKS_F32
 #define GCB_ADJ_BLOCKS_F32 4
@@ -282,13 +289,43 @@ GCB_ADJ_FN2 void plain_gather2(const DevGrid<T> &g, const int ib[2], const T l[2
     gather<T, 2, 2>(g, ib, l, F);
 }
 
+// Interpolated fields of the step's gather points, kept per thread in shared
+// memory (thread-fastest: element (point, component) at [(point*NF+c)*TPB]).
+// Point 0 is x^n, point 1 + k the step's k-th gather.
+template <typename T>
+struct FCache {
+    T *base;
+    __device__ __forceinline__ void store(int pt, const FieldPt<T, 2> &F) const
+    {
+        if (pt >= GCB_ADJ_FCACHE) return;
+        T *q = base + pt * NF * TPB;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { q[c * TPB] = F.E[c]; q[(3 + c) * TPB] = F.B[c]; }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) q[(6 + 3 * i + j) * TPB] = F.dB[i][j];
+    }
+    __device__ __forceinline__ void load(int pt, FieldPt<T, 2> &F) const
+    {
+        const T *q = base + pt * NF * TPB;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { F.E[c] = q[c * TPB]; F.B[c] = q[(3 + c) * TPB]; }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) F.dB[i][j] = q[(6 + 3 * i + j) * TPB];
+    }
+};
+
 // Plain gather that records where it was called (R^{n-1/2}, the iterates,
-// R^{n+1/2}, in that order).
+// R^{n+1/2}, in that order) and keeps what it interpolated.
 template <typename T>
 struct RecGather {
     DevGrid<T> g;
     T (*pts)[2];
     int *count;
+    FCache<T> fc;
     __device__ __forceinline__ void operator()(const int ib[2], const T l[2], FieldPt<T, 2> &F) const
     {
         const int k = (*count)++;
@@ -297,15 +334,17 @@ struct RecGather {
             pts[k][1] = l[1];
         }
         plain_gather2(g, ib, l, F);
+        fc.store(1 + k, F);
     }
 };
 
 // Node-record adjoints of one particle-step, accumulated per thread for up
-// to two cells (4 nodes x 12 components each) in shared memory laid out
-// thread-fastest, and added to the FP64 node accumulators when a cell is
+// to GCB_ADJ_CACHE cells (4 nodes x 12 components each) in shared memory laid
+// out thread-fastest, and added to the FP64 node accumulators when a cell is
 // evicted and at the end of the step: the step's gathers (x^n, R^{n-1/2},
-// the iterates, R^{n+1/2}) mostly share one or two cells, so this replaces
-// most of the per-gather atomics.
+// the iterates, R^{n+1/2}) mostly share one cell, so this replaces most of
+// the per-gather atomics.  (One cell measured faster than two: the second
+// costs shared memory that the field cache uses better.)
 template <typename T>
 struct NodeCache {
     T *acc;          // this thread's slot 0 element; element (s, o, c) at acc[((s*4+o)*NF+c)*TPB]
@@ -341,10 +380,10 @@ struct NodeCache {
         int sl;
         if (k == key[0]) {
             sl = 0;
-        } else if (k == key[1]) {
+        } else if (GCB_ADJ_CACHE > 1 && k == key[1]) {
             sl = 1;
         } else {
-            sl = 1 - mru;
+            sl = GCB_ADJ_CACHE > 1 ? 1 - mru : 0;
             flush(sl);
             if (sl) key[1] = k; else key[0] = k;
 #pragma unroll
@@ -358,7 +397,7 @@ struct NodeCache {
     __device__ __forceinline__ void finish()
     {
         flush(0);
-        flush(1);
+        if (GCB_ADJ_CACHE > 1) flush(1);
         key[0] = key[1] = -1;
     }
 };
@@ -394,9 +433,16 @@ __device__ __forceinline__ void gather_bwd(const DevGrid<T> &g, NodeCache<T> &nc
         const T dwx = (o & 1) ? g.inv_dx[0] : -g.inv_dx[0];
         const T dwy = (o & 2) ? g.inv_dx[1] : -g.inv_dx[1];
         const T *rp = g.rec + (size_t)node * g.stride;
+        // rec_o . aF, the record read in 16-byte chunks
+        constexpr int CH = Chunk<T>::n;
         T dv = T(0);
 #pragma unroll
-        for (int c = 0; c < NF; ++c) dv = fma(__ldg(rp + c), av[c], dv);
+        for (int q = 0; q < NF / CH; ++q) {
+            T v[CH];
+            load_chunk(rp + q * CH, v);
+#pragma unroll
+            for (int j = 0; j < CH; ++j) dv = fma(v[j], av[q * CH + j], dv);
+        }
         ap[0] = fma(dwx * wy, dv, ap[0]);
         ap[1] = fma(wx * dwy, dv, ap[1]);
         const T W = wx * wy;
@@ -473,10 +519,25 @@ __device__ __forceinline__ T upar_new(const Frame<T> &f0, const StepPar<T> &s, T
 //   stage K        x^n: V^n and the u_par update
 //   stage K+1      R^{n-1/2}: conversion of u
 // so that the gather, frame and scatter code is present once.
+// field and frame at gather point `pt` (FCache numbering) located at p
 template <typename T>
-__device__ __forceinline__ void gca_rev(const DevGrid<T> &g, NodeCache<T> &grad, const StepPar<T> &s,
-                                        const int ib[2], const T l[2], const T u[3], int K,
-                                        const T (*pts)[2], const T lo[NS], T li[NS])
+__device__ __forceinline__ void frame_at(const DevGrid<T> &g, const FCache<T> &fc, int pt,
+                                         const int ib[2], const T p[2], const StepPar<T> &s,
+                                         FieldPt<T, 2> &F, Frame<T> &f)
+{
+    if (pt < GCB_ADJ_FCACHE) {
+        fc.load(pt, F);
+        make_frame<T, 2, true>(F, s.c, s.inv_c2, f);
+    } else {
+        gather_frame(g, ib, p, s, F, f);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void gca_rev(const DevGrid<T> &g, NodeCache<T> &grad, const FCache<T> &fc,
+                                        const StepPar<T> &s, const int ib[2], const T l[2],
+                                        const T u[3], int K, const T (*pts)[2], const T lo[NS],
+                                        T li[NS])
 {
     using rev::FrameAdj;
     FieldPt<T, 2> F;
@@ -484,7 +545,7 @@ __device__ __forceinline__ void gca_rev(const DevGrid<T> &g, NodeCache<T> &grad,
     // forward quantities of the conversion (at R^{n-1/2}) and of the u_par update (at x^n)
     T Gf, upar, vcm[3], uperp, mu, bpg[3], upn;
     for (int j = 0; j < 2; ++j) {
-        gather_frame(g, ib, j == 0 ? pts[0] : l, s, F, f);
+        frame_at(g, fc, j == 0 ? 1 : 0, ib, j == 0 ? pts[0] : l, s, F, f);
         if (j == 0) rev::conv_fwd(f, s, u, Gf, upar, vcm, uperp, mu, bpg);
         else upn = upar_new(f, s, upar, mu, uperp);
     }
@@ -495,7 +556,8 @@ __device__ __forceinline__ void gca_rev(const DevGrid<T> &g, NodeCache<T> &grad,
     T aVn[3] = {T(0), T(0), T(0)};
     for (int st = 0; st <= K + 1; ++st) {
         const T *p = st == 0 ? pts[K] : (st < K ? pts[K - st] : (st == K ? l : pts[0]));
-        gather_frame(g, ib, p, s, F, f);
+        const int pt = st == 0 ? K + 1 : (st < K ? K - st + 1 : (st == K ? 0 : 1));
+        frame_at(g, fc, pt, ib, p, s, F, f);
         FrameAdj<T> af;
         af.zero();
         if (st == 0) {
@@ -554,6 +616,7 @@ __global__ void __launch_bounds__(TPB, RevBlocks<T>::n) k_adjoint_rev(const AdjA
     T pts[MAXG][2];
     NodeCache<T> nc;
     nc.acc = reinterpret_cast<T *>(s_raw) + threadIdx.x;
+    const FCache<T> fc{reinterpret_cast<T *>(s_raw) + GCB_ADJ_CACHE * 4 * NF * TPB + threadIdx.x};
     nc.grad = a.grad;
     nc.nx = a.g.n[0];
     nc.ny = a.g.n[1];
@@ -581,6 +644,7 @@ __global__ void __launch_bounds__(TPB, RevBlocks<T>::n) k_adjoint_rev(const AdjA
         sp.qm = a.qm[(fl >> GCB_SPECIES_SHIFT) & 3];
         FieldPt<T, 2> F0;
         gather<T, 2, 2>(a.g, ib, l, F0);
+        fc.store(0, F0);
         const T Q = fabs(sp.qm);
         const T G = sqrt(T(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * sp.inv_c2);
         const T Bm = sqrt(F0.B[0] * F0.B[0] + F0.B[1] * F0.B[1] + F0.B[2] * F0.B[2]);
@@ -594,12 +658,12 @@ __global__ void __launch_bounds__(TPB, RevBlocks<T>::n) k_adjoint_rev(const AdjA
             T uu[3] = {u[0], u[1], u[2]}, disp[2];
             bool ncv;
             int cnt = 0;
-            gca = gca_step<T, 2, 2>(RecGather<T>{a.g, pts, &cnt}, sp, ib, l, dxp, F0, uu, disp, K, ncv);
+            gca = gca_step<T, 2, 2>(RecGather<T>{a.g, pts, &cnt, fc}, sp, ib, l, dxp, F0, uu, disp, K, ncv);
             gca = gca && cnt == K + 1 && cnt <= MAXG;
         }
         T li[NS];
         if (gca) {
-            gca_rev(a.g, nc, sp, ib, l, u, K, pts, lo, li);
+            gca_rev(a.g, nc, fc, sp, ib, l, u, K, pts, lo, li);
         } else {
             T lu[3] = {lo[2], lo[3], lo[4]};
             T ldisp[2] = {lo[0] + lo[5], lo[1] + lo[6]};
@@ -631,7 +695,10 @@ __global__ void __launch_bounds__(TPB, RevBlocks<T>::n) k_adjoint_rev(const AdjA
 }
 
 template <typename T>
-constexpr int rev_smem() { return GCB_ADJ_CACHE ? 2 * 4 * NF * TPB * (int)sizeof(T) : 0; }
+constexpr int rev_smem()
+{
+    return (GCB_ADJ_CACHE * 4 + GCB_ADJ_FCACHE) * NF * TPB * (int)sizeof(T);
+}
 
 template <typename T>
 static gcb_status launch(const AdjArgs<T> &a, int method, cudaStream_t st)

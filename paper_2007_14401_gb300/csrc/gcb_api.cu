@@ -491,30 +491,81 @@ size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, in
     return kStatsBytes + (size_t)(nck + (ckpt_every - 1) + 2) * S;
 }
 
+}  // extern "C"
+
+// checks shared by the adjoint's entry points
+static gcb_status check_adjoint(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                                int n_steps, int ckpt_every, const void *ws, size_t ws_bytes)
+{
+    gcb_status s = check_problem(p, g, prm);
+    if (s != GCB_OK) return s;
+    if (g->ndim != 2 || !g->has_grad || prm->grad_mode != GCB_GRAD_GRID) {
+        set_error("the adjoint supports 2D grids with gradient records (grad_mode GRID)");
+        return GCB_EUNSUPPORTED;
+    }
+    if (n_steps < 1 || ckpt_every < 1) { set_error("n_steps and ckpt_every must be >= 1"); return GCB_EINVAL; }
+    if (prm->gca_max_iter > GCB_ADJOINT_MAX_ITER || prm->gca_fixed_iters > GCB_ADJOINT_MAX_ITER) {
+        set_error("the adjoint records at most %d fixed-point iterations per step", GCB_ADJOINT_MAX_ITER);
+        return GCB_EUNSUPPORTED;
+    }
+    const size_t need = gcb_adjoint_workspace_bytes(p, g, n_steps, ckpt_every);
+    if (!ws || !aligned(ws, 256)) { set_error("workspace NULL or not 256-byte aligned"); return GCB_EINVAL; }
+    if (ws_bytes < need) { set_error("workspace too small (%zu < %zu bytes)", ws_bytes, need); return GCB_ENOMEM; }
+    return GCB_OK;
+}
+
+extern "C" {
+
+gcb_status gcb_push_sr_ckpt(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm0,
+                            int n_steps, int ckpt_every, void *cuda_stream, void *ws,
+                            size_t ws_bytes, gcb_stats *out)
+{
+    g_err[0] = 0;
+    gcb_status s = check_adjoint(p, g, prm0, n_steps, ckpt_every, ws, ws_bytes);
+    if (s != GCB_OK) return s;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    gcb_params prm = *prm0;
+    prm.sort_every = 0;
+    const int nd = g->ndim;
+    const int nck = (n_steps + ckpt_every - 1) / ckpt_every;
+    const size_t S = state_set_bytes(p, nd);
+    unsigned long long *stats = (unsigned long long *)ws;
+    uint8_t *ck = (uint8_t *)ws + kStatsBytes;
+    if (cudaMemsetAsync(stats, 0, kStatsBytes, st) != cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(cudaGetLastError()));
+        return GCB_ECUDA;
+    }
+    if (p->n > 0) {
+        const bool fp64 = p->mom_dtype == GCB_F64;
+        gcb_particles c = state_view(p, nd, ck);
+        if ((s = copy_state(&c, p, nd, st)) != GCB_OK) return s;
+        for (int k = 0; k < n_steps; ++k) {
+            s = fp64 ? push_step_f64(p, p, g, &prm, st, stats) : push_step_f32(p, p, g, &prm, st, stats);
+            if (s != GCB_OK) return s;
+            const int kc = (k + 1) / ckpt_every;
+            if ((k + 1) % ckpt_every == 0 && kc < nck) {
+                c = state_view(p, nd, ck + (size_t)kc * S);
+                if ((s = copy_state(&c, p, nd, st)) != GCB_OK) return s;
+            }
+        }
+    }
+    return read_stats(stats, st, out);
+}
+
 gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_params *prm0,
                           int n_steps, int ckpt_every, int method, void *const *lam,
                           double *grad_rec, void *cuda_stream, void *ws, size_t ws_bytes)
 {
     g_err[0] = 0;
-    gcb_status s = check_problem(p0, g, prm0);
+    gcb_status s = check_adjoint(p0, g, prm0, n_steps, ckpt_every, ws, ws_bytes);
     if (s != GCB_OK) return s;
-    if (g->ndim != 2 || !g->has_grad || prm0->grad_mode != GCB_GRAD_GRID) {
-        set_error("the adjoint supports 2D grids with gradient records (grad_mode GRID)");
-        return GCB_EUNSUPPORTED;
-    }
-    if (n_steps < 1 || ckpt_every < 1) { set_error("n_steps and ckpt_every must be >= 1"); return GCB_EINVAL; }
+    const bool have_ckpt = (method & GCB_ADJ_HAVE_CKPT) != 0;
+    method &= ~GCB_ADJ_HAVE_CKPT;
     if (method != GCB_ADJ_REVERSE && method != GCB_ADJ_TANGENT) { set_error("unknown adjoint method %d", method); return GCB_EINVAL; }
-    if (prm0->gca_max_iter > GCB_ADJOINT_MAX_ITER || prm0->gca_fixed_iters > GCB_ADJOINT_MAX_ITER) {
-        set_error("the adjoint records at most %d fixed-point iterations per step", GCB_ADJOINT_MAX_ITER);
-        return GCB_EUNSUPPORTED;
-    }
     if (!lam || !grad_rec || !aligned(grad_rec, 8)) { set_error("lam or grad_rec NULL"); return GCB_EINVAL; }
     const size_t me = p0->mom_dtype == GCB_F64 ? 8 : 4;
     for (int k = 0; k < 7; ++k)
         if (p0->n > 0 && (!lam[k] || !aligned(lam[k], me))) { set_error("lam[%d] NULL or misaligned", k); return GCB_EINVAL; }
-    const size_t need = gcb_adjoint_workspace_bytes(p0, g, n_steps, ckpt_every);
-    if (!ws || !aligned(ws, 256)) { set_error("workspace NULL or not 256-byte aligned"); return GCB_EINVAL; }
-    if (ws_bytes < need) { set_error("workspace too small (%zu < %zu bytes)", ws_bytes, need); return GCB_ENOMEM; }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     gcb_params prm = *prm0;
     prm.sort_every = 0;
@@ -537,17 +588,19 @@ gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_
     auto step = [&](const gcb_particles *out, const gcb_particles *in) {
         return fp64 ? push_step_f64(out, in, g, &prm, st, stats) : push_step_f32(out, in, g, &prm, st, stats);
     };
-    // forward: checkpoints every ckpt_every steps
-    gcb_particles c0 = state_view(p0, nd, ck);
-    if ((s = copy_state(&c0, p0, nd, st)) != GCB_OK) return s;
-    gcb_particles cur = c0;
-    gcb_particles tA = state_view(p0, nd, tmp), tB = state_view(p0, nd, tmp + S);
-    for (int k = 0; k + 1 < nck * ckpt_every && k < (nck - 1) * ckpt_every; ++k) {
-        const bool boundary = (k + 1) % ckpt_every == 0;
-        gcb_particles out = boundary ? state_view(p0, nd, ck + (size_t)((k + 1) / ckpt_every) * S)
-                                     : (cur.u[0] == tA.u[0] ? tB : tA);
-        if ((s = step(&out, &cur)) != GCB_OK) return s;
-        cur = out;
+    if (!have_ckpt) {
+        // forward: checkpoints every ckpt_every steps
+        gcb_particles c0 = state_view(p0, nd, ck);
+        if ((s = copy_state(&c0, p0, nd, st)) != GCB_OK) return s;
+        gcb_particles cur = c0;
+        gcb_particles tA = state_view(p0, nd, tmp), tB = state_view(p0, nd, tmp + S);
+        for (int k = 0; k < (nck - 1) * ckpt_every; ++k) {
+            const bool boundary = (k + 1) % ckpt_every == 0;
+            gcb_particles out = boundary ? state_view(p0, nd, ck + (size_t)((k + 1) / ckpt_every) * S)
+                                         : (cur.u[0] == tA.u[0] ? tB : tA);
+            if ((s = step(&out, &cur)) != GCB_OK) return s;
+            cur = out;
+        }
     }
     // backward over segments
     for (int sg = nck - 1; sg >= 0; --sg) {

@@ -65,7 +65,7 @@ class GcbKsParams(C.Structure):
 EXPORTS = ["gcb_version", "gcb_status_string", "gcb_last_error", "gcb_grid_stride",
            "gcb_grid_pack", "gcb_pos_split", "gcb_pos_join", "gcb_workspace_bytes",
            "gcb_sort_sr", "gcb_push_sr", "gcb_push_sr_noalloc", "gcb_adjoint_workspace_bytes",
-           "gcb_adjoint_sr", "gcb_grid_combine", "gcb_grad_project", "gcb_ks_cell_size",
+           "gcb_adjoint_sr", "gcb_push_sr_ckpt", "gcb_grid_combine", "gcb_grad_project", "gcb_ks_cell_size",
            "gcb_push_ks"]
 
 
@@ -105,6 +105,9 @@ def load_library(path: str | None = None):
                                    C.c_int, P(C.c_void_p), C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_size_t]
     lib.gcb_adjoint_sr.restype = C.c_int
+    lib.gcb_push_sr_ckpt.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int, C.c_int,
+                                     C.c_void_p, C.c_void_p, C.c_size_t, P(GcbStats)]
+    lib.gcb_push_sr_ckpt.restype = C.c_int
     lib.gcb_grid_combine.argtypes = [P(GcbGrid), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                      C.c_void_p]
     lib.gcb_grid_combine.restype = C.c_int
@@ -364,27 +367,62 @@ LAM_ORDER = ("x0", "x1", "u0", "u1", "u2", "dxp0", "dxp1")
 
 
 ADJ_METHODS = {"reverse": 0, "tangent": 1}
+ADJ_HAVE_CKPT = 0x100
+
+
+class AdjointWorkspace:
+    """Device workspace of the adjoint (checkpoints and segment states) for a
+    given state layout, grid, n_steps and checkpoint spacing."""
+
+    def __init__(self, state: State, grid: Grid, n_steps: int, ckpt_every: int = 16):
+        nb = _lib.gcb_adjoint_workspace_bytes(C.byref(state.s), C.byref(grid.s), int(n_steps),
+                                              int(ckpt_every))
+        if nb == 0:
+            raise GcbError("gcb_adjoint_workspace_bytes: invalid arguments")
+        self.buf = torch.empty(nb, dtype=torch.uint8, device=state.u.device)
+        self.n_steps, self.ckpt_every = int(n_steps), int(ckpt_every)
+        self.have_ckpt = False
+
+
+def push_ckpt(state: State, grid: Grid, params: GcbParams, n_steps: int,
+              workspace: AdjointWorkspace, stream=None, stats: bool = False):
+    """n_steps pushes of ``state`` in place that also store the adjoint's
+    checkpoints in ``workspace`` (for a following adjoint(..., workspace=))."""
+    out = GcbStats() if stats else None
+    rc = _lib.gcb_push_sr_ckpt(C.byref(state.s), C.byref(grid.s), C.byref(params), int(n_steps),
+                               workspace.ckpt_every, _stream_ptr(stream),
+                               C.c_void_p(workspace.buf.data_ptr()), workspace.buf.numel(),
+                               C.byref(out) if stats else None)
+    _check(rc, "gcb_push_sr_ckpt")
+    workspace.have_ckpt = True
+    if stats:
+        return {k: getattr(out, k) for k, _ in GcbStats._fields_}
+    return None
 
 
 def adjoint(state: State, grid: Grid, params: GcbParams, n_steps: int, lam: torch.Tensor,
-            ckpt_every: int = 16, stream=None, method: str = "reverse") -> torch.Tensor:
+            ckpt_every: int = 16, stream=None, method: str = "reverse",
+            workspace: AdjointWorkspace | None = None) -> torch.Tensor:
     """Reverse sweep of n_steps pushes from the initial ``state`` (left
     unchanged).  ``lam`` (7, n) in the momentum dtype holds dL/d(final x0, x1,
     u0, u1, u2, dxp0, dxp1) and is overwritten with dL/d(initial state).
     Returns dL/d(record values) as a float64 tensor (nodes, 12).  method
-    "reverse" (default) or "tangent" (dual-number Jacobian columns, slower)."""
-    nb = _lib.gcb_adjoint_workspace_bytes(C.byref(state.s), C.byref(grid.s), int(n_steps),
-                                          int(ckpt_every))
-    if nb == 0:
-        raise GcbError("gcb_adjoint_workspace_bytes: invalid arguments")
-    ws = torch.empty(nb, dtype=torch.uint8, device=state.u.device)
+    "reverse" (default) or "tangent" (dual-number Jacobian columns, slower).
+    A ``workspace`` filled by push_ckpt supplies the checkpoints (and its
+    n_steps / ckpt_every must match); otherwise the forward is rerun here."""
+    if workspace is None:
+        workspace = AdjointWorkspace(state, grid, n_steps, ckpt_every)
+    elif (workspace.n_steps, workspace.ckpt_every) != (int(n_steps), int(ckpt_every)):
+        raise GcbError("workspace was sized for another n_steps / ckpt_every")
+    ws, nb = workspace.buf, workspace.buf.numel()
+    mcode = ADJ_METHODS[method] | (ADJ_HAVE_CKPT if workspace.have_ckpt else 0)
     nn = grid.n[0] * grid.n[1] * grid.n[2]
     grad = torch.empty((nn, 12), dtype=torch.float64, device=state.u.device)
     if lam.shape != (7, state.n) or lam.dtype != state.u.dtype or not lam.is_contiguous():
         raise GcbError("lam must be a contiguous (7, n) tensor of the momentum dtype")
     ptrs = (C.c_void_p * 7)(*[lam[k].data_ptr() for k in range(7)])
     rc = _lib.gcb_adjoint_sr(C.byref(state.s), C.byref(grid.s), C.byref(params), int(n_steps),
-                             int(ckpt_every), ADJ_METHODS[method], ptrs,
+                             int(ckpt_every), mcode, ptrs,
                              C.c_void_p(grad.data_ptr()),
                              _stream_ptr(stream), C.c_void_p(ws.data_ptr()), nb)
     _check(rc, "gcb_adjoint_sr")
@@ -413,10 +451,11 @@ def grad_project(grid: Grid, grad: torch.Tensor, pat: torch.Tensor, stream=None)
 
 class ModePush(torch.autograd.Function):
     """Differentiable n-step push: (x0, u0, dxp0, amps) -> (x, u, dxp), the
-    field records being base + sum_m amps[m] pat[m].  ``ctx_cfg`` is a dict
+    field records being base + sum_m amps[m] pat[m].  ``cfg`` is a dict
     with grid, base, pat, params, n_steps, ckpt_every, flags, precision,
-    pos_mode.  x as float64 (2, n); u (3, n) and dxp (2, n) in the momentum
-    dtype."""
+    pos_mode, and optionally method and ckpt_in_forward (default True: the
+    forward writes the adjoint's checkpoints).  x as float64 (2, n); u (3, n)
+    and dxp (2, n) in the momentum dtype."""
 
     @staticmethod
     def forward(ctx, x0, u0, dxp0, amps, cfg):
@@ -425,8 +464,15 @@ class ModePush(torch.autograd.Function):
         st = State(x0.shape[1], 2, cfg.get("precision", "fp64"), cfg.get("pos_mode", "f64"),
                    device=x0.device)
         st.set_tensors(x0, u0, dxp0, cfg["flags"])
-        ctx.cfg, ctx.init = cfg, st.clone()
-        push(st, grid, cfg["params"], cfg["n_steps"], stats=False)
+        ctx.cfg = cfg
+        if cfg.get("ckpt_in_forward", True):
+            # the forward stores the checkpoints; the backward starts from them
+            ctx.ws = AdjointWorkspace(st, grid, cfg["n_steps"], cfg.get("ckpt_every", 16))
+            push_ckpt(st, grid, cfg["params"], cfg["n_steps"], ctx.ws)
+            ctx.init = st          # layout only: the initial state is checkpoint 0
+        else:
+            ctx.ws, ctx.init = None, st.clone()
+            push(st, grid, cfg["params"], cfg["n_steps"], stats=False)
         return st.x_f64(), st.u.clone(), st.dxp.clone()
 
     @staticmethod
@@ -441,7 +487,8 @@ class ModePush(torch.autograd.Function):
         if gdxp is not None:
             lam[5:7] = gdxp.to(lam.dtype)
         grad = adjoint(st, cfg["grid"], cfg["params"], cfg["n_steps"], lam,
-                       cfg.get("ckpt_every", 16), method=cfg.get("method", "reverse"))
+                       cfg.get("ckpt_every", 16), method=cfg.get("method", "reverse"),
+                       workspace=ctx.ws)
         ga = grad_project(cfg["grid"], grad, cfg["pat"])
         return lam[0:2].to(torch.float64), lam[2:5].clone(), lam[5:7].clone(), ga, None
 

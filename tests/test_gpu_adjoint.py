@@ -115,7 +115,7 @@ def rel_err(got, ref, scale):
     return np.maximum(np.abs(got - ref) - FD_FLOOR, 0.0) / (np.abs(ref) + scale)
 
 
-def run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5, method="reverse"):
+def run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5, method="reverse", ckpt_fwd=True):
     """Forward + adjoint through ModePush; returns (state grads (7, n), mode grads)."""
     import torch
     base, pats, amps, st0, params, w = case
@@ -131,7 +131,7 @@ def run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5, method="reverse"):
     cfg = dict(grid=grid, base=base_rec, pat=pat_rec,
                params=G.make_params(params, **FIXED), n_steps=N_STEPS, ckpt_every=ckpt_every,
                flags=torch.tensor(st0["flags"], device=dev), precision=precision,
-               pos_mode=pos_mode, method=method)
+               pos_mode=pos_mode, method=method, ckpt_in_forward=ckpt_fwd)
     x, u, dxp = G.ModePush.apply(x0, u0, d0, a, cfg)
     n = u.shape[1]
     Gm = torch.sqrt(1.0 + (u.double() ** 2).sum(0))
@@ -186,11 +186,13 @@ def test_reverse_and_tangent_agree(G, case):
 
 
 def test_adjoint_checkpoint_interval_invariance(G, case):
-    """Checkpoint spacing changes only where the forward is recomputed: the
-    gradients agree to the rounding of the FP64 atomic accumulation."""
+    """Checkpoint spacing, and whether the checkpoints come from the forward
+    (gcb_push_sr_ckpt) or from the adjoint's own forward pass, change only
+    where states are recomputed: the gradients agree to the rounding of the
+    FP64 atomic accumulation."""
     ref = run_gpu(G, case, "fp64", "f64", "f64", ckpt_every=N_STEPS)
-    for ck in (1, 5):
-        got = run_gpu(G, case, "fp64", "f64", "f64", ckpt_every=ck)
+    for ck, fwd in ((1, True), (5, True), (5, False), (N_STEPS, False)):
+        got = run_gpu(G, case, "fp64", "f64", "f64", ckpt_every=ck, ckpt_fwd=fwd)
         np.testing.assert_allclose(got[0], ref[0], rtol=0, atol=1e-12 * np.abs(ref[0]).max())
         np.testing.assert_allclose(got[1], ref[1], rtol=1e-12, atol=1e-14)
 
