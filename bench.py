@@ -452,12 +452,12 @@ def main():
 
 
 def adjoint_launches():
-    """Kernels of one forward + reverse sweep: ADJ_STEPS pushes; in the sweep
-    the pushes up to the last checkpoint, per segment its recomputed pushes
+    """Kernels of one forward + reverse sweep: ADJ_STEPS pushes (the forward
+    stores the checkpoints); in the sweep, per segment its recomputed pushes
     and its adjoint steps, and the mode projection."""
     nck = (ADJ_STEPS + ADJ_CKPT - 1) // ADJ_CKPT
     seg = [min(ADJ_CKPT, ADJ_STEPS - s * ADJ_CKPT) for s in range(nck)]
-    return ADJ_STEPS + (nck - 1) * ADJ_CKPT + sum(2 * L - 1 for L in seg) + 1
+    return ADJ_STEPS + sum(2 * L - 1 for L in seg) + 1
 
 
 def run_adjoint(args):
@@ -485,21 +485,23 @@ def run_adjoint(args):
     gp = G.make_params(p, gca_fixed_iters=ADJ_FIXED_ITERS)
     n = init.n
     cur = init.clone()
-    ws = G.Workspace(cur, grid, gp)
     lam = torch.empty((7, n), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    aws = G.AdjointWorkspace(cur, grid, ADJ_STEPS, ADJ_CKPT)
+
     def forward():
+        # the forward pass stores the checkpoints the reverse sweep starts from
         for t_, s_ in zip(cur.tensors(), init.tensors()):
             t_.copy_(s_)
-        G.push(cur, grid, gp, ADJ_STEPS, workspace=ws, stats=False)
+        G.push_ckpt(cur, grid, gp, ADJ_STEPS, aws)
 
     def backward():
         # dL/du_final for L = mean (Gamma - 1) c^2: u / (Gamma n)
         Gm = torch.sqrt(1.0 + (cur.u * cur.u).sum(0))
         lam.zero_()
         lam[2:5] = cur.u / (Gm * n)
-        grad = G.adjoint(init, grid, gp, ADJ_STEPS, lam, ADJ_CKPT)
+        grad = G.adjoint(init, grid, gp, ADJ_STEPS, lam, ADJ_CKPT, workspace=aws)
         # the amplitudes are shared by all ranks: sum their gradients
         return multi.sum_over_ranks(G.grad_project(grid, grad, pat_rec))
 
