@@ -253,6 +253,68 @@ def run_reference(args, rank, w):
     return 0
 
 
+def end_to_end(G, ds, grid, gp, ws, ks, step, args, barrier, stream, n, multi):
+    """The metric through the public API with the state in pinned host
+    memory: every step copies each particle's whole state host -> device,
+    pushes it and copies it back.  The particles are streamed in chunks on
+    three CUDA streams (copy in, push, copy out), so that one chunk's copies
+    overlap another's push, as a caller streaming particles through the GPU
+    would; a chunk's next copy in waits for its previous copy out."""
+    import torch
+    host_all = [t.cpu().pin_memory() for t in ds.tensors()]
+    h2d = sum(t.numel() * t.element_size() for t in host_all)
+
+    def rows(t, a_, b_):
+        return [t[a_:b_]] if t.dim() == 1 else [t[r, a_:b_] for r in range(t.shape[0])]
+
+    C = max(1, args.e2e_chunks)
+    edges = [((n * c // C) // 256) * 256 for c in range(C)] + [n]
+    spans = [(a_, b_) for a_, b_ in zip(edges[:-1], edges[1:]) if b_ > a_]
+    views = [ds.view(a_, b_) for a_, b_ in spans]
+    pairs = [[(d_, h_) for t_d, t_h in zip(ds.tensors(), host_all)
+              for d_, h_ in zip(rows(t_d, a_, b_), rows(t_h, a_, b_))] for a_, b_ in spans]
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in spans]
+    ev_cmp = [torch.cuda.Event() for _ in spans]
+    ev_out = [torch.cuda.Event() for _ in spans]
+    kws = G.ks_workspace() if ks else None
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ke = max(3, args.steps // 5)
+    e0.record(stream)
+    for s_ in (s_in, s_cmp, s_out):
+        s_.wait_stream(stream)
+    for k in range(ke):
+        gp.step_index = step[0]
+        for c, v in enumerate(views):
+            if k > 0:
+                s_in.wait_event(ev_out[c])
+            with torch.cuda.stream(s_in):
+                for d_, h_ in pairs[c]:
+                    d_.copy_(h_, non_blocking=True)
+            ev_in[c].record(s_in)
+            s_cmp.wait_event(ev_in[c])
+            if ks:
+                G.push_ks(v, grid, gp, 1, stream=s_cmp, workspace=kws, stats=False)
+            else:
+                G.push(v, grid, gp, 1, stream=s_cmp, workspace=ws, stats=False)
+            ev_cmp[c].record(s_cmp)
+            s_out.wait_event(ev_cmp[c])
+            with torch.cuda.stream(s_out):
+                for d_, h_ in pairs[c]:
+                    h_.copy_(d_, non_blocking=True)
+            ev_out[c].record(s_out)
+        step[0] += 1
+    for s_ in (s_in, s_cmp, s_out):
+        stream.wait_stream(s_)
+    e1.record(stream)
+    barrier()
+    rate, _, _ = multi.whole_job_rate(n, ke, e0.elapsed_time(e1), device="cuda")
+    return {"value": rate, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+            "chunks": len(spans), "streams": "copy-in / push / copy-out"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -264,6 +326,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=4,
+                    help="particle chunks streamed through the GPU in the end-to-end timing")
     ap.add_argument("--sort-every", type=int, default=None)
     ap.add_argument("--sort-tile", default=None, help="cells per sort tile, e.g. 2,2")
     ap.add_argument("--particles", type=int, default=None,
@@ -355,25 +419,7 @@ def main():
     # pinned host memory, pushed, and copied back out
     e2e = None
     if not args.no_e2e:
-        host = [t.cpu().pin_memory() for t in ds.tensors()]
-        dev = ds.tensors()
-        h2d = sum(t.numel() * t.element_size() for t in host)
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        ke = max(3, args.steps // 5)
-        e0.record(stream)
-        for _ in range(ke):
-            for d_, h_ in zip(dev, host):
-                d_.copy_(h_, non_blocking=True)
-            one_step()
-            for d_, h_ in zip(dev, host):
-                h_.copy_(d_, non_blocking=True)
-        e1.record(stream)
-        barrier()
-        e2e_rate, _, _ = multi.whole_job_rate(n, ke, e0.elapsed_time(e1), device="cuda")
-        e2e = {"value": e2e_rate, "unit": METRIC,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d}
+        e2e = end_to_end(G, ds, grid, gp, ws, ks, step, args, barrier, stream, n, multi)
 
     fp64 = None
     if not args.no_fp64 and rank == 0 and w["fp64_b"] is not None:

@@ -267,6 +267,20 @@ class State:
         self.dxp.copy_(dxp)
         self.flags.copy_(flags)
 
+    def view(self, lo: int, hi: int) -> "State":
+        """Particles lo .. hi-1 as a State sharing this one's memory (for
+        streaming particle ranges through the GPU; lo a multiple of 64 keeps
+        every array 256-byte aligned)."""
+        v = State.__new__(State)
+        v.n, v.ndim, v.precision = int(hi - lo), self.ndim, self.precision
+        v.pos_mode, v.mom_dtype = self.pos_mode, self.mom_dtype
+        v.x, v.u, v.dxp, v.flags = (self.x[:, lo:hi], self.u[:, lo:hi], self.dxp[:, lo:hi],
+                                    self.flags[lo:hi])
+        v.x_lo = self.x_lo[:, lo:hi] if self.x_lo is not None else None
+        v.pid = self.pid[lo:hi] if self.pid is not None else None
+        v._make_struct()
+        return v
+
     def clone(self) -> "State":
         c = State.__new__(State)
         c.n, c.ndim, c.precision = self.n, self.ndim, self.precision
@@ -525,13 +539,19 @@ class KsGrid:
         self._keep = dev
 
 
+def ks_workspace(device="cuda") -> Workspace:
+    """The workspace gcb_push_ks needs (its statistics counters only)."""
+    ws = Workspace.__new__(Workspace)
+    ws.buf = torch.empty(256, dtype=torch.uint8, device=device)
+    ws.nbytes = 256
+    return ws
+
+
 def push_ks(state: State, grid: KsGrid, params: GcbParams, n_steps: int = 1, stream=None,
             workspace: Workspace | None = None, stats: bool = True):
     """n_steps covariant coupled steps of ``state`` (FP64, ndim 3) in place."""
     if workspace is None:
-        workspace = Workspace.__new__(Workspace)
-        workspace.buf = torch.empty(256, dtype=torch.uint8, device=state.x.device)
-        workspace.nbytes = 256
+        workspace = ks_workspace(state.x.device)
     out = GcbStats() if stats else None
     rc = _lib.gcb_push_ks(C.byref(state.s), C.byref(grid.s), C.byref(grid.kp), C.byref(params),
                           int(n_steps), _stream_ptr(stream), C.c_void_p(workspace.buf.data_ptr()),

@@ -197,6 +197,20 @@ def test_adjoint_checkpoint_interval_invariance(G, case):
         np.testing.assert_allclose(got[1], ref[1], rtol=1e-12, atol=1e-14)
 
 
+def test_reverse_and_tangent_agree_mixed(G, case):
+    """The FP32 constructions: written-out reverse sweep (shared-memory
+    accumulation, FP32 fast division) against dual-number columns (direct
+    FP64 atomics): equal to FP32 rounding of the different operation orders."""
+    r = run_gpu(G, case, "mixed", "pair", "f32", method="reverse")
+    t = run_gpu(G, case, "mixed", "pair", "f32", method="tangent")
+    for k in range(7):
+        sc = np.sqrt(np.mean(t[0][k] ** 2))
+        err = np.abs(r[0][k] - t[0][k]) / (np.abs(t[0][k]) + sc)
+        assert np.quantile(err, 0.99) <= 1e-3, (k, np.quantile(err, [0.5, 0.99]))
+    sc = np.sqrt(np.mean(t[1] ** 2))
+    assert np.all(np.abs(r[1] - t[1]) <= 1e-3 * (np.abs(t[1]) + sc)), (r[1], t[1])
+
+
 @pytest.mark.parametrize("method", ["reverse", "tangent"])
 def test_adjoint_mixed_close_to_fp64(G, case, fd, method):
     """FP32 forward + FP32 adjoint (FP32-pair positions, FP32 records) against
