@@ -326,7 +326,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-chunks", type=int, default=4,
+    ap.add_argument("--e2e-chunks", type=int, default=8,
                     help="particle chunks streamed through the GPU in the end-to-end timing")
     ap.add_argument("--sort-every", type=int, default=None)
     ap.add_argument("--sort-tile", default=None, help="cells per sort tile, e.g. 2,2")
