@@ -108,7 +108,7 @@ def _gen_adjoint(n, seed):
 # forward run of ADJ_STEPS pushes plus the reverse sweep for L = mean final
 # kinetic energy, which yields dL/d(initial state) of every particle and
 # dL/da_m.
-ADJ_STEPS, ADJ_CKPT, ADJ_FIXED_ITERS = 256, 16, 4
+ADJ_STEPS, ADJ_CKPT, ADJ_FIXED_ITERS = 256, 16, 6
 ADJOINT = dict(gen=_gen_adjoint, n=1 << 20,
                desc="adjoint: 2D double Harris + GEM + 64 modes at 512x256, {n} particles, "
                     f"{ADJ_STEPS} steps, checkpoints every {ADJ_CKPT}, mixed FP32 forward + "

@@ -39,7 +39,7 @@ pytestmark = pytest.mark.gpu
 N = 1 << 20
 N_STEPS = 256
 CKPT = 16
-FIXED = dict(gca_fixed_iters=4)
+FIXED = dict(gca_fixed_iters=6)
 SAMPLE = np.arange(0, N, 1024)
 N_MODES_FD = 8
 H = 1e-6
@@ -176,9 +176,9 @@ def test_adjoint_full_size_sample(G, problem, oracle_fd):
     rec["da_adj"] = ga[:N_MODES_FD].tolist()
     report(rec)
     print(rec)
-    # measured on a GB300: W 99.6 %, du0 1.6e-6 (median) / 1.1e-4 (p99), modes
-    # 1.6e-3 (max); the bounds leave an order of magnitude for the FP32
-    # rounding differences between builds
+    # measured on a GB300 (6 fixed-point iterations): W 99.5 %, du0 1.8e-6
+    # (median) / 1.2e-4 (p99), modes 1.9e-3 (max); the bounds leave about an
+    # order of magnitude for the FP32 rounding differences between builds
     assert W.mean() >= 0.95, rec
     assert rec["du0_rel_err_median"] <= 1e-4 and rec["du0_rel_err_p99"] <= 1e-2, rec
     assert rec["da_rel_err_max"] <= 1e-2, rec
