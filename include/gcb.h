@@ -127,6 +127,14 @@ typedef struct {
                                 step whose global index is a multiple of it */
     int32_t sort_tile[3];    /* cells per sort tile along each axis (0 = 8,8,4) */
     int64_t step_index;      /* global index of the first step of this call */
+    int32_t fuse_steps;      /* <= 1: one kernel launch per step, the state going
+                                through device memory every step (the PiC mode:
+                                fields may change between calls of one step);
+                                k > 1: up to k steps per launch with each
+                                particle tile's state kept on chip between them
+                                (the test-particle mode, fields static over the
+                                call); a fused launch never spans a sort.  The
+                                results are the same bit for bit. */
 } gcb_params;
 
 /* Counters of one gcb_push_sr call, summed over its steps. */

@@ -405,18 +405,31 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
         set_error("cudaMemsetAsync: %s", cudaGetErrorString(cudaGetLastError()));
         return GCB_ECUDA;
     }
-    for (int step = 0; step < n_steps; ++step) {
+    for (int step = 0; step < n_steps;) {
         const gcb_particles *in = p;
         gcb_particles q;
-        if (prm->sort_every > 0 && p->n > 0 && (prm->step_index + step) % prm->sort_every == 0) {
+        const int64_t gstep = prm->step_index + step;
+        if (prm->sort_every > 0 && p->n > 0 && gstep % prm->sort_every == 0) {
             SortPlan pl;
             SortedView v;
             s = sort_step(p, g, prm, st, ws, ws_bytes, q, pl, v);
             if (s != GCB_OK) return s;
             in = &q;
         }
-        s = fp64 ? push_step_f64(p, in, g, prm, st, stats) : push_step_f32(p, in, g, prm, st, stats);
+        // steps fused into this launch: at most fuse_steps, none past the
+        // next sort
+        int k = 1;
+        if (prm->fuse_steps > 1) {
+            k = prm->fuse_steps < n_steps - step ? prm->fuse_steps : n_steps - step;
+            if (prm->sort_every > 0) {
+                const int to_sort = prm->sort_every - (int)(gstep % prm->sort_every);
+                k = k < to_sort ? k : to_sort;
+            }
+        }
+        s = fp64 ? push_step_f64(p, in, g, prm, st, stats, k)
+                 : push_step_f32(p, in, g, prm, st, stats, k);
         if (s != GCB_OK) return s;
+        step += k;
     }
     return read_stats(stats, st, out);
 }

@@ -18,13 +18,16 @@ constexpr size_t kStatsBytes = 256;
 
 void set_error(const char *fmt, ...);
 
-// One kernel pass (one step) over all particles, reading the arrays of `in`
-// (the caller's, or a sorted copy) and writing those of `p`; stats accumulate
-// into the device counters `stats` (ST_* layout).  Defined per precision.
+// One kernel pass over all particles, reading the arrays of `in` (the
+// caller's, or a sorted copy) and writing those of `p`; stats accumulate
+// into the device counters `stats` (ST_* layout).  nsteps > 1 takes that many
+// steps in the one launch (fused kernel).  Defined per precision.
 gcb_status push_step_f64(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
-                         const gcb_params *prm, cudaStream_t st, unsigned long long *stats);
+                         const gcb_params *prm, cudaStream_t st, unsigned long long *stats,
+                         int nsteps = 1);
 gcb_status push_step_f32(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
-                         const gcb_params *prm, cudaStream_t st, unsigned long long *stats);
+                         const gcb_params *prm, cudaStream_t st, unsigned long long *stats,
+                         int nsteps = 1);
 
 // Adjoint (adjoint_sr.cu): one backward step for all particles whose
 // pre-step state is `s`; lam[7] (x0 x1 u0 u1 u2 dxp0 dxp1) is updated in

@@ -60,6 +60,7 @@ struct PushArgs {
     R f_E;
     R c2;
     int force;
+    int nsteps;               // steps of this launch (> 1 only for the fused kernel)
     unsigned long long *stats;
 };
 
@@ -133,7 +134,11 @@ __device__ __forceinline__ double wrap_f64(double x, double L)
 template <typename R>
 __device__ __forceinline__ bool finite_r(R v) { return isfinite(v); }
 
-template <typename R, int ND, int PM, int GM>
+// FUSE = false: one step per launch (the PiC mode: state through HBM every
+// step).  FUSE = true: a.nsteps steps per launch, each tile's state kept in
+// its shared-memory slots between the steps and written once at the end (the
+// test-particle mode); every step's arithmetic is the unfused step's.
+template <typename R, int ND, int PM, int GM, bool FUSE>
 __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(const PushArgs<R> a)
 {
     constexpr int TPB = Tile<R>::n;
@@ -163,8 +168,9 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
 
     const int64_t ntiles = (a.np + TPB - 1) / TPB;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t i = tile * TPB + tid;
-        const bool valid = i < a.np;
+      const int64_t i = tile * TPB + tid;
+      const bool valid = i < a.np;
+      for (int stp = 0; stp < (FUSE ? a.nsteps : 1); ++stp) {
         int cls = 2;
         uint8_t fl = 0;
         int64_t pid = 0;
@@ -174,19 +180,20 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
         FieldPt<R, ND> F;
         int ib[ND];
         if (valid) {
-            fl = a.flagsin[i];
-            if (a.pidin != a.pid) pid = a.pidin[i];
+            const bool from_smem = FUSE && stp > 0;   // the slot holds the previous step's output
+            fl = from_smem ? s_fl[tid] : a.flagsin[i];
+            if (!from_smem && a.pidin != a.pid) pid = a.pidin[i];
             bool fin = true;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
-                xs[d] = reinterpret_cast<const PosT *>(a.xin[d])[i];
-                xl[d] = PM ? a.xloin[d][i] : 0.0f;
-                dd[d] = a.dxpin[d][i];
+                xs[d] = from_smem ? s_x[d][tid] : reinterpret_cast<const PosT *>(a.xin[d])[i];
+                xl[d] = PM ? (from_smem ? s_xl[d][tid] : a.xloin[d][i]) : 0.0f;
+                dd[d] = from_smem ? s_d[d][tid] : a.dxpin[d][i];
                 fin = fin && finite_r(xs[d]) && finite_r(xl[d]) && finite_r(dd[d]);
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                uu[k] = a.uin[k][i];
+                uu[k] = from_smem ? s_u[k][tid] : a.uin[k][i];
                 fin = fin && finite_r(uu[k]);
             }
             if (fin) {
@@ -214,20 +221,23 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
                 if (a.force == GCB_FORCE_GCA) S = 0;
                 cls = S;
             } else {
-                // frozen: written back unchanged (with its flag) right here
+                // frozen: written back unchanged (with its flag) right here;
+                // fused, it stays in its slot for the final store
                 fl |= GCB_FLAG_NONFINITE;
                 ++nf;
+                if (!FUSE) {
 #pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    reinterpret_cast<PosT *>(a.x[d])[i] = xs[d];
-                    if (PM) a.xlo[d][i] = xl[d];
-                    a.dxp[d][i] = dd[d];
+                    for (int d = 0; d < ND; ++d) {
+                        reinterpret_cast<PosT *>(a.x[d])[i] = xs[d];
+                        if (PM) a.xlo[d][i] = xl[d];
+                        a.dxp[d][i] = dd[d];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) a.u[k][i] = uu[k];
+                    a.flags[i] = fl;
                 }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) a.u[k][i] = uu[k];
-                a.flags[i] = fl;
             }
-            if (a.pidin != a.pid) a.pid[i] = pid;
+            if (a.pidin != a.pid && (!FUSE || stp == 0)) a.pid[i] = pid;
         }
         __syncthreads();  // the previous tile's slots are no longer read
 #pragma unroll
@@ -345,14 +355,25 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
             if (fin) {
                 if (fail) nfl |= GCB_FLAG_GCAFAIL;
                 if (ncv) nfl |= GCB_FLAG_NONCONV;
+                if (FUSE) {
 #pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    reinterpret_cast<PosT *>(a.x[d])[gi] = xn[d];
-                    if (PM) a.xlo[d][gi] = xln[d];
-                    a.dxp[d][gi] = disp[d];
+                    for (int d = 0; d < ND; ++d) {
+                        s_x[d][sl] = xn[d];
+                        if (PM) s_xl[d][sl] = xln[d];
+                        s_d[d][sl] = disp[d];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) s_u[k][sl] = us[k];
+                } else {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        reinterpret_cast<PosT *>(a.x[d])[gi] = xn[d];
+                        if (PM) a.xlo[d][gi] = xln[d];
+                        a.dxp[d][gi] = disp[d];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) a.u[k][gi] = us[k];
                 }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) a.u[k][gi] = us[k];
                 if (done) ++ng; else ++nb;
                 if (Sprev && !Snew) ++tg;
                 if (!Sprev && Snew) ++tb;
@@ -367,17 +388,33 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
                 // is a sorted copy rather than the output arrays themselves)
                 nfl |= GCB_FLAG_NONFINITE;
                 ++nf;
+                if (!FUSE) {
 #pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    reinterpret_cast<PosT *>(a.x[d])[gi] = s_x[d][sl];
-                    if (PM) a.xlo[d][gi] = s_xl[d][sl];
-                    a.dxp[d][gi] = s_d[d][sl];
+                    for (int d = 0; d < ND; ++d) {
+                        reinterpret_cast<PosT *>(a.x[d])[gi] = s_x[d][sl];
+                        if (PM) a.xlo[d][gi] = s_xl[d][sl];
+                        a.dxp[d][gi] = s_d[d][sl];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) a.u[k][gi] = s_u[k][sl];
                 }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) a.u[k][gi] = s_u[k][sl];
             }
-            a.flags[gi] = nfl;
+            if (FUSE) s_fl[sl] = nfl; else a.flags[gi] = nfl;
         }
+        if (FUSE) __syncthreads();   // the slots hold this step's output
+      }
+      if (FUSE && valid) {
+          // the tile's state after its nsteps steps, coalesced
+#pragma unroll
+          for (int d = 0; d < ND; ++d) {
+              reinterpret_cast<PosT *>(a.x[d])[i] = s_x[d][tid];
+              if (PM) a.xlo[d][i] = s_xl[d][tid];
+              a.dxp[d][i] = s_d[d][tid];
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k) a.u[k][i] = s_u[k][tid];
+          a.flags[i] = s_fl[tid];
+      }
     }
 
     // block reduction of the counters
@@ -452,10 +489,11 @@ static void fill_args(PushArgs<R> &a, const gcb_particles *p, const gcb_particle
     a.f_E = (R)prm->f_E;
     a.c2 = (R)(prm->c * prm->c);
     a.force = prm->force;
+    a.nsteps = 1;
     a.stats = stats;
 }
 
-template <typename R, int ND, int PM, int GM>
+template <typename R, int ND, int PM, int GM, bool FUSE>
 static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
 {
     static int grid_cache[64] = {0};
@@ -468,7 +506,7 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     if (grid == 0) {
         int nsm = 0, occ = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM>, Tile<R>::n, 0) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM, FUSE>, Tile<R>::n, 0) !=
                 cudaSuccess) {
             set_error("occupancy query failed: %s", cudaGetErrorString(cudaGetLastError()));
             return GCB_ECUDA;
@@ -480,7 +518,7 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     int64_t ntiles = (a.np + TPB - 1) / TPB;
     if (ntiles == 0) return GCB_OK;
     int nb = (int)(ntiles < grid ? ntiles : grid);
-    k_push_sr<R, ND, PM, GM><<<nb, TPB, 0, st>>>(a);
+    k_push_sr<R, ND, PM, GM, FUSE><<<nb, TPB, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));
@@ -489,16 +527,27 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     return GCB_OK;
 }
 
+template <typename R, int PM, bool FUSE>
+static gcb_status dispatch_dims(const PushArgs<R> &a, const gcb_grid *g, const gcb_params *prm,
+                                cudaStream_t st)
+{
+    const bool grid_grad = prm->grad_mode == GCB_GRAD_GRID;
+    if (g->ndim == 2)
+        return grid_grad ? launch_push<R, 2, PM, 2, FUSE>(a, st) : launch_push<R, 2, PM, 1, FUSE>(a, st);
+    return grid_grad ? launch_push<R, 3, PM, 2, FUSE>(a, st) : launch_push<R, 3, PM, 1, FUSE>(a, st);
+}
+
+// nsteps > 1: that many steps in one launch (test-particle mode)
 template <typename R, int PM>
 static gcb_status dispatch_push(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
-                                const gcb_params *prm, cudaStream_t st, unsigned long long *stats)
+                                const gcb_params *prm, cudaStream_t st, unsigned long long *stats,
+                                int nsteps)
 {
     PushArgs<R> a;
     fill_args<R>(a, p, in, g, prm, stats);
-    const bool grid_grad = prm->grad_mode == GCB_GRAD_GRID;
-    if (g->ndim == 2)
-        return grid_grad ? launch_push<R, 2, PM, 2>(a, st) : launch_push<R, 2, PM, 1>(a, st);
-    return grid_grad ? launch_push<R, 3, PM, 2>(a, st) : launch_push<R, 3, PM, 1>(a, st);
+    if (nsteps <= 1) return dispatch_dims<R, PM, false>(a, g, prm, st);
+    a.nsteps = nsteps;
+    return dispatch_dims<R, PM, true>(a, g, prm, st);
 }
 
 }  // namespace gcb

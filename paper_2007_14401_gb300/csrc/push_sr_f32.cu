@@ -5,10 +5,12 @@
 namespace gcb {
 
 gcb_status push_step_f32(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
-                         const gcb_params *prm, cudaStream_t st, unsigned long long *stats)
+                         const gcb_params *prm, cudaStream_t st, unsigned long long *stats,
+                         int nsteps)
 {
-    if (p->pos_mode == GCB_POS_F32PAIR) return dispatch_push<float, 1>(p, in, g, prm, st, stats);
-    return dispatch_push<float, 0>(p, in, g, prm, st, stats);
+    if (p->pos_mode == GCB_POS_F32PAIR)
+        return dispatch_push<float, 1>(p, in, g, prm, st, stats, nsteps);
+    return dispatch_push<float, 0>(p, in, g, prm, st, stats, nsteps);
 }
 
 }  // namespace gcb

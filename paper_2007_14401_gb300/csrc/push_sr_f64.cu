@@ -4,9 +4,10 @@
 namespace gcb {
 
 gcb_status push_step_f64(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
-                         const gcb_params *prm, cudaStream_t st, unsigned long long *stats)
+                         const gcb_params *prm, cudaStream_t st, unsigned long long *stats,
+                         int nsteps)
 {
-    return dispatch_push<double, 0>(p, in, g, prm, st, stats);
+    return dispatch_push<double, 0>(p, in, g, prm, st, stats, nsteps);
 }
 
 }  // namespace gcb

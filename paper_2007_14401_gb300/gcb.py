@@ -44,7 +44,7 @@ class GcbParams(C.Structure):
                 ("force", C.c_int32), ("gca_max_iter", C.c_int32),
                 ("gca_fixed_iters", C.c_int32), ("gca_tol", C.c_double),
                 ("sort_every", C.c_int32), ("sort_tile", C.c_int32 * 3),
-                ("step_index", C.c_int64)]
+                ("step_index", C.c_int64), ("fuse_steps", C.c_int32)]
 
 
 class GcbStats(C.Structure):
@@ -337,7 +337,8 @@ def make_params(p: dict, **over) -> GcbParams:
                      int(q.get("mu_mode", 0)), int(q.get("grad_mode", 0)), int(q.get("force", 0)),
                      int(q.get("gca_max_iter", 16)), int(q.get("gca_fixed_iters", 0)),
                      float(q.get("gca_tol", 1e-7)), int(q.get("sort_every", 0)),
-                     (C.c_int32 * 3)(*tile[:3]), int(q.get("step_index", 0)))
+                     (C.c_int32 * 3)(*tile[:3]), int(q.get("step_index", 0)),
+                     int(q.get("fuse_steps", 0)))
 
 
 class Workspace:
