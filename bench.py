@@ -124,7 +124,8 @@ def _gen_adjoint(n, seed):
 ADJ_STEPS, ADJ_CKPT, ADJ_FIXED_ITERS = 256, 16, 6
 ADJOINT = dict(gen=_gen_adjoint, n=1 << 20,
                desc="adjoint: 2D double Harris + GEM + 64 modes at 512x256, {n} particles, "
-                    f"{ADJ_STEPS} steps, checkpoints every {ADJ_CKPT}, mixed FP32 forward + "
+                    f"{ADJ_STEPS} steps, checkpoints every {ADJ_CKPT} (particles sorted by cell "
+                    "at each), mixed FP32 forward + "
                     "FP32 adjoint, FP64 node accumulators; L = mean final kinetic energy, "
                     "gradients w.r.t. the 64 mode amplitudes and all initial states")
 
@@ -586,13 +587,14 @@ def run_adjoint(args):
     amps_d = torch.tensor(amps, dtype=torch.float64, device="cuda")
     G.grid_combine(grid, base_rec, pat_rec, amps_d)
     init = G.State.from_numpy(st, precision="mixed", pos_mode="pair")
-    gp = G.make_params(p, gca_fixed_iters=ADJ_FIXED_ITERS)
+    # checkpoints sorted by cell: the segments run on cell-ordered particles
+    gp = G.make_params(p, gca_fixed_iters=ADJ_FIXED_ITERS, sort_every=ADJ_CKPT, sort_tile=(1, 1))
     n = init.n
     cur = init.clone()
     lam = torch.empty((7, n), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    aws = G.AdjointWorkspace(cur, grid, ADJ_STEPS, ADJ_CKPT)
+    aws = G.AdjointWorkspace(cur, grid, ADJ_STEPS, ADJ_CKPT, gp)
 
     def forward():
         # the forward pass stores the checkpoints the reverse sweep starts from

@@ -237,17 +237,26 @@ enum { GCB_ADJ_REVERSE = 0, GCB_ADJ_TANGENT = 1 };
 /* or-ed into method: the checkpoints are already in ws (gcb_push_sr_ckpt) */
 #define GCB_ADJ_HAVE_CKPT 0x100
 
-size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, int n_steps,
-                                   int ckpt_every);
+/* 0 on invalid arguments.  With prm->sort_every > 0 the workspace also holds
+ * the sort's scratch, one int32 permutation per checkpoint and scratch copies
+ * of the adjoint arrays (see gcb_adjoint_sr). */
+size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g,
+                                   const gcb_params *prm, int n_steps, int ckpt_every);
 
 /*
  *   p0         : initial state (device arrays, read only; FP64 or mixed
  *                layout as for gcb_push_sr, ndim 2).
  *   method     : GCB_ADJ_REVERSE or GCB_ADJ_TANGENT, optionally or-ed with
  *                GCB_ADJ_HAVE_CKPT (see gcb_push_sr_ckpt).
- *   g, prm     : as for gcb_push_sr; needs g->has_grad and grad_mode GRID;
- *                sorting is not applied.  Use gca_fixed_iters > 0 so every
- *                particle-step has the same iteration count as the forward.
+ *   g, prm     : as for gcb_push_sr; needs g->has_grad and grad_mode GRID.
+ *                prm->sort_every > 0: the particles are sorted by cell (tiles
+ *                of prm->sort_tile) at every checkpoint, the start included,
+ *                so that the segments run on cell-ordered particles; lam and
+ *                the state keep the caller's order at the call's boundaries
+ *                (the adjoint is permuted with the particles inside).  The
+ *                pushes between checkpoints do not sort.  Use
+ *                gca_fixed_iters > 0 so every particle-step has the same
+ *                iteration count as the forward.
  *   lam[7]     : device arrays of n elements of the momentum type, in the
  *                order x0 x1 u0 u1 u2 dxp0 dxp1: on entry dL/d(final state),
  *                on return dL/d(initial state).
@@ -261,8 +270,9 @@ gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_
 
 /*
  * The forward pass for a later gcb_adjoint_sr: n_steps pushes of p in place
- * (as gcb_push_sr without sorting) that also store, in the adjoint workspace
- * ws, the initial state and every ckpt_every-th state.  gcb_adjoint_sr with
+ * that also store, in the adjoint workspace ws, the initial state and every
+ * ckpt_every-th state (sorted by cell first when prm->sort_every > 0; p then
+ * runs in cell order and is returned in its original order).  gcb_adjoint_sr with
  * method | GCB_ADJ_HAVE_CKPT on the same ws, the same n, layout, n_steps and
  * ckpt_every then starts from those checkpoints instead of running its own
  * forward pass (its p0 argument then only describes the layout; the caller

@@ -493,15 +493,148 @@ gcb_status copy_state(const gcb_particles *dst, const gcb_particles *src, int nd
 
 }  // namespace
 
+// Layout of the adjoint workspace (256-byte aligned sections):
+//   counters | checkpoint states (nck) | segment states (ckpt_every - 1) |
+//   2 scratch states | and with sorting (prm->sort_every > 0): the sort's
+//   own workspace | the sort's inverse permutation at each checkpoint |
+//   2 composed orders | 7 scratch adjoint arrays | a scratch id array.
+struct AdjLayout {
+    int nck;
+    size_t S;                   // bytes of one state set
+    size_t ck, seg, tmp;        // offsets of the state sets
+    bool sort;
+    size_t sortws, sortws_bytes, inv, ordA, ordB, lamt, pidt;
+    size_t total;
+};
+
+static bool adj_layout(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                       int n_steps, int ckpt_every, AdjLayout &L)
+{
+    L.nck = (n_steps + ckpt_every - 1) / ckpt_every;
+    L.S = state_set_bytes(p, g->ndim);
+    size_t o = kStatsBytes;
+    L.ck = o;
+    o += (size_t)L.nck * L.S;
+    L.seg = o;
+    o += (size_t)(ckpt_every - 1) * L.S;
+    L.tmp = o;
+    o += 2 * L.S;
+    L.sort = prm && prm->sort_every > 0 && p->n > 0;
+    L.sortws = L.sortws_bytes = L.inv = L.ordA = L.ordB = L.lamt = L.pidt = 0;
+    if (L.sort) {
+        SortPlan pl;
+        if (!sort_plan(p, g, prm, pl)) return false;
+        const size_t n = (size_t)p->n, me = p->mom_dtype == GCB_F64 ? 8 : 4;
+        L.sortws = o;
+        L.sortws_bytes = a256(pl.total);
+        o += L.sortws_bytes;
+        L.inv = o;
+        o += (size_t)L.nck * a256(4 * n);
+        L.ordA = o;
+        o += a256(4 * n);
+        L.ordB = o;
+        o += a256(4 * n);
+        L.lamt = o;
+        o += 7 * a256(me * n);
+        L.pidt = o;
+        o += a256(8 * n);
+    }
+    L.total = o;
+    return true;
+}
+
+// the caller-visible arrays of a particle set (with ids when present)
+static int particle_arrays(const gcb_particles *p, int nd, void **arr, int *es)
+{
+    const int pe = p->pos_mode == GCB_POS_F64 ? 8 : 4, me = p->mom_dtype == GCB_F64 ? 8 : 4;
+    int k = 0;
+    for (int d = 0; d < nd; ++d) { arr[k] = p->x[d]; es[k++] = pe; }
+    if (p->pos_mode == GCB_POS_F32PAIR)
+        for (int d = 0; d < nd; ++d) { arr[k] = p->x_lo[d]; es[k++] = 4; }
+    for (int c = 0; c < 3; ++c) { arr[k] = p->u[c]; es[k++] = me; }
+    for (int d = 0; d < nd; ++d) { arr[k] = p->dxp[d]; es[k++] = me; }
+    arr[k] = p->flags;
+    es[k++] = 1;
+    if (p->pid) { arr[k] = p->pid; es[k++] = 8; }
+    return k;
+}
+
+// Sort `cur` by cell into the sort workspace, store the sorted state as
+// checkpoint c and the sort's inverse permutation (new index -> old index)
+// as inv_c; `q` is the sorted copy's view.
+static gcb_status sort_checkpoint(const gcb_particles *cur, const gcb_grid *g, const gcb_params *prm,
+                                  const AdjLayout &L, uint8_t *w, int c, cudaStream_t st,
+                                  gcb_particles &q)
+{
+    SortPlan pl;
+    SortedView v;
+    gcb_status s = sort_step(cur, g, prm, st, w + L.sortws, L.sortws_bytes, q, pl, v);
+    if (s != GCB_OK) return s;
+    const size_t n4 = 4 * (size_t)cur->n;
+    if (cudaMemcpyAsync(w + L.inv + (size_t)c * a256(n4), w + L.sortws + pl.off_inv, n4,
+                        cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        set_error("cudaMemcpyAsync: %s", cudaGetErrorString(cudaGetLastError()));
+        return GCB_ECUDA;
+    }
+    gcb_particles ckv = state_view(cur, g->ndim, w + L.ck + (size_t)c * L.S);
+    return copy_state(&ckv, &q, g->ndim, st);
+}
+
+// order[j] = original index of the particle at position j of checkpoint c's
+// order: inv_0 composed with inv_1 .. inv_c.  Returns the buffer holding it.
+static int32_t *compose_order(int64_t n, const AdjLayout &L, uint8_t *w, int c, cudaStream_t st,
+                              gcb_status &s)
+{
+    const size_t n4 = 4 * (size_t)n;
+    int32_t *cur = (int32_t *)(w + L.ordA), *nxt = (int32_t *)(w + L.ordB);
+    s = GCB_OK;
+    if (cudaMemcpyAsync(cur, w + L.inv, n4, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        set_error("cudaMemcpyAsync: %s", cudaGetErrorString(cudaGetLastError()));
+        s = GCB_ECUDA;
+        return nullptr;
+    }
+    for (int k = 1; k <= c; ++k) {
+        // nxt[j] = cur[inv_k[j]]
+        void *dst[1] = {nxt};
+        const void *src[1] = {cur};
+        const int es[1] = {4};
+        s = permute_arrays(n, 1, dst, src, es, (const int32_t *)(w + L.inv + (size_t)k * a256(n4)),
+                           false, st);
+        if (s != GCB_OK) return nullptr;
+        int32_t *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    return cur;
+}
+
+// permute the 7 adjoint arrays through the scratch arrays: lam[j] =
+// lam[idx[j]] (gather) or lam[idx[j]] = lam[j] (scatter)
+static gcb_status permute_lam(int64_t n, int me, void *const *lam, const AdjLayout &L, uint8_t *w,
+                              const int32_t *idx, bool scatter, cudaStream_t st)
+{
+    void *tmp[7];
+    int es[7];
+    for (int k = 0; k < 7; ++k) {
+        tmp[k] = w + L.lamt + (size_t)k * a256((size_t)me * n);
+        es[k] = me;
+        if (cudaMemcpyAsync(tmp[k], lam[k], (size_t)me * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            set_error("cudaMemcpyAsync: %s", cudaGetErrorString(cudaGetLastError()));
+            return GCB_ECUDA;
+        }
+    }
+    return permute_arrays(n, 7, (void *const *)lam, (const void *const *)tmp, es, idx, scatter, st);
+}
+
 extern "C" {
 
-size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g, int n_steps,
-                                   int ckpt_every)
+size_t gcb_adjoint_workspace_bytes(const gcb_particles *p, const gcb_grid *g,
+                                   const gcb_params *prm, int n_steps, int ckpt_every)
 {
     if (!p || !g || n_steps < 1 || ckpt_every < 1 || p->n < 0) return 0;
-    const int nck = (n_steps + ckpt_every - 1) / ckpt_every;
-    const size_t S = state_set_bytes(p, g->ndim);
-    return kStatsBytes + (size_t)(nck + (ckpt_every - 1) + 2) * S;
+    AdjLayout L;
+    if (!adj_layout(p, g, prm, n_steps, ckpt_every, L)) return 0;
+    return L.total;
 }
 
 }  // extern "C"
@@ -521,7 +654,9 @@ static gcb_status check_adjoint(const gcb_particles *p, const gcb_grid *g, const
         set_error("the adjoint records at most %d fixed-point iterations per step", GCB_ADJOINT_MAX_ITER);
         return GCB_EUNSUPPORTED;
     }
-    const size_t need = gcb_adjoint_workspace_bytes(p, g, n_steps, ckpt_every);
+    if (p->n >= (int64_t(1) << 31)) { set_error("the adjoint needs n < 2^31"); return GCB_EUNSUPPORTED; }
+    const size_t need = gcb_adjoint_workspace_bytes(p, g, prm, n_steps, ckpt_every);
+    if (need == 0) { set_error("too many sort tiles"); return GCB_EUNSUPPORTED; }
     if (!ws || !aligned(ws, 256)) { set_error("workspace NULL or not 256-byte aligned"); return GCB_EINVAL; }
     if (ws_bytes < need) { set_error("workspace too small (%zu < %zu bytes)", ws_bytes, need); return GCB_ENOMEM; }
     return GCB_OK;
@@ -538,28 +673,56 @@ gcb_status gcb_push_sr_ckpt(const gcb_particles *p, const gcb_grid *g, const gcb
     if (s != GCB_OK) return s;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     gcb_params prm = *prm0;
-    prm.sort_every = 0;
+    prm.sort_every = 0;          // the pushes themselves do not sort
+    prm.fuse_steps = 0;
     const int nd = g->ndim;
-    const int nck = (n_steps + ckpt_every - 1) / ckpt_every;
-    const size_t S = state_set_bytes(p, nd);
+    AdjLayout L;
+    adj_layout(p, g, prm0, n_steps, ckpt_every, L);
+    uint8_t *w = (uint8_t *)ws;
     unsigned long long *stats = (unsigned long long *)ws;
-    uint8_t *ck = (uint8_t *)ws + kStatsBytes;
     if (cudaMemsetAsync(stats, 0, kStatsBytes, st) != cudaSuccess) {
         set_error("cudaMemsetAsync: %s", cudaGetErrorString(cudaGetLastError()));
         return GCB_ECUDA;
     }
     if (p->n > 0) {
         const bool fp64 = p->mom_dtype == GCB_F64;
-        gcb_particles c = state_view(p, nd, ck);
-        if ((s = copy_state(&c, p, nd, st)) != GCB_OK) return s;
-        for (int k = 0; k < n_steps; ++k) {
-            s = fp64 ? push_step_f64(p, p, g, &prm, st, stats) : push_step_f32(p, p, g, &prm, st, stats);
-            if (s != GCB_OK) return s;
-            const int kc = (k + 1) / ckpt_every;
-            if ((k + 1) % ckpt_every == 0 && kc < nck) {
-                c = state_view(p, nd, ck + (size_t)kc * S);
-                if ((s = copy_state(&c, p, nd, st)) != GCB_OK) return s;
+        auto step = [&](const gcb_particles *in) {
+            return fp64 ? push_step_f64(p, in, g, &prm, st, stats) : push_step_f32(p, in, g, &prm, st, stats);
+        };
+        for (int c = 0; c < L.nck; ++c) {
+            const gcb_particles *in = p;
+            gcb_particles q;
+            if (L.sort) {
+                // checkpoint c is the state sorted by cell; the segment starts from it
+                if ((s = sort_checkpoint(p, g, prm0, L, w, c, st, q)) != GCB_OK) return s;
+                in = &q;
+            } else {
+                gcb_particles ckv = state_view(p, nd, w + L.ck + (size_t)c * L.S);
+                if ((s = copy_state(&ckv, p, nd, st)) != GCB_OK) return s;
             }
+            const int len = n_steps - c * ckpt_every < ckpt_every ? n_steps - c * ckpt_every : ckpt_every;
+            for (int j = 0; j < len; ++j)
+                if ((s = step(j == 0 ? in : p)) != GCB_OK) return s;
+        }
+        if (L.sort) {
+            // back to the caller's order: p[order[j]] = (sorted final state)[j]
+            int32_t *order = compose_order(p->n, L, w, L.nck - 1, st, s);
+            if (s != GCB_OK) return s;
+            gcb_particles t = state_view(p, nd, w + L.tmp);
+            if ((s = copy_state(&t, p, nd, st)) != GCB_OK) return s;
+            if (p->pid) {
+                t.pid = (int64_t *)(w + L.pidt);
+                if (cudaMemcpyAsync(t.pid, p->pid, 8 * (size_t)p->n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+                    set_error("cudaMemcpyAsync: %s", cudaGetErrorString(cudaGetLastError()));
+                    return GCB_ECUDA;
+                }
+            }
+            void *dst[16], *src[16];
+            int es[16];
+            const int na = particle_arrays(p, nd, dst, es);
+            particle_arrays(&t, nd, src, es);
+            if ((s = permute_arrays(p->n, na, dst, (const void *const *)src, es, order, true, st)) != GCB_OK)
+                return s;
         }
     }
     return read_stats(stats, st, out);
@@ -576,20 +739,20 @@ gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_
     method &= ~GCB_ADJ_HAVE_CKPT;
     if (method != GCB_ADJ_REVERSE && method != GCB_ADJ_TANGENT) { set_error("unknown adjoint method %d", method); return GCB_EINVAL; }
     if (!lam || !grad_rec || !aligned(grad_rec, 8)) { set_error("lam or grad_rec NULL"); return GCB_EINVAL; }
-    const size_t me = p0->mom_dtype == GCB_F64 ? 8 : 4;
+    const int me = p0->mom_dtype == GCB_F64 ? 8 : 4;
     for (int k = 0; k < 7; ++k)
         if (p0->n > 0 && (!lam[k] || !aligned(lam[k], me))) { set_error("lam[%d] NULL or misaligned", k); return GCB_EINVAL; }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     gcb_params prm = *prm0;
     prm.sort_every = 0;
+    prm.fuse_steps = 0;
     const int nd = g->ndim;
-    const int nck = (n_steps + ckpt_every - 1) / ckpt_every;
-    const size_t S = state_set_bytes(p0, nd);
+    AdjLayout L;
+    adj_layout(p0, g, prm0, n_steps, ckpt_every, L);
+    const size_t S = L.S;
     uint8_t *w = (uint8_t *)ws;
     unsigned long long *stats = (unsigned long long *)w;
-    uint8_t *ck = w + kStatsBytes;
-    uint8_t *seg = ck + (size_t)nck * S;
-    uint8_t *tmp = seg + (size_t)(ckpt_every - 1) * S;
+    uint8_t *ck = w + L.ck, *seg = w + L.seg, *tmp = w + L.tmp;
     const size_t nrec = (size_t)(g->n[0] * g->n[1] * g->n[2]) * 12;
     if (cudaMemsetAsync(grad_rec, 0, nrec * sizeof(double), st) != cudaSuccess ||
         cudaMemsetAsync(stats, 0, kStatsBytes, st) != cudaSuccess) {
@@ -601,22 +764,36 @@ gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_
     auto step = [&](const gcb_particles *out, const gcb_particles *in) {
         return fp64 ? push_step_f64(out, in, g, &prm, st, stats) : push_step_f32(out, in, g, &prm, st, stats);
     };
+    gcb_particles tA = state_view(p0, nd, tmp), tB = state_view(p0, nd, tmp + S);
     if (!have_ckpt) {
-        // forward: checkpoints every ckpt_every steps
-        gcb_particles c0 = state_view(p0, nd, ck);
-        if ((s = copy_state(&c0, p0, nd, st)) != GCB_OK) return s;
-        gcb_particles cur = c0;
-        gcb_particles tA = state_view(p0, nd, tmp), tB = state_view(p0, nd, tmp + S);
-        for (int k = 0; k < (nck - 1) * ckpt_every; ++k) {
-            const bool boundary = (k + 1) % ckpt_every == 0;
-            gcb_particles out = boundary ? state_view(p0, nd, ck + (size_t)((k + 1) / ckpt_every) * S)
-                                         : (cur.u[0] == tA.u[0] ? tB : tA);
-            if ((s = step(&out, &cur)) != GCB_OK) return s;
-            cur = out;
+        // forward: a checkpoint every ckpt_every steps (sorted by cell first
+        // when sorting); the last segment needs no forward here
+        gcb_particles cur = *p0;
+        for (int c = 0; c < L.nck; ++c) {
+            gcb_particles ckv = state_view(p0, nd, ck + (size_t)c * S);
+            if (L.sort) {
+                gcb_particles q;
+                if ((s = sort_checkpoint(&cur, g, prm0, L, w, c, st, q)) != GCB_OK) return s;
+            } else if ((s = copy_state(&ckv, &cur, nd, st)) != GCB_OK) {
+                return s;
+            }
+            if (c == L.nck - 1) break;
+            cur = ckv;
+            for (int j = 0; j < ckpt_every; ++j) {
+                gcb_particles out = (cur.u[0] == tA.u[0]) ? tB : tA;
+                if ((s = step(&out, &cur)) != GCB_OK) return s;
+                cur = out;
+            }
         }
     }
-    // backward over segments
-    for (int sg = nck - 1; sg >= 0; --sg) {
+    // backward over segments, the adjoint kept in the order of the segment's
+    // states (and handed from one checkpoint's order to the previous one's)
+    if (L.sort) {
+        int32_t *order = compose_order(p0->n, L, w, L.nck - 1, st, s);
+        if (s != GCB_OK) return s;
+        if ((s = permute_lam(p0->n, me, lam, L, w, order, false, st)) != GCB_OK) return s;
+    }
+    for (int sg = L.nck - 1; sg >= 0; --sg) {
         const int len = (n_steps - sg * ckpt_every) < ckpt_every ? n_steps - sg * ckpt_every : ckpt_every;
         std::vector<gcb_particles> states((size_t)len);
         states[0] = state_view(p0, nd, ck + (size_t)sg * S);
@@ -626,6 +803,10 @@ gcb_status gcb_adjoint_sr(const gcb_particles *p0, const gcb_grid *g, const gcb_
         }
         for (int j = len - 1; j >= 0; --j)
             if ((s = adjoint_step(&states[j], g, &prm, lam, grad_rec, method, st)) != GCB_OK) return s;
+        if (L.sort) {
+            const int32_t *inv = (const int32_t *)(w + L.inv + (size_t)sg * a256(4 * (size_t)p0->n));
+            if ((s = permute_lam(p0->n, me, lam, L, w, inv, true, st)) != GCB_OK) return s;
+        }
     }
     return GCB_OK;
 }

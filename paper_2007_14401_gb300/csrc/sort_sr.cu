@@ -263,6 +263,35 @@ __global__ void k_gather_copy(const GatherArgs a)
     }
 }
 
+// Element-wise permutation of up to 16 arrays: dst[j] = src[idx[j]]
+// (gather) or dst[idx[j]] = src[j] (scatter).
+struct PermArgs {
+    int64_t n;
+    int na;
+    const void *src[16];
+    void *dst[16];
+    int es[16];
+    const int32_t *idx;
+    int scatter;
+};
+
+__global__ void k_permute(const PermArgs a)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a.idx[j];
+        const int64_t from = a.scatter ? j : i, to = a.scatter ? i : j;
+#pragma unroll 1
+        for (int k = 0; k < a.na; ++k) {
+            switch (a.es[k]) {
+            case 1: ((uint8_t *)a.dst[k])[to] = ((const uint8_t *)a.src[k])[from]; break;
+            case 4: ((uint32_t *)a.dst[k])[to] = ((const uint32_t *)a.src[k])[from]; break;
+            default: ((uint64_t *)a.dst[k])[to] = ((const uint64_t *)a.src[k])[from]; break;
+            }
+        }
+    }
+}
+
 static int blocks_for(int64_t n, int tpb)
 {
     int64_t b = (n + tpb - 1) / tpb;
@@ -353,6 +382,30 @@ void sorted_particles(const gcb_particles *p, int ndim, const SortedView &v, gcb
     for (int d = 0; d < ndim; ++d) q.dxp[d] = v.arr[k++];
     q.flags = (uint8_t *)v.arr[k++];
     q.pid = (int64_t *)v.arr[k++];
+}
+
+gcb_status permute_arrays(int64_t n, int na, void *const *dst, const void *const *src,
+                          const int *es, const int32_t *idx, bool scatter, cudaStream_t st)
+{
+    if (n == 0 || na == 0) return GCB_OK;
+    if (na > 16) { set_error("permute_arrays: at most 16 arrays"); return GCB_EINVAL; }
+    PermArgs a;
+    a.n = n;
+    a.na = na;
+    for (int k = 0; k < na; ++k) {
+        a.src[k] = src[k];
+        a.dst[k] = dst[k];
+        a.es[k] = es[k];
+    }
+    a.idx = idx;
+    a.scatter = scatter ? 1 : 0;
+    k_permute<<<blocks_for(n, 256), 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("k_permute: %s", cudaGetErrorString(e));
+        return GCB_ECUDA;
+    }
+    return GCB_OK;
 }
 
 }  // namespace gcb

@@ -34,5 +34,9 @@ gcb_status sort_into_workspace(const gcb_particles *p, const gcb_grid *g, const 
 gcb_status copy_back(const gcb_particles *p, const gcb_grid *g, const SortPlan &pl,
                      const SortedView &v, cudaStream_t st);
 void sorted_particles(const gcb_particles *p, int ndim, const SortedView &v, gcb_particles &q);
+// dst[k][j] = src[k][idx[j]] (gather) or dst[k][idx[j]] = src[k][j] (scatter)
+// for na arrays of element sizes es[k] (1, 4 or 8 bytes); n elements each.
+gcb_status permute_arrays(int64_t n, int na, void *const *dst, const void *const *src,
+                          const int *es, const int32_t *idx, bool scatter, cudaStream_t st);
 
 }  // namespace gcb

@@ -99,7 +99,8 @@ def load_library(path: str | None = None):
     lib.gcb_push_sr_noalloc.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int,
                                         C.c_void_p, P(GcbStats)]
     lib.gcb_push_sr_noalloc.restype = C.c_int
-    lib.gcb_adjoint_workspace_bytes.argtypes = [P(GcbParticles), P(GcbGrid), C.c_int, C.c_int]
+    lib.gcb_adjoint_workspace_bytes.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int,
+                                                C.c_int]
     lib.gcb_adjoint_workspace_bytes.restype = C.c_size_t
     lib.gcb_adjoint_sr.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams), C.c_int, C.c_int,
                                    C.c_int, P(C.c_void_p), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -389,9 +390,11 @@ class AdjointWorkspace:
     """Device workspace of the adjoint (checkpoints and segment states) for a
     given state layout, grid, n_steps and checkpoint spacing."""
 
-    def __init__(self, state: State, grid: Grid, n_steps: int, ckpt_every: int = 16):
-        nb = _lib.gcb_adjoint_workspace_bytes(C.byref(state.s), C.byref(grid.s), int(n_steps),
-                                              int(ckpt_every))
+    def __init__(self, state: State, grid: Grid, n_steps: int, ckpt_every: int = 16,
+                 params: GcbParams | None = None):
+        nb = _lib.gcb_adjoint_workspace_bytes(C.byref(state.s), C.byref(grid.s),
+                                              C.byref(params) if params is not None else None,
+                                              int(n_steps), int(ckpt_every))
         if nb == 0:
             raise GcbError("gcb_adjoint_workspace_bytes: invalid arguments")
         self.buf = torch.empty(nb, dtype=torch.uint8, device=state.u.device)
@@ -426,7 +429,7 @@ def adjoint(state: State, grid: Grid, params: GcbParams, n_steps: int, lam: torc
     A ``workspace`` filled by push_ckpt supplies the checkpoints (and its
     n_steps / ckpt_every must match); otherwise the forward is rerun here."""
     if workspace is None:
-        workspace = AdjointWorkspace(state, grid, n_steps, ckpt_every)
+        workspace = AdjointWorkspace(state, grid, n_steps, ckpt_every, params)
     elif (workspace.n_steps, workspace.ckpt_every) != (int(n_steps), int(ckpt_every)):
         raise GcbError("workspace was sized for another n_steps / ckpt_every")
     ws, nb = workspace.buf, workspace.buf.numel()
@@ -482,12 +485,17 @@ class ModePush(torch.autograd.Function):
         ctx.cfg = cfg
         if cfg.get("ckpt_in_forward", True):
             # the forward stores the checkpoints; the backward starts from them
-            ctx.ws = AdjointWorkspace(st, grid, cfg["n_steps"], cfg.get("ckpt_every", 16))
+            ctx.ws = AdjointWorkspace(st, grid, cfg["n_steps"], cfg.get("ckpt_every", 16),
+                                      cfg["params"])
             push_ckpt(st, grid, cfg["params"], cfg["n_steps"], ctx.ws)
             ctx.init = st          # layout only: the initial state is checkpoint 0
         else:
             ctx.ws, ctx.init = None, st.clone()
-            push(st, grid, cfg["params"], cfg["n_steps"], stats=False)
+            # outputs must stay in the inputs' order: no sorting in this push
+            # (the adjoint sorts at its checkpoints and restores the order)
+            fwd = GcbParams.from_buffer_copy(cfg["params"])
+            fwd.sort_every = 0
+            push(st, grid, fwd, cfg["n_steps"], stats=False)
         return st.x_f64(), st.u.clone(), st.dxp.clone()
 
     @staticmethod

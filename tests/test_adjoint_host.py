@@ -30,12 +30,16 @@ def test_adjoint_workspace_bytes():
     from paper_2007_14401_gb300 import gcb
     lib = gcb.lib()
 
-    def ws(n, steps, ck, pos_mode=gcb.POS_F64, mom=gcb.F64):
+    def ws(n, steps, ck, pos_mode=gcb.POS_F64, mom=gcb.F64, prm=None):
         p = gcb.GcbParticles()
         p.n, p.ndim, p.pos_mode, p.mom_dtype = n, 2, pos_mode, mom
         g = gcb.GcbGrid()
         g.ndim = 2
-        return lib.gcb_adjoint_workspace_bytes(C.byref(p), C.byref(g), steps, ck)
+        g.n = (C.c_int64 * 3)(64, 32, 1)
+        g.dx = (C.c_double * 3)(1.0, 1.0, 1.0)
+        return lib.gcb_adjoint_workspace_bytes(C.byref(p), C.byref(g),
+                                               C.byref(prm) if prm is not None else None,
+                                               steps, ck)
 
     # one state set of n = 1024 FP64 particles: 2 x + 3 u + 2 dxp (8 B) + flags
     S = 7 * 8 * 1024 + 1024
@@ -48,3 +52,9 @@ def test_adjoint_workspace_bytes():
     # mixed: FP32 pairs (hi, lo) and FP32 momenta
     Sm = 2 * 4 * 1024 * 2 + 5 * 4 * 1024 + 1024
     assert ws(1024, 16, 4, gcb.POS_F32PAIR, gcb.F32) == 256 + (4 + 3 + 2) * Sm
+    # sorting at the checkpoints adds the sort's scratch, one int32
+    # permutation per checkpoint, two orders, 7 adjoint copies and an id copy
+    srt = gcb.make_params(dict(dt=1.0, qm=(-1.0,)), sort_every=4, sort_tile=(1, 1))
+    extra = ws(1024, 16, 4, prm=srt) - ws(1024, 16, 4)
+    assert extra > (4 + 2) * 4 * 1024 + 7 * 8 * 1024 + 8 * 1024
+    assert ws(1024, 16, 4, prm=gcb.make_params(dict(dt=1.0, qm=(-1.0,)))) == ws(1024, 16, 4)

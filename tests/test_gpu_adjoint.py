@@ -115,7 +115,8 @@ def rel_err(got, ref, scale):
     return np.maximum(np.abs(got - ref) - FD_FLOOR, 0.0) / (np.abs(ref) + scale)
 
 
-def run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5, method="reverse", ckpt_fwd=True):
+def run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5, method="reverse", ckpt_fwd=True,
+            sort=0, outputs=False):
     """Forward + adjoint through ModePush; returns (state grads (7, n), mode grads)."""
     import torch
     base, pats, amps, st0, params, w = case
@@ -129,7 +130,8 @@ def run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5, method="reverse", c
     d0 = torch.tensor(st0["dxp"], dtype=mdt, device=dev, requires_grad=True)
     a = torch.tensor(amps, dtype=torch.float64, device=dev, requires_grad=True)
     cfg = dict(grid=grid, base=base_rec, pat=pat_rec,
-               params=G.make_params(params, **FIXED), n_steps=N_STEPS, ckpt_every=ckpt_every,
+               params=G.make_params(params, sort_every=sort, sort_tile=(1, 1), **FIXED),
+               n_steps=N_STEPS, ckpt_every=ckpt_every,
                flags=torch.tensor(st0["flags"], device=dev), precision=precision,
                pos_mode=pos_mode, method=method, ckpt_in_forward=ckpt_fwd)
     x, u, dxp = G.ModePush.apply(x0, u0, d0, a, cfg)
@@ -140,6 +142,8 @@ def run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5, method="reverse", c
         + (wt["dxp"] * dxp.double()).sum()
     L.backward()
     gs = torch.cat([x0.grad, u0.grad.double(), d0.grad.double()]).cpu().numpy()
+    if outputs:
+        return gs, a.grad.cpu().numpy(), [t.detach().double().cpu().numpy() for t in (x, u, dxp)]
     return gs, a.grad.cpu().numpy()
 
 
@@ -195,6 +199,25 @@ def test_adjoint_checkpoint_interval_invariance(G, case):
         got = run_gpu(G, case, "fp64", "f64", "f64", ckpt_every=ck, ckpt_fwd=fwd)
         np.testing.assert_allclose(got[0], ref[0], rtol=0, atol=1e-12 * np.abs(ref[0]).max())
         np.testing.assert_allclose(got[1], ref[1], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("precision,pos_mode,gdt", [("fp64", "f64", "f64"),
+                                                     ("mixed", "pair", "f32")])
+@pytest.mark.parametrize("ckpt_fwd", [True, False])
+def test_sorted_checkpoints_change_nothing(G, case, precision, pos_mode, gdt, ckpt_fwd):
+    """Sorting the particles by cell at every checkpoint only reorders the
+    work: each particle's arithmetic is unchanged, so the forward outputs and
+    the state adjoint (returned in the caller's order) are identical bit for
+    bit, and the mode gradients equal to the rounding of the FP64 node
+    accumulation."""
+    ref = run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5, ckpt_fwd=ckpt_fwd,
+                  outputs=True)
+    got = run_gpu(G, case, precision, pos_mode, gdt, ckpt_every=5, ckpt_fwd=ckpt_fwd,
+                  sort=5, outputs=True)
+    for a, b in zip(got[2], ref[2]):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(got[0], ref[0])
+    np.testing.assert_allclose(got[1], ref[1], rtol=1e-9, atol=0)
 
 
 def test_reverse_and_tangent_agree_mixed(G, case):

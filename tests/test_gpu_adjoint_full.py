@@ -1,9 +1,10 @@
 """The adjoint at the size of the adjoint benchmark, checked on a sample.
 
 Launch configuration as timed: the 512 x 256 reconnection field with its 64
-modes, 2^20 particles, 256 steps, checkpoints every 16, FP32 forward and FP32
-adjoint with FP64 node accumulators, L = mean final kinetic energy over all
-particles.  The oracle cannot differentiate 2^20 particles, so the check runs
+modes, 2^20 particles, 256 steps, checkpoints every 16 with the particles
+sorted by cell at each, FP32 forward and FP32 adjoint with FP64 node
+accumulators, L = mean final kinetic energy over all particles.  The
+oracle cannot differentiate 2^20 particles, so the check runs
 on a sample of 1024 of them (every 1024th), by central differences of the
 FP64 oracle with h = 1e-6 (and h/2, to see where the map is smooth):
 
@@ -116,16 +117,19 @@ def run_full(G, problem, weights):
     pat_rec = torch.stack([G.Grid(q, dtype="f32").rec for q in pats]).contiguous()
     G.grid_combine(grid, base_rec, pat_rec, torch.tensor(amps))
     init = G.State.from_numpy(st, precision="mixed", pos_mode="pair")
-    gp = G.make_params(params, **FIXED)
+    # as the benchmark: particles sorted by cell at every checkpoint, the
+    # forward storing the checkpoints (it returns the caller's order)
+    gp = G.make_params(params, sort_every=CKPT, sort_tile=(1, 1), **FIXED)
     cur = init.clone()
-    G.push(cur, grid, gp, N_STEPS, stats=False)
+    aws = G.AdjointWorkspace(cur, grid, N_STEPS, CKPT, gp)
+    G.push_ckpt(cur, grid, gp, N_STEPS, aws)
     u = cur.u
     Gm = torch.sqrt(1.0 + (u * u).sum(0))
     w = torch.as_tensor(np.broadcast_to(weights, (N,)).astype(np.float32), device="cuda")
     lam = torch.zeros((7, N), dtype=torch.float32, device="cuda")
     fin = torch.isfinite(u).all(0)
     lam[2:5] = torch.where(fin, u / Gm * w, torch.zeros_like(u))
-    grad = G.adjoint(init, grid, gp, N_STEPS, lam, CKPT)
+    grad = G.adjoint(init, grid, gp, N_STEPS, lam, CKPT, workspace=aws)
     ga = G.grad_project(grid, grad, pat_rec)
     torch.cuda.synchronize()
     return u.double().cpu().numpy(), lam.double().cpu().numpy(), ga.cpu().numpy()
