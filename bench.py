@@ -557,12 +557,18 @@ def main():
 
 
 def adjoint_launches():
-    """Kernels of one forward + reverse sweep: ADJ_STEPS pushes (the forward
-    stores the checkpoints); in the sweep, per segment its recomputed pushes
-    and its adjoint steps, and the mode projection."""
+    """Kernels of one forward + reverse sweep.  Forward: a sort (6 kernels)
+    at each checkpoint, ADJ_STEPS pushes, then the composed order (one
+    permutation per later checkpoint) and the scatter back to the caller's
+    order.  Sweep: the composed order again and the gather of the adjoint
+    into it; per segment its recomputed pushes, its adjoint steps and the
+    adjoint's scatter to the previous checkpoint's order; the mode
+    projection."""
     nck = (ADJ_STEPS + ADJ_CKPT - 1) // ADJ_CKPT
     seg = [min(ADJ_CKPT, ADJ_STEPS - s * ADJ_CKPT) for s in range(nck)]
-    return ADJ_STEPS + sum(2 * L - 1 for L in seg) + 1
+    forward = 6 * nck + ADJ_STEPS + (nck - 1) + 1
+    sweep = (nck - 1) + 1 + sum((L - 1) + L + 1 for L in seg) + 1
+    return forward + sweep
 
 
 def run_adjoint(args):
