@@ -40,20 +40,25 @@ def test_exports_every_declared_symbol(G):
 
 
 def test_struct_layout_matches_header(G, tmp_path):
+    """Every descriptor the binding passes by pointer has the header's size
+    and field offsets (compiled with the host C compiler)."""
+    fields = [("gcb_grid", "rec", G.GcbGrid), ("gcb_grid", "stride", G.GcbGrid),
+              ("gcb_particles", "flags", G.GcbParticles), ("gcb_particles", "pid", G.GcbParticles),
+              ("gcb_params", "gca_tol", G.GcbParams), ("gcb_params", "step_index", G.GcbParams),
+              ("gcb_params", "fuse_steps", G.GcbParams), ("gcb_stats", "sum_ekin", G.GcbStats),
+              ("gcb_grid_ks", "dl", G.GcbGridKs), ("gcb_ks_params", "r_out", G.GcbKsParams)]
+    lines = "".join(f'printf("%zu %zu\\n", sizeof({t}), offsetof({t}, {f}));\n'
+                    for t, f, _ in fields)
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gcb.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n",'
-                   'sizeof(gcb_grid), offsetof(gcb_grid, rec), sizeof(gcb_particles),'
-                   'offsetof(gcb_particles, flags), sizeof(gcb_params),'
-                   'offsetof(gcb_params, gca_tol), sizeof(gcb_stats),'
-                   'offsetof(gcb_stats, sum_ekin)); return 0;}\n')
+                   "int main(void){\n" + lines + "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
-    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()))
-    want = [C.sizeof(G.GcbGrid), G.GcbGrid.rec.offset, C.sizeof(G.GcbParticles),
-            G.GcbParticles.flags.offset, C.sizeof(G.GcbParams), G.GcbParams.gca_tol.offset,
-            C.sizeof(G.GcbStats), G.GcbStats.sum_ekin.offset]
+    got = [tuple(map(int, ln.split()))
+           for ln in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n")
+           if ln.strip()]
+    want = [(C.sizeof(cls), getattr(cls, f).offset) for _, f, cls in fields]
     assert got == want
 
 
