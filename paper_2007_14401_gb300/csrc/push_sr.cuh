@@ -27,6 +27,10 @@ template <typename R>
 struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : GCB_TILE_F32; };
 
 // minimum resident blocks per SM requested from the register allocator
+// 1: tiles whose particles all take one branch skip the staging (see k_push_sr)
+#ifndef GCB_UNIFORM_TILES
+#define GCB_UNIFORM_TILES 1
+#endif
 #ifndef GCB_MIN_BLOCKS_F32
 #define GCB_MIN_BLOCKS_F32 4
 #endif
@@ -153,7 +157,6 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
     __shared__ R s_d[ND][TPB];
     __shared__ R s_F[NF][TPB];
     __shared__ uint8_t s_fl[TPB];
-    __shared__ uint8_t s_cls[TPB];
     __shared__ unsigned short s_perm[TPB];
     __shared__ int s_wc[2][NWARP];
     __shared__ unsigned long long s_acc[ST_COUNT];
@@ -239,104 +242,154 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
             }
             if (a.pidin != a.pid && (!FUSE || stp == 0)) a.pid[i] = pid;
         }
-        __syncthreads();  // the previous tile's slots are no longer read
+        // Tiles whose valid particles all take one branch (the common case in
+        // strongly magnetized runs) skip the compaction and the staging of
+        // the field: each thread advances its own particle.  The rest of the
+        // state is held in registers through phase 2 (REG: 2D, measured
+        // faster) or kept in the thread's slot and read where used (3D,
+        // whose kernels hold more live values and whose tiles are more often
+        // mixed, measured faster that way).
+        constexpr bool REG = (ND == 2);
+        int uni = 0;
+        if (GCB_UNIFORM_TILES) {
+            if (__syncthreads_and(!valid || cls == 0)) uni = 1;
+            else if (__syncthreads_and(!valid || cls == 1)) uni = 2;
+        }
+        bool work, isg;
+        int sl = tid;
+        if (uni) {
+            // the barrier of the vote has ended every read of the slots
+            if (!REG && valid) {
 #pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            if (valid) {
-                s_x[d][tid] = xs[d];
-                if (PM) s_xl[d][tid] = xl[d];
-                s_d[d][tid] = dd[d];
-                s_l[d][tid] = l[d];
-                s_ib[d][tid] = ib[d];
+                for (int d = 0; d < ND; ++d) {
+                    s_x[d][tid] = xs[d];
+                    if (PM) s_xl[d][tid] = xl[d];
+                    s_d[d][tid] = dd[d];
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s_u[k][tid] = uu[k];
             }
-        }
-        if (valid && cls != 2) {
+            if (!REG) s_fl[tid] = fl;
+            work = valid && cls != 2;
+            isg = uni == 1;
+        } else {
+            __syncthreads();  // the previous tile's slots are no longer read
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                s_F[k][tid] = F.E[k];
-                s_F[3 + k][tid] = F.B[k];
+            for (int d = 0; d < ND; ++d) {
+                if (valid) {
+                    s_x[d][tid] = xs[d];
+                    if (PM) s_xl[d][tid] = xl[d];
+                    s_d[d][tid] = dd[d];
+                    s_l[d][tid] = l[d];
+                    s_ib[d][tid] = ib[d];
+                }
             }
-            if (GM != 0) {
+            if (valid && cls != 2) {
 #pragma unroll
-                for (int ii = 0; ii < ND; ++ii)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) s_F[6 + 3 * ii + j][tid] = F.dB[ii][j];
-            }
-        }
-        if (valid) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) s_u[k][tid] = uu[k];
-        }
-        s_fl[tid] = fl;
-        s_cls[tid] = (uint8_t)cls;
-        const unsigned bgm = __ballot_sync(0xffffffffu, cls == 0);
-        const unsigned bbm = __ballot_sync(0xffffffffu, cls == 1);
-        if (lane == 0) {
-            s_wc[0][warp] = __popc(bgm);
-            s_wc[1][warp] = __popc(bbm);
-        }
-        __syncthreads();
-        int offG = 0, offB = 0, totG = 0, totB = 0;
-#pragma unroll
-        for (int w = 0; w < NWARP; ++w) {
-            int cg = s_wc[0][w], cb = s_wc[1][w];
-            if (w < warp) { offG += cg; offB += cb; }
-            totG += cg;
-            totB += cb;
-        }
-        const unsigned lt = (1u << lane) - 1u;
-        if (cls == 0) s_perm[offG + __popc(bgm & lt)] = (unsigned short)tid;
-        if (cls == 1) s_perm[totG + offB + __popc(bbm & lt)] = (unsigned short)tid;
-        __syncthreads();
-
-        // phase 2: advance slot perm[tid]
-        if (tid < totG + totB) {
-            const int sl = s_perm[tid];
-            const bool isg = tid < totG;
-            uint8_t f0 = s_fl[sl];
-            StepPar<R> sp = a.sp;
-            sp.qm = a.qm[(f0 >> GCB_SPECIES_SHIFT) & 3];
-            int ibs[ND];
-            R ls[ND], ds[ND], us[3], disp[ND];
-#pragma unroll
-            for (int d = 0; d < ND; ++d) { ibs[d] = s_ib[d][sl]; ls[d] = s_l[d][sl]; ds[d] = s_d[d][sl]; }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) us[k] = s_u[k][sl];
-            int it = 0;
-            bool ncv = false, fail = false;
-            bool done = false;
-            FieldPt<R, ND> F0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) { F0.E[k] = s_F[k][sl]; F0.B[k] = s_F[3 + k][sl]; }
-            if (isg) {
+                for (int k = 0; k < 3; ++k) {
+                    s_F[k][tid] = F.E[k];
+                    s_F[3 + k][tid] = F.B[k];
+                }
                 if (GM != 0) {
 #pragma unroll
                     for (int ii = 0; ii < ND; ++ii)
 #pragma unroll
-                        for (int j = 0; j < 3; ++j) F0.dB[ii][j] = s_F[6 + 3 * ii + j][sl];
+                        for (int j = 0; j < 3; ++j) s_F[6 + 3 * ii + j][tid] = F.dB[ii][j];
                 }
-                done = gca_step<R, ND, GM>(PlainGather<R, ND, GM>{a.g}, sp, ibs, ls, ds, F0, us,
+            }
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s_u[k][tid] = uu[k];
+            }
+            s_fl[tid] = fl;
+            const unsigned bgm = __ballot_sync(0xffffffffu, cls == 0);
+            const unsigned bbm = __ballot_sync(0xffffffffu, cls == 1);
+            if (lane == 0) {
+                s_wc[0][warp] = __popc(bgm);
+                s_wc[1][warp] = __popc(bbm);
+            }
+            __syncthreads();
+            int offG = 0, offB = 0, totG = 0, totB = 0;
+#pragma unroll
+            for (int w = 0; w < NWARP; ++w) {
+                int cg = s_wc[0][w], cb = s_wc[1][w];
+                if (w < warp) { offG += cg; offB += cb; }
+                totG += cg;
+                totB += cb;
+            }
+            const unsigned lt = (1u << lane) - 1u;
+            if (cls == 0) s_perm[offG + __popc(bgm & lt)] = (unsigned short)tid;
+            if (cls == 1) s_perm[totG + offB + __popc(bbm & lt)] = (unsigned short)tid;
+            __syncthreads();
+            // this thread advances slot perm[tid]: [GCA ..., Boris ...]
+            work = tid < totG + totB;
+            isg = tid < totG;
+            if (work) {
+                sl = s_perm[tid];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    ib[d] = s_ib[d][sl];
+                    l[d] = s_l[d][sl];
+                    if (REG) {
+                        xs[d] = s_x[d][sl];
+                        xl[d] = PM ? s_xl[d][sl] : 0.0f;
+                        dd[d] = s_d[d][sl];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    F.E[k] = s_F[k][sl];
+                    F.B[k] = s_F[3 + k][sl];
+                    if (REG) uu[k] = s_u[k][sl];
+                }
+                if (REG) fl = s_fl[sl];
+                if (isg && GM != 0) {
+#pragma unroll
+                    for (int ii = 0; ii < ND; ++ii)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) F.dB[ii][j] = s_F[6 + 3 * ii + j][sl];
+                }
+            }
+        }
+
+        // phase 2: advance the particle of slot sl (field, cell and offset in
+        // F, ib, l; the rest of its state in registers (REG) or in the slot)
+        if (work) {
+            const uint8_t f0 = REG ? fl : s_fl[sl];
+            StepPar<R> sp = a.sp;
+            sp.qm = a.qm[(f0 >> GCB_SPECIES_SHIFT) & 3];
+            R ds[ND], us[3], disp[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) ds[d] = REG ? dd[d] : s_d[d][sl];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) us[k] = REG ? uu[k] : s_u[k][sl];
+            int it = 0;
+            bool ncv = false, fail = false;
+            bool done = false;
+            if (isg) {
+                done = gca_step<R, ND, GM>(PlainGather<R, ND, GM>{a.g}, sp, ib, l, ds, F, us,
                                            disp, it, ncv);
                 if (!done) {
                     fail = true;
                     it = 0;
                     ncv = false;
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) us[k] = s_u[k][sl];
+                    for (int k = 0; k < 3; ++k) us[k] = REG ? uu[k] : s_u[k][sl];
                 }
             }
-            if (!done) boris<R, ND>(F0.E, F0.B, sp, us, disp);
+            if (!done) boris<R, ND>(F.E, F.B, sp, us, disp);
             // store: x^{n+1} = x^n + disp (wrapped), dxp = disp
             PosT xn[ND];
             float xln[ND];
             bool fin = true;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
+                const PosT x0 = REG ? xs[d] : s_x[d][sl];
                 if (PM == 0) {
-                    xn[d] = (PosT)wrap_f64((double)s_x[d][sl] + (double)disp[d], a.L[d]);
+                    xn[d] = (PosT)wrap_f64((double)x0 + (double)disp[d], a.L[d]);
                     xln[d] = 0.0f;
                 } else {
-                    float h = (float)s_x[d][sl], lo = s_xl[d][sl];
+                    float h = (float)x0, lo = REG ? xl[d] : s_xl[d][sl];
                     pair_add_wrap(h, lo, (float)disp[d], a.Lf[d]);
                     xn[d] = (PosT)h;
                     xln[d] = lo;
@@ -349,8 +402,8 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
             const int Snew = isg ? 0 : 1;
             uint8_t nfl = (uint8_t)((f0 & 0xC0) | (Sprev ? GCB_FLAG_SPREV : 0) | (Snew ? GCB_FLAG_S : 0));
             // the particle goes straight back to its own index in the output
-            // arrays (for an all-GCA or all-Boris tile slot == thread, so
-            // these stores are coalesced; otherwise L2 merges the tile)
+            // arrays (for a uniform tile, or an all-GCA or all-Boris one,
+            // slot == thread and these stores are coalesced)
             const int64_t gi = tile * TPB + sl;
             if (fin) {
                 if (fail) nfl |= GCB_FLAG_GCAFAIL;
@@ -385,18 +438,30 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
                 ek += (double)(u2 / (R(1) + sqrt(R(1) + u2)));
             } else {
                 // not advanced: the input state is kept (copied when the input
-                // is a sorted copy rather than the output arrays themselves)
+                // is a sorted copy rather than the output arrays themselves;
+                // fused, written to the slot, which a uniform 2D tile's first
+                // step has not staged)
                 nfl |= GCB_FLAG_NONFINITE;
                 ++nf;
-                if (!FUSE) {
 #pragma unroll
-                    for (int d = 0; d < ND; ++d) {
-                        reinterpret_cast<PosT *>(a.x[d])[gi] = s_x[d][sl];
-                        if (PM) a.xlo[d][gi] = s_xl[d][sl];
-                        a.dxp[d][gi] = s_d[d][sl];
+                for (int d = 0; d < ND; ++d) {
+                    const PosT x0 = REG ? xs[d] : s_x[d][sl];
+                    const float l0 = PM ? (REG ? xl[d] : s_xl[d][sl]) : 0.0f;
+                    const R d0 = REG ? dd[d] : s_d[d][sl];
+                    if (FUSE) {
+                        s_x[d][sl] = x0;
+                        if (PM) s_xl[d][sl] = l0;
+                        s_d[d][sl] = d0;
+                    } else {
+                        reinterpret_cast<PosT *>(a.x[d])[gi] = x0;
+                        if (PM) a.xlo[d][gi] = l0;
+                        a.dxp[d][gi] = d0;
                     }
+                }
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) a.u[k][gi] = s_u[k][sl];
+                for (int k = 0; k < 3; ++k) {
+                    const R u0 = REG ? uu[k] : s_u[k][sl];
+                    if (FUSE) s_u[k][sl] = u0; else a.u[k][gi] = u0;
                 }
             }
             if (FUSE) s_fl[sl] = nfl; else a.flags[gi] = nfl;
