@@ -297,7 +297,9 @@ def end_to_end(G, ds, grid, gp, ws, ks, step, args, barrier, stream, n, multi):
     def rows(t, a_, b_):
         return [t[a_:b_]] if t.dim() == 1 else [t[r, a_:b_] for r in range(t.shape[0])]
 
-    C = max(1, args.e2e_chunks)
+    # at most --e2e-chunks chunks of at least 2^21 particles (smaller chunks
+    # cost more in per-copy overhead than their overlap gains)
+    C = max(1, min(args.e2e_chunks, n >> 21))
     edges = [((n * c // C) // 256) * 256 for c in range(C)] + [n]
     spans = [(a_, b_) for a_, b_ in zip(edges[:-1], edges[1:]) if b_ > a_]
     views = [ds.view(a_, b_) for a_, b_ in spans]
