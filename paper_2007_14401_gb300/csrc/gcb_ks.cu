@@ -190,11 +190,11 @@ __device__ __forceinline__ void boris_local(const double E[3], const double B[3]
     for (int k = 0; k < 3; ++k) u[k] = fma(h, E[k], fma(sf, x[k], um[k]));
 }
 
+// (m: the metric at x, returned for reuse)
 template <typename FT>
 __device__ __forceinline__ void half_kick(const KsGrid<FT> &g, double a, double qm, double dt,
-                                          const double x[3], double u[3])
+                                          const double x[3], double u[3], Metric &m)
 {
-    Metric m;
     ks_metric(a, x[0], x[1], false, m);
     double D[3], B[3], Dh[3], Bh[3], uh[3];
     ks_gather(g, x[0], x[1], D, B);
@@ -234,12 +234,13 @@ __device__ __forceinline__ bool imr_done(const StepCfg &c, int iters, double res
 }
 
 // GREOM: half kick, implicit midpoint for (x, u) (no field inside), half kick.
+// (mfin: the metric at x^{n+1})
 template <typename FT>
 __device__ void greom_step(const KsGrid<FT> &g, const StepCfg &c, double qm, double x[3],
-                           double u[3], int &iters, bool &nonconv)
+                           double u[3], int &iters, bool &nonconv, Metric &mfin)
 {
     double up[3] = {u[0], u[1], u[2]};
-    half_kick(g, c.a, qm, c.dt, x, up);
+    half_kick(g, c.a, qm, c.dt, x, up, mfin);
     double xk[3] = {x[0], x[1], x[2]}, wk[3] = {up[0], up[1], up[2]};
     iters = 0;
     nonconv = false;
@@ -268,7 +269,7 @@ __device__ void greom_step(const KsGrid<FT> &g, const StepCfg &c, double qm, dou
         ++iters;
         if (imr_done(c, iters, res, nonconv)) break;
     }
-    half_kick(g, c.a, qm, c.dt, xk, wk);
+    half_kick(g, c.a, qm, c.dt, xk, wk, mfin);
 #pragma unroll
     for (int k = 0; k < 3; ++k) { x[k] = xk[k]; u[k] = wk[k]; }
 }
@@ -319,7 +320,7 @@ __device__ __forceinline__ double gr_perp2(const GFrame &F, const StepCfg &c, do
 template <typename FT>
 __device__ bool grgca_step(const KsGrid<FT> &g, const StepCfg &c, double qm, const GFrame &F0,
                            double R[3], double &upar, double mu, double uperp, const double bpg[3],
-                           int &iters, bool &nonconv)
+                           int &iters, bool &nonconv, GFrame &F1)
 {
     const double u1 = fma(0.5 * c.dt * F0.m.alpha * qm, F0.Dpar, upar);
     double Rk[3] = {R[0], R[1], R[2]}, wk = u1;
@@ -362,8 +363,7 @@ __device__ bool grgca_step(const KsGrid<FT> &g, const StepCfg &c, double qm, con
         if (imr_done(c, iters, res, nonconv)) break;
     }
     if (!okall) return false;
-    GFrame F1;
-    gr_frame(g, c.a, Rk, false, F1);
+    gr_frame(g, c.a, Rk, false, F1);   // also the reconstruction's frame
     if (!F1.ok) return false;
     upar = fma(0.5 * c.dt * F1.m.alpha * qm, F1.Dpar, wk);
 #pragma unroll
@@ -386,15 +386,19 @@ struct Args {
 
 // one coupled covariant step of one particle (Sec. 3.2); returns the branch
 // taken (0 GCA, 1 GREOM) and fills the flag bits
+// (mfin: the metric at the new position, before any pole reflection, which
+// leaves it unchanged: it depends on theta through sin^2 and cos^2 only)
 template <typename FT>
 __device__ int ks_particle(const KsGrid<FT> &g, const StepCfg &c, double qm, int S, const GFrame &F0,
-                           double x[3], double u[3], int &iters, bool &nonconv, bool &fail)
+                           double x[3], double u[3], int &iters, bool &nonconv, bool &fail,
+                           Metric &mfin)
 {
     fail = false;
     if (S == 0) {
         bool ok = F0.ok;
         double R[3] = {x[0], x[1], x[2]};
         double upar = 0.0, mu = 0.0, uperp = 0.0, bpg[3] = {0.0, 0.0, 0.0};
+        GFrame F1;
         if (ok) {
             // decomposition at R^n = x^n with Gamma of the full u (Sec. 3.2)
             double v[3];
@@ -414,11 +418,11 @@ __device__ int ks_particle(const KsGrid<FT> &g, const StepCfg &c, double qm, int
                 for (int i = 0; i < 3; ++i) bpg[i] = ug[i] * iu;
                 mu = uperp * uperp / (2.0 * F0.Bmag * F0.kappa);
             }
-            ok = grgca_step(g, c, qm, F0, R, upar, mu, uperp, bpg, iters, nonconv);
+            ok = grgca_step(g, c, qm, F0, R, upar, mu, uperp, bpg, iters, nonconv, F1);
         }
         if (ok) {
-            GFrame F1;   // reconstruction at R^{n+1}, gyration direction kept
-            gr_frame(g, c.a, R, false, F1);
+            // reconstruction at R^{n+1} (frame F1 from the step), gyration
+            // direction kept
             ok = F1.ok;
             if (ok) {
                 const double G1 = F1.kappa * sqrt(1.0 + upar * upar + gr_perp2(F1, c, mu, uperp));
@@ -428,12 +432,13 @@ __device__ int ks_particle(const KsGrid<FT> &g, const StepCfg &c, double qm, int
                     u[i] = upar * F1.bdn[i] + F1.vE[i] * G1 + ugm * bpg[i];
                     x[i] = R[i];
                 }
+                mfin = F1.m;
                 return 0;
             }
         }
         fail = true;
     }
-    greom_step(g, c, qm, x, u, iters, nonconv);
+    greom_step(g, c, qm, x, u, iters, nonconv, mfin);
     return 1;
 }
 
@@ -535,7 +540,8 @@ __global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args 
             gr_frame(g, a.c.a, x, false, F0);
             int it = 0;
             bool ncv = false, fail = false;
-            const int br = ks_particle(g, a.c, qm, S, F0, x, u, it, ncv, fail);
+            Metric mfin;
+            const int br = ks_particle(g, a.c, qm, S, F0, x, u, it, ncv, fail, mfin);
             // poles: reflect theta, rotate phi by pi, flip u_theta
             if (x[1] < 0.0) { x[1] = -x[1]; x[2] += PI; u[1] = -u[1]; }
             if (x[1] > PI) { x[1] = 2.0 * PI - x[1]; x[2] += PI; u[1] = -u[1]; }
@@ -560,10 +566,8 @@ __global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args 
                 if (fail) ++gf;
                 si += it;
                 mi = max(mi, (unsigned)it);
-                Metric m;
-                ks_metric(a.c.a, x[0], x[1], false, m);
                 double v[3];
-                raise(m, u, v);
+                raise(mfin, u, v);
                 const double u2 = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
                 ek += u2 / (1.0 + sqrt(1.0 + u2));
             } else {
