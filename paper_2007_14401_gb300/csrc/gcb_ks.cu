@@ -310,6 +310,37 @@ __device__ __forceinline__ void gr_frame(const KsGrid<FT> &g, double a, const do
     F.Dpar = D[0] * F.bdn[0] + D[1] * F.bdn[1] + D[2] * F.bdn[2];
 }
 
+// The frame at x^n (no metric derivatives) kept between the switch and the
+// step: the values a step reads, one shared-memory row each.
+constexpr int NFR = 26;
+
+__device__ __forceinline__ void frame_store(double (*s)[TPB], int t, const GFrame &F)
+{
+    const double v[NFR] = {F.m.alpha, F.m.beta_r, F.m.sqrtg, F.m.grr, F.m.grp, F.m.gtt,
+                           F.m.gpp, F.m.drr, F.m.drp, F.m.dtt, F.m.dpp, F.D[0], F.D[1],
+                           F.D[2], F.Bmag, F.bdn[0], F.bdn[1], F.bdn[2], F.bup[0], F.bup[1],
+                           F.bup[2], F.vE[0], F.vE[1], F.vE[2], F.kappa, F.Dpar};
+#pragma unroll
+    for (int k = 0; k < NFR; ++k) s[k][t] = v[k];
+}
+
+__device__ __forceinline__ void frame_load(const double (*s)[TPB], int t, GFrame &F)
+{
+    double v[NFR];
+#pragma unroll
+    for (int k = 0; k < NFR; ++k) v[k] = s[k][t];
+    F.m.alpha = v[0]; F.m.beta_r = v[1]; F.m.sqrtg = v[2];
+    F.m.grr = v[3]; F.m.grp = v[4]; F.m.gtt = v[5]; F.m.gpp = v[6];
+    F.m.drr = v[7]; F.m.drp = v[8]; F.m.dtt = v[9]; F.m.dpp = v[10];
+    F.D[0] = v[11]; F.D[1] = v[12]; F.D[2] = v[13];
+    F.Bmag = v[14];
+    F.bdn[0] = v[15]; F.bdn[1] = v[16]; F.bdn[2] = v[17];
+    F.bup[0] = v[18]; F.bup[1] = v[19]; F.bup[2] = v[20];
+    F.vE[0] = v[21]; F.vE[1] = v[22]; F.vE[2] = v[23];
+    F.kappa = v[24];
+    F.Dpar = v[25];
+}
+
 __device__ __forceinline__ double gr_perp2(const GFrame &F, const StepCfg &c, double mu, double up)
 {
     return c.mu_mode ? up * up : 2.0 * mu * F.Bmag * F.kappa;
@@ -446,7 +477,8 @@ template <typename FT>
 __global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args a)
 {
     __shared__ double s_x[3][TPB], s_u[3][TPB];
-    __shared__ uint8_t s_fl[TPB], s_S[TPB];
+    __shared__ double s_F[NFR][TPB];
+    __shared__ uint8_t s_fl[TPB], s_S[TPB], s_ok[TPB];
     __shared__ unsigned short s_perm[TPB];
     __shared__ int s_wc[2][NWARP];
     __shared__ unsigned long long s_acc[ST_COUNT];
@@ -465,6 +497,8 @@ __global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args 
         int cls = 2;
         uint8_t fl = 0;
         double xs[3] = {0, 0, 0}, us[3] = {0, 0, 0};
+        __syncthreads();  // the previous tile's slots are no longer read
+        s_ok[tid] = 0;
         if (valid) {
             fl = a.flagsin[i];
             bool fin = true;
@@ -480,6 +514,8 @@ __global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args 
                 // Eq. (volint), |D^|/|B^| against f_E; division-free form
                 GFrame F;
                 gr_frame(g, a.c.a, xs, false, F);
+                frame_store(s_F, tid, F);   // the step starts from this frame
+                s_ok[tid] = F.ok ? 1 : 0;
                 double v[3], Dd[3];
                 raise(F.m, us, v);
                 const double G = sqrt(1.0 + us[0] * v[0] + us[1] * v[1] + us[2] * v[2]);
@@ -505,7 +541,6 @@ __global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args 
             }
             if (a.pidin != a.pid) a.pid[i] = a.pidin[i];
         }
-        __syncthreads();
         if (valid) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) { s_x[k][tid] = xs[k]; s_u[k][tid] = us[k]; }
@@ -537,7 +572,8 @@ __global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args 
 #pragma unroll
             for (int k = 0; k < 3; ++k) { x[k] = s_x[k][sl]; u[k] = s_u[k][sl]; }
             GFrame F0;
-            gr_frame(g, a.c.a, x, false, F0);
+            frame_load(s_F, sl, F0);
+            F0.ok = s_ok[sl] != 0;
             int it = 0;
             bool ncv = false, fail = false;
             Metric mfin;
