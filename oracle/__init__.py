@@ -96,7 +96,8 @@ class KsField(C.Structure):
 
 
 class KsParams(C.Structure):
-    _fields_ = [("a", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double)]
+    _fields_ = [("a", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("kick_basis", C.c_int)]
 
 
 def _load():
@@ -130,6 +131,8 @@ def _load():
             lib.orc_ks_cell_sizes.argtypes = [P(KsField), C.c_double, C.c_void_p]
             lib.orc_ks_frame.argtypes = [C.c_double, C.c_double, C.c_double, D3, D3,
                                          C.c_double * 6]
+            lib.orc_ks_kick.argtypes = [C.c_double, C.c_double, C.c_double, D3, D3, C.c_double,
+                                        C.c_double, C.c_int, D3]
             lib.orc_ks_step_one.argtypes = [P(KsField), P(KsParams), P(Params), C.c_void_p,
                                             D3, D3, P(C.c_ubyte), P(Detail)]
             lib.orc_push_ks.argtypes = [C.c_long, C.c_void_p * 3, C.c_void_p * 3, C.c_void_p,
@@ -333,8 +336,11 @@ def ks_grid_field(fields) -> OracleKsField:
                          B=fields["B"])
 
 
-def ks_params(a, r_in, r_out) -> KsParams:
-    return KsParams(a, r_in, r_out)
+KICK_TETRAD, KICK_GLOBAL = 0, 1
+
+
+def ks_params(a, r_in, r_out, kick_basis=KICK_TETRAD) -> KsParams:
+    return KsParams(a, r_in, r_out, kick_basis)
 
 
 def ks_metric(a, r, th) -> dict:
@@ -359,6 +365,15 @@ def ks_cell_sizes(field: OracleKsField, a) -> np.ndarray:
     out = np.empty((field.nth - 1, field.nr - 1))
     lib.orc_ks_cell_sizes(C.byref(field.s), a, out.ctypes.data)
     return out
+
+
+def ks_kick(a, r, th, D, B, qm, dtau, u, basis=KICK_TETRAD) -> np.ndarray:
+    """Boris kick (Sec. 2.3) of covariant u by contravariant D, B at (r, theta)
+    over proper time dtau, in the local frame or the global coordinate basis."""
+    lib = _load()
+    uu = (C.c_double * 3)(*u)
+    lib.orc_ks_kick(a, r, th, (C.c_double * 3)(*D), (C.c_double * 3)(*B), qm, dtau, int(basis), uu)
+    return np.array(uu[:])
 
 
 def ks_frame(a, r, th, u, F):

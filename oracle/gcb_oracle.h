@@ -89,6 +89,7 @@ typedef struct {
 typedef struct {
     double a;            /* black-hole spin */
     double r_in, r_out;  /* particles leaving [r_in, r_out] are flagged EXITED */
+    int kick_basis;      /* GREOM half kicks: 0 local frame (tetrad), 1 global coordinate basis */
 } orc_ks_params;
 
 /* Everything one particle-step computed, for the closed-form tests. */
@@ -156,6 +157,11 @@ void orc_ks_cell_sizes(const orc_ks_field *f, double a, double *dl);
 /* Local-frame components: out[0..2] of covariant u, out[3..5] of contravariant F. */
 void orc_ks_frame(double a, double r, double th, const double u[3], const double F[3],
                   double out[6]);
+
+/* Boris kick (Sec. 2.3) of covariant u by contravariant D, B at (r, theta)
+ * over proper time dtau: basis 0 in the local frame, 1 in the global basis. */
+void orc_ks_kick(double a, double r, double th, const double D[3], const double B[3], double qm,
+                 double dtau, int basis, double u[3]);
 
 /* One coupled covariant step (Sec. 3.2) of one particle (x = r, theta, phi;
  * u covariant); dl is the cell-size table (NULL: dl = 1). */

@@ -300,19 +300,99 @@ static void boris_local(const double E[3], const double B[3], double qm, double 
     for (int k = 0; k < 3; ++k) u[k] = um[k] + x[k] + h * E[k];
 }
 
-static void ks_half_kick(const orc_ks_field *f, double a, double qm, double dt, const double x[3],
-                         double u[3])
+/* ---------------------------------------------------------------------- */
+/* The same kick in the global coordinate basis (Sec. 2.3 and 2.4 name a    */
+/* Boris-like push without tetrads as an option).  Reading: the three Boris */
+/* stages with each frame dot product replaced by its metric contraction    */
+/* and the frame cross product by the Levi-Civita tensor                    */
+/* e_ijk = sqrt(gamma) [ijk] acting on raised vectors (covariant result):   */
+/*   u-_i = u_i + h gamma_ij D^j,   Gamma- = (1 + gamma^{ij} u-_i u-_j)^(1/2),  */
+/*   t^k = h B^k / Gamma-,          s^k = 2 t^k / (1 + gamma_ij t^i t^j),   */
+/*   u'_i = u-_i + e_ijk (gamma^{jl} u-_l) t^k,                              */
+/*   u+_i = u-_i + e_ijk (gamma^{jl} u'_l) s^k,   u_i <- u+_i + h gamma_ij D^j. */
+/* It reproduces the frame kick because the triad L has det L = 1/sqrt(gamma). */
+/* ---------------------------------------------------------------------- */
+static double levi_civita(int i, int j, int k)
+{
+    return 0.5 * (double)((i - j) * (j - k) * (k - i));
+}
+
+static void contract(const double G[3][3], const double v[3], double w[3])
+{
+    for (int i = 0; i < 3; ++i) {
+        w[i] = 0.0;
+        for (int j = 0; j < 3; ++j) w[i] += G[i][j] * v[j];
+    }
+}
+
+static void cross_covariant(const metric_t *M, const double a_up[3], const double b_up[3],
+                            double c[3])
+{
+    for (int i = 0; i < 3; ++i) {
+        c[i] = 0.0;
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) c[i] += M->sqrtg * levi_civita(i, j, k) * a_up[j] * b_up[k];
+    }
+}
+
+static void boris_global(const metric_t *M, const double D[3], const double B[3], double qm,
+                         double dtau, double u[3])
+{
+    double h = 0.5 * qm * dtau, Dd[3], um[3], um_up[3], t[3], t_dn[3], s[3], up[3], up_up[3], x[3];
+    contract(M->gdn, D, Dd);
+    for (int k = 0; k < 3; ++k) um[k] = u[k] + h * Dd[k];
+    contract(M->gup, um, um_up);
+    double gm = sqrt(1.0 + um[0] * um_up[0] + um[1] * um_up[1] + um[2] * um_up[2]);
+    for (int k = 0; k < 3; ++k) t[k] = h * B[k] / gm;
+    contract(M->gdn, t, t_dn);
+    double t2 = t[0] * t_dn[0] + t[1] * t_dn[1] + t[2] * t_dn[2];
+    for (int k = 0; k < 3; ++k) s[k] = 2.0 * t[k] / (1.0 + t2);
+    cross_covariant(M, um_up, t, x);
+    for (int k = 0; k < 3; ++k) up[k] = um[k] + x[k];
+    contract(M->gup, up, up_up);
+    cross_covariant(M, up_up, s, x);
+    for (int k = 0; k < 3; ++k) u[k] = um[k] + x[k] + h * Dd[k];
+}
+
+/* Kick of covariant u by the contravariant fields D, B at (r, theta) over
+ * proper time dtau, in the local frame (basis 0) or the global basis (1). */
+static void ks_kick(double a, double r, double th, const double D[3], const double B[3],
+                    double qm, double dtau, int basis, double u[3])
 {
     metric_t M;
-    ks_metric(a, x[0], x[1], &M);
-    double D[3], B[3], L[3][3], uh[3], Dh[3], Bh[3];
-    orc_ks_gather(f, x[0], x[1], D, B);
+    ks_metric(a, r, th, &M);
+    if (basis == 1) {
+        boris_global(&M, D, B, qm, dtau, u);
+        return;
+    }
+    double L[3][3], uh[3], Dh[3], Bh[3];
     chol3(M.gup, L);
     frame_in(L, u, uh);
     field_in(L, D, Dh);
     field_in(L, B, Bh);
-    boris_local(Dh, Bh, qm, 0.5 * dt * M.alpha, uh);
+    boris_local(Dh, Bh, qm, dtau, uh);
     frame_out(L, uh, u);
+}
+
+void orc_ks_kick(double a, double r, double th, const double D[3], const double B[3], double qm,
+                 double dtau, int basis, double u[3])
+{
+    ks_kick(a, r, th, D, B, qm, dtau, basis, u);
+}
+
+/* GREOM half kick (Sec. 2.3 steps 1 and 3): fields and metric at x, proper
+ * time alpha dt / 2. */
+static void ks_half_kick(const orc_ks_field *f, double a, int basis, double qm, double dt,
+                         const double x[3], double u[3])
+{
+    double D[3], B[3], alpha;
+    orc_ks_gather(f, x[0], x[1], D, B);
+    {
+        metric_t M;
+        ks_metric(a, x[0], x[1], &M);
+        alpha = M.alpha;
+    }
+    ks_kick(a, x[0], x[1], D, B, qm, 0.5 * dt * alpha, basis, u);
 }
 
 /* 3+1 geodesic terms (Sec. 2.3): V^i = alpha gamma^{ij} u_j / Gamma - beta^i,
@@ -351,12 +431,12 @@ static int ks_converged(const orc_params *p, int iters, double res, int *nonconv
 }
 
 /* GREOM step (Sec. 2.3): half kick at x^n, IMR for (x, u), half kick at x^{n+1}. */
-static int greom_step(const orc_ks_field *f, double a, const orc_params *p, double qm,
+static int greom_step(const orc_ks_field *f, double a, int basis, const orc_params *p, double qm,
                       double x[3], double u[3], int *iters, int *nonconv, double *resid)
 {
     double dt = p->dt;
     double up[3] = {u[0], u[1], u[2]};
-    ks_half_kick(f, a, qm, dt, x, up);
+    ks_half_kick(f, a, basis, qm, dt, x, up);
     double xk[3] = {x[0], x[1], x[2]}, wk[3] = {up[0], up[1], up[2]};
     *iters = 0;
     *nonconv = 0;
@@ -379,7 +459,7 @@ static int greom_step(const orc_ks_field *f, double a, const orc_params *p, doub
         *resid = res;
         if (ks_converged(p, *iters, res, nonconv)) break;
     }
-    ks_half_kick(f, a, qm, dt, xk, wk);
+    ks_half_kick(f, a, basis, qm, dt, xk, wk);
     for (int k = 0; k < 3; ++k) { x[k] = xk[k]; u[k] = wk[k]; }
     return 1;
 }
@@ -582,7 +662,7 @@ void orc_ks_step_one(const orc_ks_field *f, const orc_ks_params *kp, const orc_p
         }
     }
     if (use_boris) {
-        greom_step(f, a, p, qm, xn, un, &iters, &nonconv, &resid);
+        greom_step(f, a, kp->kick_basis, p, qm, xn, un, &iters, &nonconv, &resid);
         d->branch = 1;
     } else {
         d->branch = 0;

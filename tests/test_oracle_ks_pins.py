@@ -298,3 +298,92 @@ def test_greom_half_kicks_rotate_in_the_local_frame():
     got = math.atan2(uh0[1] * uh1[2] - uh0[2] * uh1[1], uh0[1] * uh1[1] + uh0[2] * uh1[2])
     assert abs(got) == pytest.approx(ang, rel=1e-5)
     assert math.copysign(1, got) == -math.copysign(1, qm)   # right-handed about r^ for q < 0
+
+
+# ---------------------------------------------------------------------------
+# The GREOM kick in the global coordinate basis (the option of Sec. 2.3 and
+# Sec. 2.4: a Boris-like push without tetrads)
+# ---------------------------------------------------------------------------
+KICK_POINTS = [(0.9, 1.3, 0.4), (0.9, 1.5, 0.3), (0.9, 3.0, math.pi / 2), (0.5, 40.0, 2.9),
+               (0.999, 1.2, 0.01), (0.0, 7.0, 1.0)]
+
+
+@pytest.mark.parametrize("a,r,th", KICK_POINTS)
+def test_global_kick_without_electric_field_is_the_boris_rotation(a, r, th):
+    """D = 0: the kick turns u about B, so gamma^{ij} u_i u_j and u_i B^i are
+    kept; the part of u normal to B turns by 2 atan(|t|), |t| = |h| |B| / Gamma
+    with |B|^2 = gamma_ij B^i B^j and h = (q/m) dtau / 2 (Boris 1970); the turn
+    is left-handed about B for q > 0 and right-handed for q < 0."""
+    rng = np.random.default_rng(int(r * 1000) + int(th * 100))
+    m = O.ks_metric(a, r, th)
+    gup, gdn = m["gup"], m["gdn"]
+    for qm in (-7.0, 3.0):
+        B = rng.normal(size=3) * 2.0
+        u = rng.normal(size=3) * 3.0
+        dtau = 0.2
+        u1 = O.ks_kick(a, r, th, np.zeros(3), B, qm, dtau, u, basis=O.KICK_GLOBAL)
+        uu = u @ gup @ u
+        assert u1 @ gup @ u1 == pytest.approx(uu, rel=1e-13)
+        assert u1 @ B == pytest.approx(u @ B, rel=1e-12, abs=1e-12 * math.sqrt(uu))
+        Bn = math.sqrt(B @ gdn @ B)
+        b_dn, b_up = gdn @ B / Bn, B / Bn
+        p0 = u - (u @ b_up) * b_dn
+        p1 = u1 - (u1 @ b_up) * b_dn
+        p0u, p1u = gup @ p0, gup @ p1
+        cos = p0 @ p1u / (p0 @ p0u)
+        sin = m["sqrtg"] * (b_up @ np.cross(p0u, p1u)) / (p0 @ p0u)
+        turn = math.atan2(sin, cos)
+        h = 0.5 * qm * dtau
+        assert abs(turn) == pytest.approx(2 * math.atan(abs(h) * Bn / math.sqrt(1 + uu)), rel=1e-11)
+        assert math.copysign(1.0, turn) == -math.copysign(1.0, qm)
+
+
+@pytest.mark.parametrize("a,r,th", KICK_POINTS)
+def test_global_kick_without_magnetic_field_is_linear(a, r, th):
+    """B = 0: covariant u_i gains (q/m) dtau gamma_ij D^j exactly."""
+    rng = np.random.default_rng(7)
+    m = O.ks_metric(a, r, th)
+    D, u = rng.normal(size=3), rng.normal(size=3) * 2.0
+    qm, dtau = -4.0, 0.3
+    u1 = O.ks_kick(a, r, th, D, np.zeros(3), qm, dtau, u, basis=O.KICK_GLOBAL)
+    want = u + qm * dtau * (m["gdn"] @ D)
+    np.testing.assert_allclose(u1, want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+
+
+def test_global_kick_equals_the_local_frame_kick():
+    """The frame cross product of L^{-1} a and L^{-1} b maps back to
+    sqrt(gamma) [ijk] a^j b^k because det L = 1 / sqrt(gamma), and frame dot
+    products are metric contractions: the two bases give one kick."""
+    rng = np.random.default_rng(3)
+    for a, r, th in KICK_POINTS:
+        for scale in (1e-3, 1.0, 1e3):
+            D, B = rng.normal(size=3) * 0.3, rng.normal(size=3) * scale
+            u = rng.normal(size=3) * rng.choice([0.1, 10.0, 1e3])
+            qm, dtau = rng.choice([-1e3, -2.0, 5.0]), 0.05
+            uf = O.ks_kick(a, r, th, D, B, qm, dtau, u, basis=O.KICK_TETRAD)
+            ug = O.ks_kick(a, r, th, D, B, qm, dtau, u, basis=O.KICK_GLOBAL)
+            assert np.abs(ug - uf).max() <= 1e-13 * np.abs(uf).max()
+
+
+def test_greom_steps_in_both_bases_agree():
+    """Whole GREOM steps (half kick, implicit midpoint, half kick) in the Wald
+    field, in the local frame and in the global basis: equal up to rounding."""
+    from paper_2007_14401_gb300 import inputs
+    fields, st, p = inputs.kerr_wald(nr=48, nth=40, n_particles=64, seed=9)
+    of = O.ks_grid_field(fields)
+    dl = O.ks_cell_sizes(of, p["a"])
+    op = O.make_params(dt=p["dt"], f_rho=p["f_rho"], f_E=p["f_E"], qm=(-30.0,),
+                       force=O.FORCE_BORIS, fixed_iters=8)
+    out = []
+    for basis in (O.KICK_TETRAD, O.KICK_GLOBAL):
+        s = {k: v.copy() for k, v in st.items()}
+        O.push_ks(s, of, O.ks_params(p["a"], p["r_in"], p["r_out"], basis), op, 5, dl=dl)
+        out.append(s)
+    f, g = out
+    live = (f["flags"] & (O.FLAG_EXITED | O.FLAG_NONFINITE)) == 0
+    assert live.mean() > 0.9
+    np.testing.assert_array_equal(f["flags"], g["flags"])
+    dx = np.abs(f["x"] - g["x"])[:, live]
+    dx[2] = np.minimum(dx[2], 2 * np.pi - dx[2])
+    assert dx.max() <= 1e-12 * np.abs(f["x"][:, live]).max()
+    assert np.abs(f["u"] - g["u"])[:, live].max() <= 1e-12 * (np.abs(f["u"][:, live]).max() + 1)

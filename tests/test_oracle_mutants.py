@@ -70,8 +70,19 @@ MUTANTS_KS = [
      "G[i] = -Gam * M->dalpha[i] + ub - M->alpha * uu / Gam;"),
     ("velocity_shift_sign", "V[i] = M->alpha * s / Gam - M->beta[i];",
      "V[i] = M->alpha * s / Gam + M->beta[i];"),
-    ("half_kick_full_dt", "boris_local(Dh, Bh, qm, 0.5 * dt * M.alpha, uh);",
-     "boris_local(Dh, Bh, qm, dt * M.alpha, uh);"),
+    ("half_kick_full_dt", "ks_kick(a, x[0], x[1], D, B, qm, 0.5 * dt * alpha, basis, u);",
+     "ks_kick(a, x[0], x[1], D, B, qm, dt * alpha, basis, u);"),
+    ("global_kick_sqrtg_dropped",
+     "c[i] += M->sqrtg * levi_civita(i, j, k) * a_up[j] * b_up[k];",
+     "c[i] += levi_civita(i, j, k) * a_up[j] * b_up[k];"),
+    ("global_kick_cross_not_raised", "cross_covariant(M, um_up, t, x);",
+     "cross_covariant(M, um, t, x);"),
+    ("global_kick_t2_euclidean", "double t2 = t[0] * t_dn[0] + t[1] * t_dn[1] + t[2] * t_dn[2];",
+     "double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];"),
+    ("global_kick_D_not_lowered", "for (int k = 0; k < 3; ++k) um[k] = u[k] + h * Dd[k];",
+     "for (int k = 0; k < 3; ++k) um[k] = u[k] + h * D[k];"),
+    ("global_kick_handedness", "return 0.5 * (double)((i - j) * (j - k) * (k - i));",
+     "return -0.5 * (double)((i - j) * (j - k) * (k - i));"),
     ("frame_transposed", "for (int i = 0; i < 3; ++i) uh[a] += L[i][a] * u[i];",
      "for (int i = 0; i < 3; ++i) uh[a] += L[a][i] * u[i];"),
     ("gca_drift_dropped", "for (int j = 0; j < 3; ++j) s += Fb.M.gup[i][j] * (ub * Fb.bdn[j] / Gam + Fb.vE[j]);",
