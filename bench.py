@@ -364,6 +364,8 @@ def main():
                     help="particle chunks streamed through the GPU in the end-to-end timing")
     ap.add_argument("--sort-every", type=int, default=None)
     ap.add_argument("--sort-tile", default=None, help="cells per sort tile, e.g. 2,2")
+    ap.add_argument("--ks-kick", default="tetrad", choices=["tetrad", "global"],
+                    help="kerr_wald: basis of the GREOM half kicks (local frame or global)")
     ap.add_argument("--particles", type=int, default=None,
                     help="particles per GPU (smaller cases for profiling only)")
     args = ap.parse_args()
@@ -400,7 +402,8 @@ def main():
     fields, st, p = w["gen"](n_req, multi.rank_seed(rank))
     ks = w["precision"] == "ks"
     if ks:
-        grid = G.KsGrid(fields, p["a"], p["r_in"], p["r_out"], dtype=w["grid"])
+        grid = G.KsGrid(fields, p["a"], p["r_in"], p["r_out"], dtype=w["grid"],
+                        kick_basis=G.KS_GLOBAL if args.ks_kick == "global" else G.KS_TETRAD)
         ds = G.State.from_numpy(st, precision="fp64")
     else:
         grid = G.Grid(fields, dtype=w["grid"])
@@ -542,7 +545,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if w["precision"] == "mixed" else "f64", "data": "synthetic",
-                "config": workload_config(w, n_all, world, sort_every, tile),
+                "config": dict(workload_config(w, n_all, world, sort_every, tile),
+                               **({"kick_basis": args.ks_kick} if ks else {})),
                 "roofline": roofline,
                 "e2e": e2e,
                 "gpu_launches": args.steps + 6 * n_sorts,

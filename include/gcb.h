@@ -317,9 +317,24 @@ typedef struct {
     const double *dl;
 } gcb_grid_ks;
 
+/*
+ * Basis of the GREOM half kicks (Sec. 2.3 steps 1 and 3).
+ *   GCB_KS_TETRAD: the Boris kick in the local frame of the normal observer,
+ *     the paper's choice (triad from gamma^{ij} = L L^T, L the Cholesky factor).
+ *   GCB_KS_GLOBAL: the same kick written in the global coordinate basis, which
+ *     the paper (Sec. 2.3, Sec. 2.4) names as an option for spacetimes where a
+ *     tetrad is awkward: D_i = gamma_ij D^j, u-_i = u_i + h D_i,
+ *     t^k = h B^k / Gamma-, |t|^2 = gamma_ij t^i t^j, cross products
+ *     (a x b)_i = sqrt(gamma) [ijk] a^j b^k of raised vectors, h = (q/m) alpha dt / 4.
+ *     Identical to the tetrad kick up to rounding (det L = 1/sqrt(gamma)).
+ * The GRGCA kick adds (q/m) alpha dt/2 D_par to the scalar u_par in both bases.
+ */
+enum { GCB_KS_TETRAD = 0, GCB_KS_GLOBAL = 1 };
+
 typedef struct {
     double a;                /* spin, 0 <= a < 1 */
     double r_in, r_out;      /* particles leaving [r_in, r_out] get GCB_FLAG_EXITED */
+    int32_t kick_basis;      /* GCB_KS_TETRAD (0, default) or GCB_KS_GLOBAL; other: GCB_EINVAL */
 } gcb_ks_params;
 
 /*

@@ -327,6 +327,10 @@ static gcb_status check_ks(const gcb_grid_ks *gk, const gcb_ks_params *kp)
         set_error("need 0 <= a < 1 and 0 < r_in < r_out");
         return GCB_EINVAL;
     }
+    if (kp->kick_basis != GCB_KS_TETRAD && kp->kick_basis != GCB_KS_GLOBAL) {
+        set_error("kick_basis must be GCB_KS_TETRAD or GCB_KS_GLOBAL");
+        return GCB_EINVAL;
+    }
     return GCB_OK;
 }
 

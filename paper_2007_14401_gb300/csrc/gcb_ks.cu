@@ -121,6 +121,11 @@ __device__ __forceinline__ void con_to_frame(const Tri &t, const double F[3], do
     h[2] = (F[2] - t.l20 * h[0]) / t.l22;
 }
 
+struct StepCfg {
+    double a, dt, f_rho, f_E, r_in, r_out, tol;
+    int max_iter, fixed_iters, force, mu_mode, basis;
+};
+
 template <typename FT>
 struct KsGrid {
     const FT *rec;
@@ -190,20 +195,61 @@ __device__ __forceinline__ void boris_local(const double E[3], const double B[3]
     for (int k = 0; k < 3; ++k) u[k] = fma(h, E[k], fma(sf, x[k], um[k]));
 }
 
+// The same kick in the global coordinate basis (the option of Sec. 2.3 and
+// 2.4 that needs no tetrad): covariant u and D_i = gamma_ij D^j, contravariant
+// B^k, t^k = h B^k / Gamma-, |t|^2 = gamma_ij t^i t^j and cross products
+// (v x t)_i = sqrt(gamma) [ijk] v^j t^k of raised vectors; the frame form
+// maps onto this one because det L = 1 / sqrt(gamma).
+__device__ __forceinline__ void boris_global(const Metric &m, const double D[3], const double B[3],
+                                             double qm, double dtau, double u[3])
+{
+    const double h = 0.5 * qm * dtau;
+    double Dd[3], Bd[3], um[3], v[3], t[3], x[3], w[3];
+    lower(m, D, Dd);
+    lower(m, B, Bd);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) um[k] = fma(h, Dd[k], u[k]);
+    raise(m, um, v);
+    const double gm = sqrt(1.0 + um[0] * v[0] + um[1] * v[1] + um[2] * v[2]);
+    const double hg = h / gm;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = hg * B[k];
+    const double t2 = hg * hg * (Bd[0] * B[0] + Bd[1] * B[1] + Bd[2] * B[2]);
+    const double sf = 2.0 / (1.0 + t2);
+    const double sg = m.sqrtg;
+    x[0] = sg * (v[1] * t[2] - v[2] * t[1]);
+    x[1] = sg * (v[2] * t[0] - v[0] * t[2]);
+    x[2] = sg * (v[0] * t[1] - v[1] * t[0]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w[k] = um[k] + x[k];
+    raise(m, w, v);
+    x[0] = sg * (v[1] * t[2] - v[2] * t[1]);
+    x[1] = sg * (v[2] * t[0] - v[0] * t[2]);
+    x[2] = sg * (v[0] * t[1] - v[1] * t[0]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u[k] = fma(h, Dd[k], fma(sf, x[k], um[k]));
+}
+
+// One GREOM half kick over alpha dt / 2 at x, in the basis c.basis selects
 // (m: the metric at x, returned for reuse)
 template <typename FT>
-__device__ __forceinline__ void half_kick(const KsGrid<FT> &g, double a, double qm, double dt,
+__device__ __forceinline__ void half_kick(const KsGrid<FT> &g, const StepCfg &c, double qm,
                                           const double x[3], double u[3], Metric &m)
 {
-    ks_metric(a, x[0], x[1], false, m);
-    double D[3], B[3], Dh[3], Bh[3], uh[3];
+    ks_metric(c.a, x[0], x[1], false, m);
+    double D[3], B[3];
     ks_gather(g, x[0], x[1], D, B);
+    if (c.basis == GCB_KS_GLOBAL) {
+        boris_global(m, D, B, qm, 0.5 * c.dt * m.alpha, u);
+        return;
+    }
+    double Dh[3], Bh[3], uh[3];
     Tri t;
     make_tri(m, t);
     cov_to_frame(t, u, uh);
     con_to_frame(t, D, Dh);
     con_to_frame(t, B, Bh);
-    boris_local(Dh, Bh, qm, 0.5 * dt * m.alpha, uh);
+    boris_local(Dh, Bh, qm, 0.5 * c.dt * m.alpha, uh);
     frame_to_cov(t, uh, u);
 }
 
@@ -220,11 +266,6 @@ __device__ __forceinline__ void geodesic_G(const Metric &m, const double u[3], d
     G[2] = 0.0;   // axisymmetric: no phi dependence
 }
 
-struct StepCfg {
-    double a, dt, f_rho, f_E, r_in, r_out, tol;
-    int max_iter, fixed_iters, force, mu_mode;
-};
-
 __device__ __forceinline__ bool imr_done(const StepCfg &c, int iters, double res, bool &nonconv)
 {
     if (c.fixed_iters > 0) return iters >= c.fixed_iters;
@@ -240,7 +281,7 @@ __device__ void greom_step(const KsGrid<FT> &g, const StepCfg &c, double qm, dou
                            double u[3], int &iters, bool &nonconv, Metric &mfin)
 {
     double up[3] = {u[0], u[1], u[2]};
-    half_kick(g, c.a, qm, c.dt, x, up, mfin);
+    half_kick(g, c, qm, x, up, mfin);
     double xk[3] = {x[0], x[1], x[2]}, wk[3] = {up[0], up[1], up[2]};
     iters = 0;
     nonconv = false;
@@ -269,7 +310,7 @@ __device__ void greom_step(const KsGrid<FT> &g, const StepCfg &c, double qm, dou
         ++iters;
         if (imr_done(c, iters, res, nonconv)) break;
     }
-    half_kick(g, c.a, qm, c.dt, xk, wk, mfin);
+    half_kick(g, c, qm, xk, wk, mfin);
 #pragma unroll
     for (int k = 0; k < 3; ++k) { x[k] = xk[k]; u[k] = wk[k]; }
 }
@@ -735,6 +776,7 @@ static gcb_status push_step(const gcb_particles *p, const gcb_particles *in, con
     a.c.fixed_iters = prm->gca_fixed_iters;
     a.c.force = prm->force;
     a.c.mu_mode = prm->mu_mode;
+    a.c.basis = kp->kick_basis;
     a.stats = stats;
     return launch<FT>(g, a, st);
 }

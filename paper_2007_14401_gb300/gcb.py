@@ -59,7 +59,11 @@ class GcbGridKs(C.Structure):
 
 
 class GcbKsParams(C.Structure):
-    _fields_ = [("a", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double)]
+    _fields_ = [("a", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("kick_basis", C.c_int32)]
+
+
+KS_TETRAD, KS_GLOBAL = 0, 1   # GREOM half kicks in the local frame / the global basis
 
 
 EXPORTS = ["gcb_version", "gcb_status_string", "gcb_last_error", "gcb_grid_stride",
@@ -524,7 +528,7 @@ class KsGrid:
     table of Eq. (volint), both on the device."""
 
     def __init__(self, fields: dict, a: float, r_in: float, r_out: float, dtype: str = "f32",
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, kick_basis: int = KS_TETRAD):
         nth, nr = np.asarray(fields["D"][0]).shape
         self.dtype = F32 if dtype == "f32" else F64
         self.stride = _lib.gcb_grid_stride(2, self.dtype, 0)
@@ -540,7 +544,7 @@ class KsGrid:
         _check(_lib.gcb_grid_pack(C.byref(g), ptrs, _stream_ptr(stream)), "gcb_grid_pack")
         self.dl = torch.empty((nth - 1) * (nr - 1), dtype=torch.float64, device=device)
         self.s = GcbGridKs(g, fields["logr0"], self.dl.data_ptr())
-        self.kp = GcbKsParams(a, r_in, r_out)
+        self.kp = GcbKsParams(a, r_in, r_out, kick_basis)
         _check(_lib.gcb_ks_cell_size(C.byref(self.s), C.byref(self.kp),
                                      C.c_void_p(self.dl.data_ptr()), _stream_ptr(stream)),
                "gcb_ks_cell_size")

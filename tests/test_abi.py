@@ -46,7 +46,8 @@ def test_struct_layout_matches_header(G, tmp_path):
               ("gcb_particles", "flags", G.GcbParticles), ("gcb_particles", "pid", G.GcbParticles),
               ("gcb_params", "gca_tol", G.GcbParams), ("gcb_params", "step_index", G.GcbParams),
               ("gcb_params", "fuse_steps", G.GcbParams), ("gcb_stats", "sum_ekin", G.GcbStats),
-              ("gcb_grid_ks", "dl", G.GcbGridKs), ("gcb_ks_params", "r_out", G.GcbKsParams)]
+              ("gcb_grid_ks", "dl", G.GcbGridKs), ("gcb_ks_params", "r_out", G.GcbKsParams),
+              ("gcb_ks_params", "kick_basis", G.GcbKsParams)]
     lines = "".join(f'printf("%zu %zu\\n", sizeof({t}), offsetof({t}, {f}));\n'
                     for t, f, _ in fields)
     src = tmp_path / "layout.c"
@@ -91,3 +92,11 @@ def test_argument_errors_without_gpu(G):
     rc = lib.gcb_push_sr(C.byref(p), C.byref(g), C.byref(prm), 1, None, None, 0, None)
     assert rc == 1 and b"stride" in lib.gcb_last_error()
     assert lib.gcb_pos_split(-1, None, None, None, None) == 1
+    # Kerr-Schild: an unknown kick basis is refused before any launch
+    gk = G.GcbGrid(2, G.F32, (C.c_int64 * 3)(16, 17, 1), (C.c_double * 3)(0.1, 3.141592653589793 / 16, 1), 0,
+                   lib.gcb_grid_stride(2, G.F32, 0), 4096)
+    ks = G.GcbGridKs(gk, 0.3, 4096)
+    for basis, want in ((2, 1), (-1, 1)):
+        rc = lib.gcb_ks_cell_size(C.byref(ks), C.byref(G.GcbKsParams(0.9, 1.5, 50.0, basis)),
+                                  C.c_void_p(4096), None)
+        assert rc == want and b"kick_basis" in lib.gcb_last_error()

@@ -4,6 +4,8 @@ FP64 records: one step from identical states reproduces the oracle's flags
 bit-exactly where the switch margin exceeds 1e-12 and its state to a relative
 1e-12 (fixed implicit-midpoint iteration count on both sides).  FP32 records
 (FP32 field interpolation, FP64 everything else): within FP32 rounding.
+Both bases of the GREOM half kicks (local frame, global coordinates) are
+checked against the oracle's own kick in that basis, and against each other.
 """
 import numpy as np
 import pytest
@@ -32,7 +34,7 @@ def wald():
 def oracle_setup(fields, p, **over):
     q = dict(p, **over)
     of = O.ks_grid_field(fields)
-    kp = O.ks_params(q["a"], q["r_in"], q["r_out"])
+    kp = O.ks_params(q["a"], q["r_in"], q["r_out"], q.get("kick_basis", 0))
     op = O.make_params(c=1.0, dt=q["dt"], f_rho=q["f_rho"], f_E=q["f_E"], qm=q["qm"],
                        mu_mode=q.get("mu_mode", 0), force=q.get("force", 0),
                        max_iter=q.get("gca_max_iter", 16), fixed_iters=q.get("gca_fixed_iters", 0),
@@ -42,7 +44,8 @@ def oracle_setup(fields, p, **over):
 
 def run_both(G, fields, st, p, n_steps=1, dtype="f64", **over):
     q = dict(p, **over)
-    grid = G.KsGrid(fields, q["a"], q["r_in"], q["r_out"], dtype=dtype)
+    grid = G.KsGrid(fields, q["a"], q["r_in"], q["r_out"], dtype=dtype,
+                    kick_basis=q.get("kick_basis", 0))
     ds = G.State.from_numpy(st, precision="fp64")
     gs = G.push_ks(ds, grid, G.make_params(q), n_steps)
     got = ds.to_numpy()
@@ -126,3 +129,56 @@ def test_exits_and_frozen(G, wald):
                           ref["flags"] & (O.FLAG_EXITED | O.FLAG_NONFINITE))
     assert np.all(got["flags"][:5] & G.FLAG_EXITED)
     assert gs["n_nonfinite"] == os_["n_nonfinite"]
+
+
+@pytest.mark.parametrize("force", [1, 0])
+def test_global_basis_one_step(G, wald, force):
+    """GREOM half kicks in the global coordinate basis: flags and states as the
+    oracle's global-basis kick, to the tolerance of the tetrad path."""
+    fields, st, p = wald
+    over = dict(qm=(-30.0,), force=force, gca_fixed_iters=5, kick_basis=G.KS_GLOBAL)
+    m = margins(fields, st, p, **over)
+    got, ref, gs, os_, _, _ = run_both(G, fields, st, p, **over)
+    robust = np.abs(m) > 1e-12
+    assert not np.any((got["flags"] != ref["flags"]) & robust)
+    same = got["flags"] == ref["flags"]
+    assert same.mean() > 0.999
+    dx = np.abs(got["x"] - ref["x"])[:, same]
+    dx[2] = np.minimum(dx[2], 2 * np.pi - dx[2])
+    assert np.all(dx <= 1e-12 * np.maximum(np.abs(ref["x"][:, same]), 1.0))
+    un = np.linalg.norm(ref["u"][:, same], axis=0) + 1.0
+    assert np.all(np.abs(got["u"] - ref["u"])[:, same] <= 1e-12 * un)
+    for k in ("n_boris", "n_gca", "n_gcafail", "n_nonfinite", "sum_iter", "max_iter"):
+        assert gs[k] == os_[k], k
+    assert gs["n_boris"] > 0
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_global_basis_equals_tetrad_on_gpu(G, wald, dtype):
+    """The two bases compute one kick (det L = 1/sqrt(gamma)): ten steps of
+    the CUDA path in each agree to rounding for every particle whose branch
+    sequence is the same in both."""
+    fields, st, p = wald
+    out = []
+    for basis in (G.KS_TETRAD, G.KS_GLOBAL):
+        q = dict(p, qm=(-30.0,), gca_fixed_iters=5)
+        grid = G.KsGrid(fields, q["a"], q["r_in"], q["r_out"], dtype=dtype, kick_basis=basis)
+        ds = G.State.from_numpy(st, precision="fp64")
+        stats = G.push_ks(ds, grid, G.make_params(q), 10)
+        out.append((ds.to_numpy(), stats))
+    (a, sa), (b, sb) = out
+    same = a["flags"] == b["flags"]
+    assert same.mean() > 0.999 and sa["n_boris"] > 0
+    dx = np.abs(a["x"] - b["x"])[:, same]
+    dx[2] = np.minimum(dx[2], 2 * np.pi - dx[2])
+    dx /= np.maximum(np.abs(a["x"][:, same]), 1.0)
+    assert np.median(dx) < 1e-13 and np.max(dx) < 1e-9
+    un = np.linalg.norm(a["u"][:, same], axis=0) + 1.0
+    du = np.abs(a["u"] - b["u"])[:, same] / un
+    assert np.median(du) < 1e-13 and np.max(du) < 1e-9
+
+
+def test_unknown_kick_basis_is_refused(G, wald):
+    fields, st, p = wald
+    with pytest.raises(RuntimeError, match="kick_basis"):
+        G.KsGrid(fields, p["a"], p["r_in"], p["r_out"], kick_basis=3)
