@@ -39,8 +39,8 @@ __device__ __forceinline__ void ks_metric(double a, double r, double th, bool de
     const double irho2 = 1.0 / rho2;
     const double z = 2.0 * r * irho2;
     const double onez = 1.0 + z;
-    const double ionez = 1.0 / onez;
-    m.alpha = sqrt(ionez);
+    m.alpha = rsqrt(onez);
+    const double ionez = m.alpha * m.alpha;
     m.beta_r = z * ionez;
     const double P = fma(z * a2, s2, fma(r, r, a2));
     m.grr = P * ionez * irho2;
@@ -52,7 +52,7 @@ __device__ __forceinline__ void ks_metric(double a, double r, double th, bool de
     m.drp = -a * onez * s2;
     m.dtt = rho2;
     m.dpp = P * s2;
-    m.sqrtg = rho2 * s * sqrt(onez);
+    m.sqrtg = rho2 * s * (onez * m.alpha);
     if (!derivs) return;
     // d rho^2, d z, d P, d sin^2 with respect to (r, theta)
     const double drho2[2] = {2.0 * r, -2.0 * a2 * s * c};
@@ -92,15 +92,20 @@ __device__ __forceinline__ void lower(const Metric &m, const double v[3], double
 // Local frame of the normal observer: gamma^{ij} = L L^T with L lower
 // triangular; for this metric L has L10 = L21 = 0.  Frame components of a
 // covariant vector: u^ = L^T u; of a contravariant one: F^ = L^{-1} F.
+// (i00, i11, i22: reciprocals of the diagonal, so no conversion divides)
 struct Tri {
-    double l00, l20, l11, l22;
+    double l00, l20, l11, l22, i00, i11, i22;
 };
 __device__ __forceinline__ void make_tri(const Metric &m, Tri &t)
 {
-    t.l00 = sqrt(m.grr);
-    t.l20 = m.grp / t.l00;
-    t.l11 = sqrt(m.gtt);
-    t.l22 = sqrt(fma(-t.l20, t.l20, m.gpp));
+    t.i00 = rsqrt(m.grr);
+    t.l00 = m.grr * t.i00;
+    t.l20 = m.grp * t.i00;
+    t.i11 = rsqrt(m.gtt);
+    t.l11 = m.gtt * t.i11;
+    const double d22 = fma(-t.l20, t.l20, m.gpp);
+    t.i22 = rsqrt(d22);
+    t.l22 = d22 * t.i22;
 }
 __device__ __forceinline__ void cov_to_frame(const Tri &t, const double u[3], double h[3])
 {
@@ -110,15 +115,15 @@ __device__ __forceinline__ void cov_to_frame(const Tri &t, const double u[3], do
 }
 __device__ __forceinline__ void frame_to_cov(const Tri &t, const double h[3], double u[3])
 {
-    u[2] = h[2] / t.l22;
-    u[1] = h[1] / t.l11;
-    u[0] = (h[0] - t.l20 * u[2]) / t.l00;
+    u[2] = h[2] * t.i22;
+    u[1] = h[1] * t.i11;
+    u[0] = (h[0] - t.l20 * u[2]) * t.i00;
 }
 __device__ __forceinline__ void con_to_frame(const Tri &t, const double F[3], double h[3])
 {
-    h[0] = F[0] / t.l00;
-    h[1] = F[1] / t.l11;
-    h[2] = (F[2] - t.l20 * h[0]) / t.l22;
+    h[0] = F[0] * t.i00;
+    h[1] = F[1] * t.i11;
+    h[2] = (F[2] - t.l20 * h[0]) * t.i22;
 }
 
 struct StepCfg {
@@ -180,8 +185,9 @@ __device__ __forceinline__ void boris_local(const double E[3], const double B[3]
 #pragma unroll
     for (int k = 0; k < 3; ++k) um[k] = fma(h, E[k], u[k]);
     const double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    const double hg = h / gm;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) t[k] = h * B[k] / gm;
+    for (int k = 0; k < 3; ++k) t[k] = hg * B[k];
     const double sf = 2.0 / (1.0 + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
     x[0] = um[1] * t[2] - um[2] * t[1];
     x[1] = um[2] * t[0] - um[0] * t[2];
@@ -255,13 +261,16 @@ __device__ __forceinline__ void half_kick(const KsGrid<FT> &g, const StepCfg &c,
 
 // V^i = alpha gamma^{ij} u_j / Gamma - beta^i and
 // G_i = -Gamma d_i alpha + u_j d_i beta^j - alpha u_j u_k d_i gamma^{jk} / (2 Gamma)
-__device__ __forceinline__ void geodesic_G(const Metric &m, const double u[3], double Gam, double G[3])
+// (iGam = 1 / Gam)
+__device__ __forceinline__ void geodesic_G(const Metric &m, const double u[3], double Gam,
+                                           double iGam, double G[3])
 {
+    const double ha = 0.5 * m.alpha * iGam;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const double uu = m.dgrr[i] * u[0] * u[0] + 2.0 * m.dgrp[i] * u[0] * u[2] +
                           m.dgtt[i] * u[1] * u[1] + m.dgpp[i] * u[2] * u[2];
-        G[i] = -Gam * m.da[i] + u[0] * m.dbr[i] - m.alpha * uu / (2.0 * Gam);
+        G[i] = -Gam * m.da[i] + u[0] * m.dbr[i] - ha * uu;
     }
     G[2] = 0.0;   // axisymmetric: no phi dependence
 }
@@ -294,9 +303,10 @@ __device__ void greom_step(const KsGrid<FT> &g, const StepCfg &c, double qm, dou
         double v[3];
         raise(m, ub, v);
         const double Gam = sqrt(1.0 + ub[0] * v[0] + ub[1] * v[1] + ub[2] * v[2]);
+        const double iGam = 1.0 / Gam;
         double G[3];
-        geodesic_G(m, ub, Gam, G);
-        const double f = m.alpha / Gam;
+        geodesic_G(m, ub, Gam, iGam, G);
+        const double f = m.alpha * iGam;
         const double V[3] = {f * v[0] - m.beta_r, f * v[1], f * v[2]};
         double res = 0.0;
 #pragma unroll
@@ -333,12 +343,12 @@ __device__ __forceinline__ void gr_frame(const KsGrid<FT> &g, double a, const do
     lower(F.m, B, Bd);
     const double B2 = Bd[0] * B[0] + Bd[1] * B[1] + Bd[2] * B[2];
     F.ok = B2 > 0.0;
-    const double Bm = sqrt(F.ok ? B2 : 1.0);
-    F.Bmag = Bm;
-    const double ib = 1.0 / Bm;
+    const double B2s = F.ok ? B2 : 1.0;
+    const double ib = rsqrt(B2s);
+    F.Bmag = B2s * ib;
 #pragma unroll
     for (int i = 0; i < 3; ++i) { F.bdn[i] = Bd[i] * ib; F.bup[i] = B[i] * ib; }
-    const double sg = F.m.sqrtg / (F.ok ? B2 : 1.0);
+    const double sg = F.m.sqrtg * (ib * ib);
     const double *D = F.D;
     F.vE[0] = sg * (D[1] * B[2] - D[2] * B[1]);
     F.vE[1] = sg * (D[2] * B[0] - D[0] * B[2]);
@@ -347,7 +357,7 @@ __device__ __forceinline__ void gr_frame(const KsGrid<FT> &g, double a, const do
     raise(F.m, F.vE, v);
     const double v2 = F.vE[0] * v[0] + F.vE[1] * v[1] + F.vE[2] * v[2];
     F.ok = F.ok && v2 < 1.0;
-    F.kappa = 1.0 / sqrt(F.ok ? 1.0 - v2 : 1.0);
+    F.kappa = rsqrt(F.ok ? 1.0 - v2 : 1.0);
     F.Dpar = D[0] * F.bdn[0] + D[1] * F.bdn[1] + D[2] * F.bdn[2];
 }
 
@@ -408,18 +418,19 @@ __device__ bool grgca_step(const KsGrid<FT> &g, const StepCfg &c, double qm, con
         gr_frame(g, c.a, Rb, true, Fb);
         okall = okall && Fb.ok;
         const double Gam = Fb.kappa * sqrt(1.0 + ub * ub + gr_perp2(Fb, c, mu, uperp));
+        const double iGam = 1.0 / Gam;
         const double ug = sqrt(gr_perp2(Fb, c, mu, uperp));
         double uf[3], w[3], vv[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             uf[i] = ub * Fb.bdn[i] + Fb.vE[i] * Gam + ug * bpg[i];
-            w[i] = ub * Fb.bdn[i] / Gam + Fb.vE[i];
+            w[i] = ub * iGam * Fb.bdn[i] + Fb.vE[i];
         }
         raise(Fb.m, w, vv);
         const double V[3] = {Fb.m.alpha * vv[0] - Fb.m.beta_r, Fb.m.alpha * vv[1],
                              Fb.m.alpha * vv[2]};
         double G[3];
-        geodesic_G(Fb.m, uf, Gam, G);
+        geodesic_G(Fb.m, uf, Gam, iGam, G);
         const double Gb = G[0] * Fb.bup[0] + G[1] * Fb.bup[1] + G[2] * Fb.bup[2];
         double res = 0.0;
 #pragma unroll
