@@ -182,3 +182,44 @@ def test_unknown_kick_basis_is_refused(G, wald):
     fields, st, p = wald
     with pytest.raises(RuntimeError, match="kick_basis"):
         G.KsGrid(fields, p["a"], p["r_in"], p["r_out"], kick_basis=3)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_ambient_region_on_gpu(G, dtype):
+    """The ambient-region test of Sec. 4.2 through the CUDA path: electrons
+    at rest at r = 5.5 r_g on the equator of the Wald field with
+    Omega_C0 = 10, 1e2, 1e3, 1e4 c/r_g (one species each), 191 steps of
+    2 pi / 60 to t = 20 r_g/c, f_rho = f_E = 1.  The branch of every step is
+    the oracle's (Boris throughout for rho_C0 = 0.1 r_g, GRGCA throughout
+    below), and so are the final positions (FP64 records: 1e-9 relative;
+    FP32 records: FP32 interpolation)."""
+    import math
+    fields, _, p = inputs.kerr_wald(nr=256, nth=256, Qm=0.0, n_particles=1, seed=0)
+    a = p["a"]
+    x0 = np.array([5.5, math.pi / 2, 0.0])
+    of = O.ks_grid_field(fields)
+    D, B = O.ks_gather(of, x0[0], x0[1])
+    m = O.ks_metric(a, x0[0], x0[1])
+    Bn = math.sqrt(B @ m["gdn"] @ B)
+    omegas = (10.0, 1e2, 1e3, 1e4)
+    qm = tuple(-w / Bn for w in omegas)
+    st = dict(x=np.repeat(x0[:, None], 4, axis=1), u=np.zeros((3, 4)), dxp=np.zeros((3, 4)),
+              flags=(np.arange(4, dtype=np.uint8) << 6))
+    q = dict(p, dt=2 * math.pi / 60, f_rho=1.0, f_E=1.0, qm=qm)
+    grid = G.KsGrid(fields, a, p["r_in"], p["r_out"], dtype=dtype)
+    ds = G.State.from_numpy(st, precision="fp64")
+    gp = G.make_params(q)
+    ref = copy_state(st)
+    of_, kp, op, dl = oracle_setup(fields, q)
+    Sg, So = [], []
+    for _ in range(191):
+        G.push_ks(ds, grid, gp, 1, stats=False)
+        Sg.append(ds.flags.cpu().numpy() & G.FLAG_S)
+        O.push_ks(ref, of_, kp, op, 1, dl=dl)
+        So.append(ref["flags"] & O.FLAG_S)
+    Sg, So = np.array(Sg), np.array(So)
+    np.testing.assert_array_equal(Sg, So)
+    assert Sg[:, 0].all() and not Sg[:, 1:].any()
+    got = ds.to_numpy()
+    tol = 1e-9 if dtype == "f64" else 1e-5
+    np.testing.assert_allclose(got["x"], ref["x"], rtol=tol, atol=tol)

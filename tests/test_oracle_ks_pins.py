@@ -387,3 +387,75 @@ def test_greom_steps_in_both_bases_agree():
     dx[2] = np.minimum(dx[2], 2 * np.pi - dx[2])
     assert dx.max() <= 1e-12 * np.abs(f["x"][:, live]).max()
     assert np.abs(f["u"] - g["u"])[:, live].max() <= 1e-12 * (np.abs(f["u"][:, live]).max() + 1)
+
+
+# ---------------------------------------------------------------------------
+# The ambient-region test of Sec. 4.2: electrons at rest at r = 5.5 r_g on the
+# equator of the Wald field, integrated to t = 20 r_g/c with f_rho = f_E = 1
+# and dt = 2 pi / 60 (the step that resolves the gyration at Omega_C0 = c/r_g)
+# ---------------------------------------------------------------------------
+AMBIENT_T = 20.0
+AMBIENT_DT = 2 * math.pi / 60
+
+
+@pytest.fixture(scope="module")
+def ambient():
+    from paper_2007_14401_gb300 import inputs
+    fields, _, p = inputs.kerr_wald(nr=256, nth=256, Qm=0.0, n_particles=1, seed=0)
+    of = O.ks_grid_field(fields)
+    dl = O.ks_cell_sizes(of, p["a"])
+    kp = O.ks_params(p["a"], p["r_in"], p["r_out"])
+    x0 = np.array([5.5, math.pi / 2, 0.0])
+    D, B = O.ks_gather(of, x0[0], x0[1])
+    m = O.ks_metric(p["a"], x0[0], x0[1])
+    Bn = math.sqrt(B @ m["gdn"] @ B)
+    return of, dl, kp, x0, Bn
+
+
+def ambient_run(amb, omega, dt, force, per_step=False):
+    """One electron with Omega_C0 = |q/m| B(x0) = omega (rho_C0 = r_g / omega)."""
+    of, dl, kp, x0, Bn = amb
+    n = int(round(AMBIENT_T / dt))
+    st = dict(x=x0[:, None].copy(), u=np.zeros((3, 1)), dxp=np.zeros((3, 1)),
+              flags=np.zeros(1, np.uint8))
+    op = O.make_params(dt=AMBIENT_T / n, f_rho=1.0, f_E=1.0, qm=(-omega / Bn,), force=force)
+    S = []
+    if per_step:
+        for _ in range(n):
+            O.push_ks(st, of, kp, op, 1, dl=dl)
+            S.append(int(st["flags"][0] & O.FLAG_S))
+    else:
+        O.push_ks(st, of, kp, op, n, dl=dl)
+    return st["x"][:, 0], np.array(S)
+
+
+def proper_distance(x, y):
+    return math.hypot(x[0] - y[0], y[0] * (x[1] - y[1]), y[0] * (x[2] - y[2]))
+
+
+@pytest.mark.parametrize("omega", [100.0, 1000.0])
+def test_ambient_region_coupled_pusher_tracks_the_resolved_orbit(ambient, omega):
+    """Sec. 4.2, ambient region: with rho_C0 <= 1e-2 r_g the sub-grid
+    gyration trips the f_rho test, so the coupled pusher takes GRGCA at every
+    step, and its trajectory stays on the gyro-resolved GREOM reference
+    (dt = 2 pi / (60 Omega_C0)) to within a couple of rho_C0, while plain
+    Boris at the coupled pusher's step drifts off by orders of magnitude more."""
+    x_c, S = ambient_run(ambient, omega, AMBIENT_DT, O.FORCE_NONE, per_step=True)
+    assert len(S) == 191 and not S.any()
+    x_ref, _ = ambient_run(ambient, omega, 2 * math.pi / (60 * omega), O.FORCE_BORIS)
+    x_b, _ = ambient_run(ambient, omega, AMBIENT_DT, O.FORCE_BORIS)
+    d_c, d_b = proper_distance(x_c, x_ref), proper_distance(x_b, x_ref)
+    assert d_c < 2.0 / omega, (d_c, 1 / omega)
+    assert d_b > 30 * d_c
+
+
+def test_ambient_region_resolved_gyration_stays_on_boris(ambient):
+    """rho_C0 = 1e-1 r_g: the gyro-radius exceeds the cell, the coupled
+    pusher never leaves Boris (so it is the Boris pusher) and stays on the
+    resolved reference to within the gyro-radius."""
+    x_c, S = ambient_run(ambient, 10.0, AMBIENT_DT, O.FORCE_NONE, per_step=True)
+    assert S.all()
+    x_b, _ = ambient_run(ambient, 10.0, AMBIENT_DT, O.FORCE_BORIS)
+    np.testing.assert_array_equal(x_c, x_b)
+    x_ref, _ = ambient_run(ambient, 10.0, 2 * math.pi / 600, O.FORCE_BORIS)
+    assert proper_distance(x_c, x_ref) < 0.1
