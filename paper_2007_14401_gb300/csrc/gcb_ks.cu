@@ -30,10 +30,54 @@ struct Metric {
     double dgrr[2], dgrp[2], dgtt[2], dgpp[2];   // d_i gamma^{..}
 };
 
-__device__ __forceinline__ void ks_metric(double a, double r, double th, bool derivs, Metric &m)
+// sin theta, cos theta and log r of a point
+struct TrigLog {
+    double s, c, lr;
+};
+
+__device__ __forceinline__ void trig_log(double r, double th, TrigLog &t)
 {
-    double s, c;
-    sincos(th, &s, &c);
+    sincos(th, &t.s, &t.c);
+    t.lr = log(r);
+}
+
+// The same at (r, th) near a point (r0, th0) whose values t0 are known
+// (ir0 = 1/r0): sin and cos by the angle-addition formula with the Maclaurin
+// series of sin d and cos d (d = th - th0, through d^7 and d^6), log r =
+// log r0 + log(1 + e) (e = r/r0 - 1) by the Mercator series through e^9.  For
+// |d| <= 0.02 and |e| <= 0.01 the truncation errors are below 1e-18; farther
+// away, or within sin th0 <= 0.05 of a pole (where sin th would lose relative
+// precision), the library functions.
+__device__ __forceinline__ void trig_log_near(const TrigLog &t0, double r0, double ir0, double th0,
+                                              double r, double th, TrigLog &t)
+{
+    const double d = th - th0;
+    const double e = (r - r0) * ir0;
+    if (!(fabs(d) <= 0.02 && fabs(e) <= 0.01 && fabs(t0.s) > 0.05)) {
+        trig_log(r, th, t);
+        return;
+    }
+    const double d2 = d * d;
+    const double sd = d * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0) * (1.0 - d2 * (1.0 / 42.0))));
+    const double cd = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0) * (1.0 - d2 * (1.0 / 30.0)));
+    t.s = fma(t0.s, cd, t0.c * sd);
+    t.c = fma(t0.c, cd, -t0.s * sd);
+    double q = 1.0 / 9.0;
+    q = fma(-e, q, 1.0 / 8.0);
+    q = fma(-e, q, 1.0 / 7.0);
+    q = fma(-e, q, 1.0 / 6.0);
+    q = fma(-e, q, 1.0 / 5.0);
+    q = fma(-e, q, 0.25);
+    q = fma(-e, q, 1.0 / 3.0);
+    q = fma(-e, q, 0.5);
+    q = fma(-e, q, 1.0);
+    t.lr = fma(e, q, t0.lr);
+}
+
+// (t: sin and cos of th)
+__device__ __forceinline__ void ks_metric(double a, double r, const TrigLog &t, bool derivs, Metric &m)
+{
+    const double s = t.s, c = t.c;
     const double s2 = s * s, a2 = a * a;
     const double rho2 = fma(r, r, a2 * c * c);
     const double irho2 = 1.0 / rho2;
@@ -141,10 +185,10 @@ struct KsGrid {
 
 // cell (clamped to the grid, so points just outside extrapolate the edge cell)
 template <typename FT>
-__device__ __forceinline__ void ks_cell(const KsGrid<FT> &g, double r, double th, int &i, int &j,
+__device__ __forceinline__ void ks_cell(const KsGrid<FT> &g, double lr, double th, int &i, int &j,
                                         double &tr, double &tt)
 {
-    double s = (log(r) - g.logr0) * g.inv_dlogr;
+    double s = (lr - g.logr0) * g.inv_dlogr;
     double q = th * g.inv_dth;
     double fi = fmin(fmax(floor(s), 0.0), (double)(g.nr - 2));
     double fj = fmin(fmax(floor(q), 0.0), (double)(g.nth - 2));
@@ -155,13 +199,14 @@ __device__ __forceinline__ void ks_cell(const KsGrid<FT> &g, double r, double th
 }
 
 // linear-shape-function gather of D^i, B^i (Sec. 4 intro) in the record type
+// (lr: log r)
 template <typename FT>
-__device__ __forceinline__ void ks_gather(const KsGrid<FT> &g, double r, double th, double D[3],
+__device__ __forceinline__ void ks_gather(const KsGrid<FT> &g, double lr, double th, double D[3],
                                           double B[3])
 {
     int i, j;
     double tr, tt;
-    ks_cell(g, r, th, i, j, tr, tt);
+    ks_cell(g, lr, th, i, j, tr, tt);
     FT acc[6] = {FT(0), FT(0), FT(0), FT(0), FT(0), FT(0)};
     const FT ftr = (FT)tr, ftt = (FT)tt;
 #pragma unroll
@@ -237,26 +282,26 @@ __device__ __forceinline__ void boris_global(const Metric &m, const double D[3],
 }
 
 // One GREOM half kick over alpha dt / 2 at x, in the basis c.basis selects
-// (m: the metric at x, returned for reuse)
+// (t: trigonometry and log r at x; m: the metric at x, returned for reuse)
 template <typename FT>
 __device__ __forceinline__ void half_kick(const KsGrid<FT> &g, const StepCfg &c, double qm,
-                                          const double x[3], double u[3], Metric &m)
+                                          const double x[3], const TrigLog &t, double u[3], Metric &m)
 {
-    ks_metric(c.a, x[0], x[1], false, m);
+    ks_metric(c.a, x[0], t, false, m);
     double D[3], B[3];
-    ks_gather(g, x[0], x[1], D, B);
+    ks_gather(g, t.lr, x[1], D, B);
     if (c.basis == GCB_KS_GLOBAL) {
         boris_global(m, D, B, qm, 0.5 * c.dt * m.alpha, u);
         return;
     }
     double Dh[3], Bh[3], uh[3];
-    Tri t;
-    make_tri(m, t);
-    cov_to_frame(t, u, uh);
-    con_to_frame(t, D, Dh);
-    con_to_frame(t, B, Bh);
+    Tri tri;
+    make_tri(m, tri);
+    cov_to_frame(tri, u, uh);
+    con_to_frame(tri, D, Dh);
+    con_to_frame(tri, B, Bh);
     boris_local(Dh, Bh, qm, 0.5 * c.dt * m.alpha, uh);
-    frame_to_cov(t, uh, u);
+    frame_to_cov(tri, uh, u);
 }
 
 // V^i = alpha gamma^{ij} u_j / Gamma - beta^i and
@@ -284,13 +329,14 @@ __device__ __forceinline__ bool imr_done(const StepCfg &c, int iters, double res
 }
 
 // GREOM: half kick, implicit midpoint for (x, u) (no field inside), half kick.
-// (mfin: the metric at x^{n+1})
+// (t0: trigonometry and log r at x^n; mfin: the metric at x^{n+1})
 template <typename FT>
 __device__ void greom_step(const KsGrid<FT> &g, const StepCfg &c, double qm, double x[3],
-                           double u[3], int &iters, bool &nonconv, Metric &mfin)
+                           double u[3], const TrigLog &t0, int &iters, bool &nonconv, Metric &mfin)
 {
+    const double ir0 = 1.0 / x[0];
     double up[3] = {u[0], u[1], u[2]};
-    half_kick(g, c, qm, x, up, mfin);
+    half_kick(g, c, qm, x, t0, up, mfin);
     double xk[3] = {x[0], x[1], x[2]}, wk[3] = {up[0], up[1], up[2]};
     iters = 0;
     nonconv = false;
@@ -298,8 +344,10 @@ __device__ void greom_step(const KsGrid<FT> &g, const StepCfg &c, double qm, dou
         double xb[3], ub[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) { xb[k] = 0.5 * (xk[k] + x[k]); ub[k] = 0.5 * (wk[k] + up[k]); }
+        TrigLog tb;
+        trig_log_near(t0, x[0], ir0, x[1], xb[0], xb[1], tb);
         Metric m;
-        ks_metric(c.a, xb[0], xb[1], true, m);
+        ks_metric(c.a, xb[0], tb, true, m);
         double v[3];
         raise(m, ub, v);
         const double Gam = sqrt(1.0 + ub[0] * v[0] + ub[1] * v[1] + ub[2] * v[2]);
@@ -320,7 +368,9 @@ __device__ void greom_step(const KsGrid<FT> &g, const StepCfg &c, double qm, dou
         ++iters;
         if (imr_done(c, iters, res, nonconv)) break;
     }
-    half_kick(g, c, qm, xk, wk, mfin);
+    TrigLog t1;
+    trig_log_near(t0, x[0], ir0, x[1], xk[0], xk[1], t1);
+    half_kick(g, c, qm, xk, t1, wk, mfin);
 #pragma unroll
     for (int k = 0; k < 3; ++k) { x[k] = xk[k]; u[k] = wk[k]; }
 }
@@ -332,13 +382,14 @@ struct GFrame {
     bool ok;
 };
 
+// (t: trigonometry and log r at R)
 template <typename FT>
 __device__ __forceinline__ void gr_frame(const KsGrid<FT> &g, double a, const double R[3],
-                                         bool derivs, GFrame &F)
+                                         const TrigLog &t, bool derivs, GFrame &F)
 {
-    ks_metric(a, R[0], R[1], derivs, F.m);
+    ks_metric(a, R[0], t, derivs, F.m);
     double B[3];
-    ks_gather(g, R[0], R[1], F.D, B);
+    ks_gather(g, t.lr, R[1], F.D, B);
     double Bd[3];
     lower(F.m, B, Bd);
     const double B2 = Bd[0] * B[0] + Bd[1] * B[1] + Bd[2] * B[2];
@@ -401,9 +452,10 @@ __device__ __forceinline__ double gr_perp2(const GFrame &F, const StepCfg &c, do
 // full velocity rebuilt at the midpoint, half kick (Sec. 2.4 steps 1-3).
 template <typename FT>
 __device__ bool grgca_step(const KsGrid<FT> &g, const StepCfg &c, double qm, const GFrame &F0,
-                           double R[3], double &upar, double mu, double uperp, const double bpg[3],
-                           int &iters, bool &nonconv, GFrame &F1)
+                           const TrigLog &t0, double R[3], double &upar, double mu, double uperp,
+                           const double bpg[3], int &iters, bool &nonconv, GFrame &F1)
 {
+    const double ir0 = 1.0 / R[0];
     const double u1 = fma(0.5 * c.dt * F0.m.alpha * qm, F0.Dpar, upar);
     double Rk[3] = {R[0], R[1], R[2]}, wk = u1;
     iters = 0;
@@ -414,8 +466,10 @@ __device__ bool grgca_step(const KsGrid<FT> &g, const StepCfg &c, double qm, con
 #pragma unroll
         for (int k = 0; k < 3; ++k) Rb[k] = 0.5 * (Rk[k] + R[k]);
         const double ub = 0.5 * (wk + u1);
+        TrigLog tb;
+        trig_log_near(t0, R[0], ir0, R[1], Rb[0], Rb[1], tb);
         GFrame Fb;
-        gr_frame(g, c.a, Rb, true, Fb);
+        gr_frame(g, c.a, Rb, tb, true, Fb);
         okall = okall && Fb.ok;
         const double Gam = Fb.kappa * sqrt(1.0 + ub * ub + gr_perp2(Fb, c, mu, uperp));
         const double iGam = 1.0 / Gam;
@@ -446,7 +500,9 @@ __device__ bool grgca_step(const KsGrid<FT> &g, const StepCfg &c, double qm, con
         if (imr_done(c, iters, res, nonconv)) break;
     }
     if (!okall) return false;
-    gr_frame(g, c.a, Rk, false, F1);   // also the reconstruction's frame
+    TrigLog t1;
+    trig_log_near(t0, R[0], ir0, R[1], Rk[0], Rk[1], t1);
+    gr_frame(g, c.a, Rk, t1, false, F1);   // also the reconstruction's frame
     if (!F1.ok) return false;
     upar = fma(0.5 * c.dt * F1.m.alpha * qm, F1.Dpar, wk);
 #pragma unroll
@@ -473,8 +529,8 @@ struct Args {
 // leaves it unchanged: it depends on theta through sin^2 and cos^2 only)
 template <typename FT>
 __device__ int ks_particle(const KsGrid<FT> &g, const StepCfg &c, double qm, int S, const GFrame &F0,
-                           double x[3], double u[3], int &iters, bool &nonconv, bool &fail,
-                           Metric &mfin)
+                           const TrigLog &t0, double x[3], double u[3], int &iters, bool &nonconv,
+                           bool &fail, Metric &mfin)
 {
     fail = false;
     if (S == 0) {
@@ -501,7 +557,7 @@ __device__ int ks_particle(const KsGrid<FT> &g, const StepCfg &c, double qm, int
                 for (int i = 0; i < 3; ++i) bpg[i] = ug[i] * iu;
                 mu = uperp * uperp / (2.0 * F0.Bmag * F0.kappa);
             }
-            ok = grgca_step(g, c, qm, F0, R, upar, mu, uperp, bpg, iters, nonconv, F1);
+            ok = grgca_step(g, c, qm, F0, t0, R, upar, mu, uperp, bpg, iters, nonconv, F1);
         }
         if (ok) {
             // reconstruction at R^{n+1} (frame F1 from the step), gyration
@@ -521,15 +577,18 @@ __device__ int ks_particle(const KsGrid<FT> &g, const StepCfg &c, double qm, int
         }
         fail = true;
     }
-    greom_step(g, c, qm, x, u, iters, nonconv, mfin);
+    greom_step(g, c, qm, x, u, t0, iters, nonconv, mfin);
     return 1;
 }
 
+// Three resident blocks per SM (at most 170 registers a thread, a few bytes of
+// spill): faster than two blocks without spills for this FP64-bound kernel.
 template <typename FT>
-__global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args a)
+__global__ void __launch_bounds__(TPB, 3) k_push_ks(const KsGrid<FT> g, const Args a)
 {
     __shared__ double s_x[3][TPB], s_u[3][TPB];
     __shared__ double s_F[NFR][TPB];
+    __shared__ double s_T[3][TPB];   // sin theta, cos theta, log r at x^n
     __shared__ uint8_t s_fl[TPB], s_S[TPB], s_ok[TPB];
     __shared__ unsigned short s_perm[TPB];
     __shared__ int s_wc[2][NWARP];
@@ -564,9 +623,14 @@ __global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args 
             if (fin && !(fl & (GCB_FLAG_NONFINITE | GCB_FLAG_EXITED))) {
                 // switch (Sec. 3, 4.2): Gamma/(|q/m| B) against the cell size of
                 // Eq. (volint), |D^|/|B^| against f_E; division-free form
+                TrigLog t;
+                trig_log(xs[0], xs[1], t);
                 GFrame F;
-                gr_frame(g, a.c.a, xs, false, F);
+                gr_frame(g, a.c.a, xs, t, false, F);
                 frame_store(s_F, tid, F);   // the step starts from this frame
+                s_T[0][tid] = t.s;
+                s_T[1][tid] = t.c;
+                s_T[2][tid] = t.lr;
                 s_ok[tid] = F.ok ? 1 : 0;
                 double v[3], Dd[3];
                 raise(F.m, us, v);
@@ -575,7 +639,7 @@ __global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args 
                 const double Em = sqrt(fmax(Dd[0] * F.D[0] + Dd[1] * F.D[1] + Dd[2] * F.D[2], 0.0));
                 int ci, cj;
                 double tr, tt;
-                ks_cell(g, xs[0], xs[1], ci, cj, tr, tt);
+                ks_cell(g, t.lr, xs[1], ci, cj, tr, tt);
                 const double dl = g.dl[(size_t)cj * (g.nr - 1) + ci];
                 const double Q = fabs(a.qm[(fl >> GCB_SPECIES_SHIFT) & 3]);
                 // B = 0 or v_E >= c: Boris
@@ -626,10 +690,11 @@ __global__ void __launch_bounds__(TPB) k_push_ks(const KsGrid<FT> g, const Args 
             GFrame F0;
             frame_load(s_F, sl, F0);
             F0.ok = s_ok[sl] != 0;
+            const TrigLog t0 = {s_T[0][sl], s_T[1][sl], s_T[2][sl]};
             int it = 0;
             bool ncv = false, fail = false;
             Metric mfin;
-            const int br = ks_particle(g, a.c, qm, S, F0, x, u, it, ncv, fail, mfin);
+            const int br = ks_particle(g, a.c, qm, S, F0, t0, x, u, it, ncv, fail, mfin);
             // poles: reflect theta, rotate phi by pi, flip u_theta
             if (x[1] < 0.0) { x[1] = -x[1]; x[2] += PI; u[1] = -u[1]; }
             if (x[1] > PI) { x[1] = 2.0 * PI - x[1]; x[2] += PI; u[1] = -u[1]; }
