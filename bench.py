@@ -94,7 +94,7 @@ WORKLOADS = {
         # + DMUL + DADD, ncu thread-instruction counts of this kernel at 2^18
         # particles) against the FP64 FMA peak 152 SMs x 2 DFMA/clk x 2 flops
         # x 2.07 GHz = 1.2586 TFLOP/s
-        alu=dict(flops=1925.1, peak=1.2586, peak_source="derived: 152 SMs x 2 DFMA/clk "
+        alu=dict(flops=1724.4, peak=1.2586, peak_source="derived: 152 SMs x 2 DFMA/clk "
                  "x 2 flop x 2.07 GHz (ncu peak_sustained dfma 304 inst/clk)")),
     "sheet3d": dict(
         gen=_gen_sheet3d, n=1 << 26, precision="mixed", grid="f32", sort_every=8,
