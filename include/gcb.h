@@ -351,8 +351,12 @@ gcb_status gcb_ks_cell_size(const gcb_grid_ks *g, const gcb_ks_params *kp, doubl
  * with rho~_C = Gamma/(|q/m| B) and E/B in the local frame of the normal
  * observer; GRGCA (decomposition at x^n, half kick of u_par by D_par,
  * implicit midpoint on (R, u_par), half kick, reconstruction at R^{n+1}) or
- * GREOM (local-frame Boris half kicks over alpha dt/2 around an implicit
- * midpoint geodesic step).  ws/out as gcb_push_sr (sorting unsupported here).
+ * GREOM (Boris half kicks over alpha dt/2, in the local frame or the global
+ * basis as kp->kick_basis selects, around an implicit midpoint geodesic
+ * step).  ws/out as gcb_push_sr (sorting unsupported here).
+ * Errors: GCB_EINVAL for an invalid grid, spin, radii, kick_basis or
+ * parameter; GCB_EUNSUPPORTED for particles that are not ndim 3 with FP64
+ * positions and momenta.
  */
 gcb_status gcb_push_ks(const gcb_particles *p, const gcb_grid_ks *g, const gcb_ks_params *kp,
                        const gcb_params *prm, int n_steps, void *cuda_stream, void *ws,
