@@ -26,16 +26,24 @@ namespace gcb {
 template <typename R>
 struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : GCB_TILE_F32; };
 
-// minimum resident blocks per SM requested from the register allocator
 // 1: tiles whose particles all take one branch skip the staging (see k_push_sr)
 #ifndef GCB_UNIFORM_TILES
 #define GCB_UNIFORM_TILES 1
 #endif
+// minimum resident blocks per SM requested from the register allocator
 #ifndef GCB_MIN_BLOCKS_F32
 #define GCB_MIN_BLOCKS_F32 4
 #endif
+// 3D FP32: three blocks (at most 170 registers a thread; 184 unconstrained,
+// which leaves two) take the 3D sheet push from 2.53 to 2.11 ms at 2^24
+// particles; four (128 registers) spill and gain nothing more
+#ifndef GCB_MIN_BLOCKS_F32_3D
+#define GCB_MIN_BLOCKS_F32_3D 3
+#endif
 template <typename R, int ND>
-struct MinBlocks { static constexpr int n = (sizeof(R) == 8 || ND == 3) ? 1 : GCB_MIN_BLOCKS_F32; };
+struct MinBlocks {
+    static constexpr int n = sizeof(R) == 8 ? 1 : (ND == 3 ? GCB_MIN_BLOCKS_F32_3D : GCB_MIN_BLOCKS_F32);
+};
 
 template <typename R>
 struct PushArgs {
