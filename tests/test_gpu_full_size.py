@@ -71,7 +71,7 @@ def rows_by_pid(G, ds, pids):
     return out
 
 
-def assert_permutation(G, ds):
+def assert_permutation(ds):
     import torch
     seen = torch.zeros(ds.n, dtype=torch.int32, device=ds.pid.device)
     seen.index_add_(0, ds.pid, torch.ones_like(ds.pid, dtype=torch.int32))
@@ -129,9 +129,9 @@ def flat_run(request, G):
                                              else s[q]) for q in s}
         if k == 0:
             out["step1"] = rows_by_pid(G, ds, pids)
-            assert_permutation(G, ds)
+            assert_permutation(ds)
     out["step9"] = rows_by_pid(G, ds, pids)
-    assert_permutation(G, ds)
+    assert_permutation(ds)
     out["counted"] = counted(total, n, 9)
     del ds, ws, grid
     torch.cuda.empty_cache()
