@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -100,3 +101,17 @@ def test_argument_errors_without_gpu(G):
         rc = lib.gcb_ks_cell_size(C.byref(ks), C.byref(G.GcbKsParams(0.9, 1.5, 50.0, basis)),
                                   C.c_void_p(4096), None)
         assert rc == want and b"kick_basis" in lib.gcb_last_error()
+
+
+def test_binding_fails_loudly_without_the_library():
+    """No CPU fallback: importing the binding with the CUDA library absent raises."""
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import paper_2007_14401_gb300.build as b\n"
+            "b.LIB = b.LIB + '.absent'\n"
+            "try:\n"
+            "    import paper_2007_14401_gb300.gcb\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e); sys.exit(0)\n"
+            "sys.exit(3)\n") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "is not built" in r.stdout, r.stdout + r.stderr
