@@ -71,8 +71,8 @@ WORKLOADS = {
     "reconnection2d": dict(
         gen=_gen_reconnection, n=1 << 24, precision="mixed", grid="f32", sort_every=8,
         tile=(1, 1), state_b=37, field_b=2048 * 1024 * 48, fp64_b=(57, 2048 * 1024 * 96),
-        desc="2D double Harris + GEM + 64 modes, 2048x1024 grid, {n} particles, mixed FP32 "
-             "(FP32-pair positions)",
+        desc="2D double Harris + GEM + 64 modes, 2048x1024 grid, {n} particles",
+        prec="mixed: FP32 fields and arithmetic, FP32-pair positions",
         extra=dict(grid=[2048, 1024], dt=0.45, omega_c_dt_max=1e5, curvature=1,
                    grad_mode="grid", gca_tol=1e-7),
         # DRAM bytes (read + write) of one push launch at 2^24 particles, from
@@ -82,13 +82,15 @@ WORKLOADS = {
     "harris2d_fp64": dict(
         gen=_gen_harris, n=16384, precision="fp64", grid="f64", sort_every=0, tile=(1, 1),
         state_b=57, field_b=128 * 128 * 48, fp64_b=None,
-        desc="2D Harris sheet 128x128, {n} particles (q/m = -1, -10, -1e2, -1e3), FP64",
+        desc="2D Harris sheet 128x128, {n} particles (q/m = -1, -10, -1e2, -1e3)",
+        prec="FP64 fields, state and arithmetic",
         extra=dict(grid=[128, 128], dt=1.0, curvature=1, grad_mode="dw", gca_tol=1e-7)),
     "kerr_wald": dict(
         gen=_gen_kerr, n=1 << 22, precision="ks", grid="f32", sort_every=0, tile=(1, 1),
         state_b=49, field_b=512 * 512 * 32, fp64_b=None,
         desc="Kerr-Schild a=0.9, Wald field + split monopole, 512x512 (log r, theta) grid, "
-             "{n} electrons, |q/m| = 1e3, FP32 field records, FP64 metric and state",
+             "{n} electrons, |q/m| = 1e3",
+        prec="FP32 field records, FP64 metric, state and arithmetic",
         extra=dict(grid=[512, 512], dt=0.02, spin=0.9),
         # FP64-issue bound: FP64 flops per particle-step as executed (2 DFMA
         # + DMUL + DADD, ncu thread-instruction counts of this kernel at 2^18
@@ -100,13 +102,15 @@ WORKLOADS = {
         gen=_gen_sheet3d, n=1 << 26, precision="mixed", grid="f32", sort_every=8,
         tile=(1, 1, 1), state_b=49, field_b=256 ** 3 * 32, fp64_b=(73, 256 ** 3 * 48),
         desc="3D kinked Harris sheet 256^3, guide 0.3, {n} particles (70% MJ upstream, 30% "
-             "power law in the sheet), |q/m| = 20, mixed FP32 (FP32-pair positions)",
+             "power law in the sheet), |q/m| = 20",
+        prec="mixed: FP32 fields and arithmetic, FP32-pair positions",
         extra=dict(grid=[256, 256, 256], dt=0.45, curvature=1, grad_mode="dw", gca_tol=1e-7)),
     "sheet3d_literal": dict(
         gen=_gen_sheet3d_literal, n=1 << 26, precision="mixed", grid="f32", sort_every=8,
         tile=(1, 1, 1), state_b=49, field_b=256 ** 3 * 32, fp64_b=(73, 256 ** 3 * 48),
         desc="3D kinked Harris sheet 256^3, guide 0.3, {n} particles (70% MJ upstream, 30% "
-             "power law in the sheet), |q/m| = 2.1e6 (all GCA), mixed FP32 (FP32-pair positions)",
+             "power law in the sheet), |q/m| = 2.1e6 (all GCA)",
+        prec="mixed: FP32 fields and arithmetic, FP32-pair positions",
         extra=dict(grid=[256, 256, 256], dt=0.45, curvature=1, grad_mode="dw", gca_tol=1e-7)),
 }
 
@@ -128,6 +132,75 @@ ADJOINT = dict(gen=_gen_adjoint, n=1 << 20,
                     "at each), mixed FP32 forward + "
                     "FP32 adjoint, FP64 node accumulators; L = mean final kinetic energy, "
                     "gradients w.r.t. the 64 mode amplitudes and all initial states")
+
+
+def omega_c_dt(fields, p, x, u, flags):
+    """Omega_C dt = |q/m| |B(x)| dt / (c Gamma) of every particle (host
+    diagnostic of the bench line, float64): |B| interpolated at x with the
+    linear shape functions of the grid, Gamma from the full momentum."""
+    B = np.sqrt(sum(np.asarray(b, dtype=np.float64) ** 2 for b in fields["B"]))
+    shape = B.shape                       # (ny, nx) or (nz, ny, nx)
+    nd = len(shape)
+    dx = fields["dx"]
+    c = p.get("c", 1.0)
+    qm = np.abs(np.asarray(list(p["qm"]) + [0.0] * 4, dtype=np.float64))
+    out = np.empty(x.shape[1])
+    step = 1 << 21
+    for a in range(0, x.shape[1], step):
+        b = min(x.shape[1], a + step)
+        s = [x[d, a:b] / dx[d] for d in range(nd)]
+        i0 = [np.floor(v).astype(np.int64) for v in s]
+        t = [v - i for v, i in zip(s, i0)]
+        n_ax = list(reversed(shape))      # nodes along x, y, (z)
+        acc = np.zeros(b - a)
+        for o in range(1 << nd):
+            w = np.ones(b - a)
+            idx = []
+            for d in range(nd):
+                hi = (o >> d) & 1
+                w *= t[d] if hi else 1.0 - t[d]
+                idx.append((i0[d] + hi) % n_ax[d])
+            acc += w * B[tuple(reversed(idx))]
+        gam = np.sqrt(1.0 + np.sum(u[:, a:b].astype(np.float64) ** 2, axis=0) / c ** 2)
+        out[a:b] = qm[(flags[a:b].astype(np.int64) >> 6) & 3] * acc * p["dt"] / (c * gam)
+    return out
+
+
+def coupling_report(G, multi, ds, grid, gp, ws, ks, snap, step_first, steps, fields, p):
+    """Branch mix of the timed steps: the state at the first timed step is
+    restored and the same steps are replayed (same step indices, hence the
+    same sorts) one call each with its statistics, reduced over the ranks
+    after every call; Omega_C dt of this rank's particles at the first timed
+    step."""
+    for t, s in zip(ds.tensors(), snap):
+        t.copy_(s)
+    tot = None
+    for k in range(steps):
+        gp.step_index = step_first + k
+        s = G.push_ks(ds, grid, gp, 1) if ks else G.push(ds, grid, gp, 1, workspace=ws)
+        s = multi.reduce_stats(s, device="cuda")
+        if tot is None:
+            tot = dict(s)
+        else:
+            for key, v in s.items():
+                tot[key] = max(tot[key], v) if key == "max_iter" else tot[key] + v
+    ps = tot["n_boris"] + tot["n_gca"]
+    mix = {"timed_steps": steps, "particle_steps": ps, "boris": tot["n_boris"],
+           "gca": tot["n_gca"], "boris_fraction": tot["n_boris"] / max(1, ps),
+           "to_gca": tot["n_to_gca"], "to_boris": tot["n_to_boris"],
+           "mean_iter": tot["sum_iter"] / max(1, tot["n_gca"]), "max_iter": tot["max_iter"],
+           "nonconv": tot["n_nonconv"], "gcafail": tot["n_gcafail"],
+           "nonfinite": tot["n_nonfinite"]}
+    if not ks:
+        x = snap[0].double().cpu().numpy()
+        if ds.x_lo is not None:
+            x = x + snap[4].double().cpu().numpy()
+        om = omega_c_dt(fields, p, x, snap[1].cpu().numpy(), snap[3].cpu().numpy())
+        om = om[np.isfinite(om)]
+        mix["omega_c_dt_first_step"] = {"min": float(om.min()), "median": float(np.median(om)),
+                                        "max": float(om.max()),
+                                        "particles": int(om.size)}
+    return mix
 
 
 def workload_config(w, n_total, ngpu, sort_every, sort_tile):
@@ -257,11 +330,12 @@ def run_reference(args, rank, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": dict(workload_config(w, w["n"] * args.gpus, args.gpus, w["sort_every"],
-                                           w["tile"]),
-                           sample=f"{n} particles per step (bounded sample)"),
+            "precision": "FP64 oracle (plain C, OpenMP over particles, host cores)",
+            "config": workload_config(w, w["n"] * args.gpus, args.gpus, w["sort_every"],
+                                      w["tile"]),
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
-                             "sample": f"{n} particles x {args.steps} steps, FP64 oracle"},
+                             "sample": f"{n} particles of the workload per step (bounded "
+                                       f"sample) x {args.steps} steps, FP64 oracle"},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -360,6 +434,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fused", action="store_true",
                     help="skip the test-particle (fused-step) measurement")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint / forward cost ratio of the default line")
     ap.add_argument("--e2e-chunks", type=int, default=8,
                     help="particle chunks streamed through the GPU in the end-to-end timing")
     ap.add_argument("--sort-every", type=int, default=None)
@@ -431,6 +507,9 @@ def main():
     for _ in range(args.warmup):
         one_step()
     barrier()
+    # the state at the first timed step, for replaying the timed steps with
+    # their statistics afterwards (the push is deterministic per particle)
+    snap, step_first = [t.clone() for t in ds.tensors()], step[0]
     clk = ClockSampler(local)
     clk.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -457,7 +536,9 @@ def main():
     n = ds.n
     # whole job: all ranks' particle-steps over the slowest rank's time
     value, ms, n_all = multi.whole_job_rate(n, args.steps, ms, device="cuda")
-    stats = G.push_ks(ds, grid, gp, 1) if ks else G.push(ds, grid, gp, 1, workspace=ws)
+    mix = coupling_report(G, multi, ds, grid, gp, ws, ks, snap, step_first, args.steps, fields,
+                          p)
+    del snap
 
     # end to end through host buffers: per step, the state is copied in from
     # pinned host memory, pushed, and copied back out
@@ -545,6 +626,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if w["precision"] == "mixed" else "f64", "data": "synthetic",
+                "precision": w["prec"],
                 "config": dict(workload_config(w, n_all, world, sort_every, tile),
                                **({"kick_basis": args.ks_kick} if ks else {})),
                 "roofline": roofline,
@@ -555,11 +637,10 @@ def main():
                                                / max(1, n_sorts)),
                          "ms_push_kernel": avg_launch},
                 "clocks": clocks,
-                "branch_mix": {"boris": stats["n_boris"], "gca": stats["n_gca"],
-                               "mean_iter": stats["sum_iter"] / max(1, stats["n_gca"]),
-                               "max_iter": stats["max_iter"], "nonconv": stats["n_nonconv"],
-                               "gcafail": stats["n_gcafail"]},
+                "branch_mix": mix,
                 "fp64": fp64, "test_particle_mode": tpm}
+        if not args.no_adjoint and args.workload == "reconnection2d":
+            line["adjoint_vs_forward"] = adjoint_vs_forward(G)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(fields, st, p)
         print(json.dumps(line), flush=True)
@@ -584,6 +665,71 @@ def adjoint_launches():
     return forward + sweep
 
 
+def adjoint_setup(G, n_req, seed, reduce=lambda g: g):
+    """The adjoint workload on the current GPU: returns (n, lam, forward,
+    backward, number of modes); forward() runs ADJ_STEPS pushes from the initial state storing
+    the checkpoints, backward() the reverse sweep for L = mean final kinetic
+    energy, returning dL/da_m (passed through ``reduce``)."""
+    import torch
+    base, pats, amps, st, p = ADJOINT["gen"](n_req, seed)
+    grid = G.Grid(base, dtype="f32")
+    base_rec = grid.rec.clone()
+    pat_rec = torch.stack([G.Grid(q, dtype="f32").rec for q in pats]).contiguous()
+    amps_d = torch.tensor(amps, dtype=torch.float64, device="cuda")
+    G.grid_combine(grid, base_rec, pat_rec, amps_d)
+    init = G.State.from_numpy(st, precision="mixed", pos_mode="pair")
+    # checkpoints sorted by cell: the segments run on cell-ordered particles
+    gp = G.make_params(p, gca_fixed_iters=ADJ_FIXED_ITERS, sort_every=ADJ_CKPT, sort_tile=(1, 1))
+    n = init.n
+    cur = init.clone()
+    lam = torch.empty((7, n), dtype=torch.float32, device="cuda")
+    aws = G.AdjointWorkspace(cur, grid, ADJ_STEPS, ADJ_CKPT, gp)
+
+    def forward():
+        # the forward pass stores the checkpoints the reverse sweep starts from
+        for t_, s_ in zip(cur.tensors(), init.tensors()):
+            t_.copy_(s_)
+        G.push_ckpt(cur, grid, gp, ADJ_STEPS, aws)
+
+    def backward():
+        # dL/du_final for L = mean (Gamma - 1) c^2: u / (Gamma n)
+        Gm = torch.sqrt(1.0 + (cur.u * cur.u).sum(0))
+        lam.zero_()
+        lam[2:5] = cur.u / (Gm * n)
+        grad = G.adjoint(init, grid, gp, ADJ_STEPS, lam, ADJ_CKPT, workspace=aws)
+        return reduce(G.grad_project(grid, grad, pat_rec))
+
+    return n, lam, forward, backward, len(amps)
+
+
+def adjoint_vs_forward(G, reps=3):
+    """One GPU: the adjoint workload's forward (ADJ_STEPS pushes storing the
+    checkpoints) and reverse sweep, each timed with CUDA events; medians of
+    ``reps`` after one untimed pair."""
+    import torch
+    n, _, forward, backward, _ = adjoint_setup(G, ADJOINT["n"], 1)
+    forward()
+    backward()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    tf, tb = [], []
+    for _ in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        forward()
+        e[1].record(stream)
+        backward()
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        tf.append(e[0].elapsed_time(e[1]))
+        tb.append(e[1].elapsed_time(e[2]))
+    ms_f, ms_b = statistics.median(tf), statistics.median(tb)
+    return {"workload": ADJOINT["desc"].format(n=n), "ms_forward": ms_f, "ms_reverse": ms_b,
+            "reverse_over_forward": ms_b / ms_f, "reps": reps,
+            "note": "forward = the push steps storing the checkpoints; reverse = recomputed "
+                    "segments + the adjoint kernel per step + the mode projection"}
+
+
 def run_adjoint(args):
     """Forward ADJ_STEPS pushes + reverse sweep on one GPU (replicas only under
     torchrun: each rank differentiates its own particles, and the 64 mode
@@ -599,36 +745,10 @@ def run_adjoint(args):
     from paper_2007_14401_gb300 import gcb as G
     from paper_2007_14401_gb300 import multi
     n_req = ADJOINT["n"] if args.particles is None else args.particles
-    base, pats, amps, st, p = ADJOINT["gen"](n_req, multi.rank_seed(rank))
-    grid = G.Grid(base, dtype="f32")
-    base_rec = grid.rec.clone()
-    pat_rec = torch.stack([G.Grid(q, dtype="f32").rec for q in pats]).contiguous()
-    amps_d = torch.tensor(amps, dtype=torch.float64, device="cuda")
-    G.grid_combine(grid, base_rec, pat_rec, amps_d)
-    init = G.State.from_numpy(st, precision="mixed", pos_mode="pair")
-    # checkpoints sorted by cell: the segments run on cell-ordered particles
-    gp = G.make_params(p, gca_fixed_iters=ADJ_FIXED_ITERS, sort_every=ADJ_CKPT, sort_tile=(1, 1))
-    n = init.n
-    cur = init.clone()
-    lam = torch.empty((7, n), dtype=torch.float32, device="cuda")
+    # the amplitudes are shared by all ranks: their gradients are summed
+    n, lam, forward, backward, n_modes = adjoint_setup(G, n_req, multi.rank_seed(rank),
+                                                       multi.sum_over_ranks)
     stream = torch.cuda.current_stream()
-
-    aws = G.AdjointWorkspace(cur, grid, ADJ_STEPS, ADJ_CKPT, gp)
-
-    def forward():
-        # the forward pass stores the checkpoints the reverse sweep starts from
-        for t_, s_ in zip(cur.tensors(), init.tensors()):
-            t_.copy_(s_)
-        G.push_ckpt(cur, grid, gp, ADJ_STEPS, aws)
-
-    def backward():
-        # dL/du_final for L = mean (Gamma - 1) c^2: u / (Gamma n)
-        Gm = torch.sqrt(1.0 + (cur.u * cur.u).sum(0))
-        lam.zero_()
-        lam[2:5] = cur.u / (Gm * n)
-        grad = G.adjoint(init, grid, gp, ADJ_STEPS, lam, ADJ_CKPT, workspace=aws)
-        # the amplitudes are shared by all ranks: sum their gradients
-        return multi.sum_over_ranks(G.grad_project(grid, grad, pat_rec))
 
     for _ in range(args.warmup if args.steps > 1 else 1):
         forward()
@@ -666,7 +786,7 @@ def run_adjoint(args):
                 "config": {"workload": ADJOINT["desc"].format(n=n), "particles": n,
                            "push_steps_per_step": ADJ_STEPS, "ckpt_every": ADJ_CKPT,
                            "gca_fixed_iters": ADJ_FIXED_ITERS, "grid": [512, 256],
-                           "modes": len(amps),
+                           "modes": n_modes,
                            "l2": "particle state 39 MB fits L2; checkpoints 620 MB do not"},
                 "adjoint": {"ms_forward": ms_f, "ms_reverse": ms_b,
                             "reverse_over_forward": ms_b / ms_f,

@@ -381,9 +381,13 @@ gcb_status gcb_push_ks(const gcb_particles *p, const gcb_grid_ks *g, const gcb_k
  *   needs more scratch than the array holds -- sorting (prm->sort_every > 0)
  *   needs about 75 bytes per particle, so it fits only small problems;
  *   without sorting the need is 256 bytes.
- *   The first call on a device looks up the array's device address with
- *   cudaGetSymbolAddress (make it before any stream capture).  All calls
- *   share the array: calls whose GPU work overlaps race on it.
+ *   Each call looks up the array's device address with
+ *   cudaGetSymbolAddress on the current device, so an address made stale by
+ *   a device reset is never reused.  While its stream is capturing, a call
+ *   does not look the address up: it takes the one the last call outside a
+ *   capture found on that device, and fails with GCB_EINVAL if there is
+ *   none, so make the first call on each device before any stream capture.
+ *   All calls share the array: calls whose GPU work overlaps race on it.
  */
 gcb_status gcb_push_sr_noalloc(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
                                int n_steps, void *cuda_stream, gcb_stats *out);

@@ -12,12 +12,17 @@
 //
 // The array below lives in every device context that loads this library and
 // stays there until the process exits (GCB_NOALLOC_SCRATCH_BYTES per GPU).
-// Its name is a host-side stand-in, not a device address, so the first call
-// on each device looks the address up with cudaGetSymbolAddress while that
-// device is current and caches it; make that first call before any stream
-// capture.  Every call shares the one array: gcb_push_sr clears what must
-// start at zero at the start of each call, and two calls whose work overlaps
-// on the GPU (different streams, or different host threads) race on it.
+// Its name is a host-side stand-in, not a device address, so each call looks
+// the address up with cudaGetSymbolAddress while the call's device is
+// current.  Looking it up again on every call keeps a device reset
+// (cudaDeviceReset unloads the module, which may put the array elsewhere
+// when it is reloaded) from leaving a stale address behind.  While the
+// call's stream is capturing, no lookup is made (it may load the module);
+// the address the last call outside a capture found on that device is used,
+// so the first call on each device must come before any stream capture.
+// Every call shares the one array: gcb_push_sr clears what must start at
+// zero at the start of each call, and two calls whose work overlaps on the
+// GPU (different streams, or different host threads) race on it.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -51,10 +56,16 @@ extern "C" gcb_status gcb_push_sr_noalloc(const gcb_particles *p, const gcb_grid
         gcb::set_error("gcb_push_sr_noalloc: no usable current device");
         return GCB_ECUDA;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)cuda_stream, &cap) != cudaSuccess) {
+        gcb::set_error("gcb_push_sr_noalloc: cudaStreamIsCapturing failed: %s",
+                       cudaGetErrorString(cudaGetLastError()));
+        return GCB_ECUDA;
+    }
     void *ptr = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void *a = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&a, g_scratch);
             if (e != cudaSuccess || !a) {
@@ -63,6 +74,10 @@ extern "C" gcb_status gcb_push_sr_noalloc(const gcb_particles *p, const gcb_grid
                 return GCB_ECUDA;
             }
             g_ptr[dev] = a;
+        } else if (!g_ptr[dev]) {
+            gcb::set_error("gcb_push_sr_noalloc: the first call on a device must not be made "
+                           "while its stream is capturing a graph");
+            return GCB_EINVAL;
         }
         ptr = g_ptr[dev];
     }

@@ -3,9 +3,10 @@
 Test particles in static fields do not interact, so the push exchanges
 nothing between ranks.  What crosses ranks is bookkeeping: the step time (the
 whole job is as slow as its slowest rank: max), the particle count (sum),
-and, after an adjoint sweep, the gradients with respect to shared inputs such
-as the field-mode amplitudes (sum).  Each function is a no-op reduction when
-no process group is initialised.
+the push statistics (counters and the kinetic-energy sum: sum; the largest
+fixed-point iteration count: max), and, after an adjoint sweep, the gradients
+with respect to shared inputs such as the field-mode amplitudes (sum).  Each
+function is a no-op reduction when no process group is initialised.
 """
 from __future__ import annotations
 
@@ -42,3 +43,24 @@ def sum_over_ranks(x: torch.Tensor) -> torch.Tensor:
     if _group_size() > 1:
         dist.all_reduce(x, op=dist.ReduceOp.SUM)
     return x
+
+
+# gcb_stats fields summed over ranks (the rest: max_iter, a maximum)
+STATS_SUM = ("n_boris", "n_gca", "n_to_gca", "n_to_boris", "n_nonconv", "n_gcafail",
+             "n_nonfinite", "sum_iter", "sum_ekin")
+
+
+def reduce_stats(stats: dict, device="cpu") -> dict:
+    """Whole-job statistics of one push call from each rank's: one SUM
+    allreduce of the counters and the kinetic-energy sum (float64, exact for
+    counts below 2^53) and one MAX allreduce of max_iter.  Returns a new dict
+    with the same keys; the identity without a process group."""
+    s = torch.tensor([float(stats[k]) for k in STATS_SUM], dtype=torch.float64, device=device)
+    m = torch.tensor([int(stats["max_iter"])], dtype=torch.int64, device=device)
+    if _group_size() > 1:
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    out = {k: (float(v) if k == "sum_ekin" else int(round(float(v))))
+           for k, v in zip(STATS_SUM, s.tolist())}
+    out["max_iter"] = int(m.item())
+    return {k: out[k] for k in stats}

@@ -33,9 +33,14 @@ def test_reference_arm_line(workload):
     assert line["metric"] == line["unit"] == "particle-steps/s"
     assert line["value"] > 0 and line["higher_is_better"] is True
     assert line["steps"] == 1 and line["warmup"] == 3 and line["n_gpus"] == 1
-    assert line["config"]["workload"] and "sample" in line["config"]
+    # the same config as the GPU arm's line (the workload, not a precision)
+    w = bench.WORKLOADS[workload]
+    assert line["config"] == json.loads(json.dumps(
+        bench.workload_config(w, w["n"], 1, w["sort_every"], w["tile"])))
+    assert "FP64 oracle" in line["precision"] and line["dtype"] == "f64"
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert "bounded sample" in cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
@@ -69,3 +74,24 @@ def test_adjoint_launch_count():
     (529)."""
     assert (bench.ADJ_STEPS, bench.ADJ_CKPT) == (256, 16)
     assert bench.adjoint_launches() == 368 + 529
+
+
+def test_omega_c_dt_closed_forms():
+    """The bench line's Omega_C dt diagnostic: |q/m| |B| dt / (c Gamma) with
+    |B| interpolated linearly between nodes (exact for a field linear in x,
+    periodic wrap at the last cell), Gamma from the full momentum."""
+    import numpy as np
+    nx, ny = 8, 4
+    X = np.tile(np.arange(nx, dtype=float), (ny, 1))
+    Bz = 1.0 + 0.5 * X                     # |B| = 1 + x/2 on the nodes
+    zero = np.zeros((ny, nx))
+    fields = {"E": [zero, zero, zero], "B": [zero, zero, Bz], "dx": (1.0, 1.0)}
+    p = {"qm": (-2.0, 3.0), "dt": 0.5, "c": 1.0}
+    x = np.array([[0.0, 2.25, 6.5, 7.5], [0.1, 1.0, 3.9, 2.0]])
+    u = np.array([[0.0, 1.0, 0.0, 0.0], [0.0, 0.0, 2.0, 0.0], [0.0, 0.0, 0.0, 0.0]])
+    flags = np.array([0, 64, 0, 64], dtype=np.uint8)   # species 0, 1, 0, 1
+    got = bench.omega_c_dt(fields, p, x, u, flags)
+    Bx = np.array([1.0, 2.125, 4.25, 0.5 * (4.5 + 1.0)])     # last: wraps to node 0
+    gam = np.sqrt(1 + np.array([0.0, 1.0, 4.0, 0.0]))
+    want = np.array([2.0, 3.0, 2.0, 3.0]) * Bx * 0.5 / gam
+    assert np.allclose(got, want, rtol=1e-14)

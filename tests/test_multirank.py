@@ -1,9 +1,11 @@
 """The multi-rank bookkeeping on two gloo ranks (CPU): whole-job throughput
-over the slowest rank, particle totals, the sum of per-rank gradients, and
-distinct per-rank seeds."""
+over the slowest rank, particle totals, the sum of per-rank gradients,
+distinct per-rank seeds, and the push statistics reduced over ranks that
+each push their own shard of one particle set."""
 import os
 import socket
 
+import numpy as np
 import pytest
 import torch
 import torch.distributed as dist
@@ -54,3 +56,60 @@ def test_single_process_is_identity():
     assert (ms, total) == (4.0, 500) and rate == pytest.approx(500 * 2 / 4e-3)
     x = torch.ones(3)
     assert torch.equal(multi.sum_over_ranks(x), torch.ones(3))
+
+
+def _shard_worker(rank, world, port, out):
+    """Each rank pushes its contiguous shard of one particle set with the
+    FP64 oracle and reduces the statistics over the ranks."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle as O
+        from paper_2007_14401_gb300 import inputs, multi
+        from tests.helpers import oracle_field, oracle_params
+        fields, st, p = inputs.harris_2d(n_per_species=96, seed=5)
+        n = st["flags"].size
+        lo, hi = n * rank // world, n * (rank + 1) // world
+        shard = inputs.subset(st, np.arange(lo, hi))
+        of, op = oracle_field(fields), oracle_params(p)
+        per_call = []
+        for _ in range(3):                    # one reduction per push call
+            s = O.push_sr(shard, of, op, 4, nthreads=1)
+            per_call.append(multi.reduce_stats(s))
+        out[rank] = per_call
+    finally:
+        dist.destroy_process_group()
+
+
+def test_stats_reduced_over_rank_shards_equal_one_process(orc):
+    """Two gloo ranks each push half of the Harris particle set (the oracle
+    per rank, the four q/m species spread over both); the statistics reduced
+    over the ranks after every call equal those of one process pushing the
+    whole set."""
+    from paper_2007_14401_gb300 import inputs
+    from tests.helpers import oracle_field, oracle_params
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_shard_worker, args=(world, _free_port(), out), nprocs=world,
+                       start_method="spawn")
+    fields, st, p = inputs.harris_2d(n_per_species=96, seed=5)
+    of, op = oracle_field(fields), oracle_params(p)
+    whole = [orc.push_sr(st, of, op, 4, nthreads=1) for _ in range(3)]
+    for r in range(world):
+        for got, ref in zip(out[r], whole):
+            for k, v in ref.items():
+                if k == "sum_ekin":
+                    assert got[k] == pytest.approx(v, rel=1e-12)
+                else:
+                    assert got[k] == v, k
+    assert whole[0]["n_gca"] > 0 and whole[0]["n_boris"] > 0
+    assert out[0] == out[1]
+
+
+def test_reduce_stats_single_process_is_identity():
+    from paper_2007_14401_gb300 import multi
+    s = {"n_boris": 3, "n_gca": 5, "n_to_gca": 1, "n_to_boris": 0, "n_nonconv": 0,
+         "n_gcafail": 0, "n_nonfinite": 0, "sum_iter": 15, "max_iter": 4, "sum_ekin": 0.25}
+    assert multi.reduce_stats(s) == s
