@@ -33,8 +33,12 @@ MU_CONSERVE, UPERP_CONSERVE = 0, 1
 FLAG_S, FLAG_SPREV, FLAG_NONCONV, FLAG_GCAFAIL, FLAG_NONFINITE, FLAG_EXITED = 1, 2, 4, 8, 16, 32
 KS_GRID, KS_VACUUM, KS_MONOPOLE = 0, 1, 2
 
+_SRC_GRAD = os.path.join(_HERE, "gcb_oracle_grad.cpp")
+_LIB_GRAD = os.path.join(_BUILD, "liboracle_grad.so")
+
 _lock = threading.Lock()
 _lib = None
+_lib_grad = None
 
 
 def build(force: bool = False) -> str:
@@ -56,6 +60,25 @@ def build(force: bool = False) -> str:
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_grad(force: bool = False) -> str:
+    """Compile the dual-number gradient oracle (g++, OpenMP) into its own
+    library; returns its path.  ``GCB_ORACLE_GRAD_LIB`` names a prebuilt
+    library to load instead (the mutation test's planted mistakes)."""
+    alt = os.environ.get("GCB_ORACLE_GRAD_LIB")
+    if alt:
+        return alt
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = force or not os.path.exists(_LIB_GRAD) or max(
+        os.path.getmtime(_SRC_GRAD), os.path.getmtime(_HDR)) > os.path.getmtime(_LIB_GRAD)
+    if stale:
+        tmp = _LIB_GRAD + f".{os.getpid()}.tmp"
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", tmp,
+               _SRC_GRAD, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_GRAD)
+    return _LIB_GRAD
 
 
 class Field(C.Structure):
@@ -409,3 +432,66 @@ def push_ks(state: dict, field, kp, params, n_steps, dl=None, nthreads=0) -> dic
     if rc != 0:
         raise RuntimeError("orc_push_ks failed")
     return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+
+# --------------------------------------------------------------------------
+# dual-number gradient of the flat-space push (gcb_oracle_grad.cpp)
+# --------------------------------------------------------------------------
+def _load_grad():
+    global _lib_grad
+    with _lock:
+        if _lib_grad is None:
+            lib = C.CDLL(build_grad())
+            lib.orcg_push_jac.argtypes = [C.c_long, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_long, C.c_long, C.c_double,
+                                          C.c_double, C.c_void_p, C.c_void_p, C.c_int,
+                                          C.c_void_p, C.POINTER(Params), C.c_int, C.c_int,
+                                          C.c_void_p]
+            lib.orcg_push_jac.restype = C.c_int
+            _lib_grad = lib
+    return _lib_grad
+
+
+REC_ORDER = ("E0", "E1", "E2", "B0", "B1", "B2", "dxB0", "dxB1", "dxB2", "dyB0", "dyB1", "dyB2")
+
+
+def mode_records(fields) -> np.ndarray:
+    """(ny*nx, 12) float64 node records of a 2D field dict with gradient
+    grids, in REC_ORDER."""
+    comps = list(fields["E"]) + list(fields["B"]) + list(fields["dB"])[:6]
+    return np.ascontiguousarray(np.stack([np.asarray(c, dtype=np.float64).reshape(-1)
+                                          for c in comps], axis=1))
+
+
+def push_jac(state: dict, base: dict, patterns: list, amps, params: Params, n_steps: int,
+             nthreads: int = 0) -> np.ndarray:
+    """n_steps of the 2D push (grad mode GRID) in the field base + sum_m
+    amps[m] patterns[m], with the derivatives of every particle's final state
+    carried along by dual numbers.  ``state`` (x, u, dxp, flags) is advanced
+    in place (the oracle's values); returns the Jacobian (n, 7, M + 3):
+    d(final x0, x1, u0, u1, u2, dxp0, dxp1) / d(a_0 .. a_{M-1}, u0_x, u0_y,
+    u0_z) of each particle."""
+    lib = _load_grad()
+    amps = np.ascontiguousarray(amps, dtype=np.float64)
+    M = amps.size
+    if M > 64:
+        raise ValueError("at most 64 mode amplitudes")
+    rec = mode_records(base)
+    if M:
+        pat = np.ascontiguousarray(np.stack([mode_records(q) for q in patterns], axis=2))
+    else:
+        pat = np.zeros((rec.shape[0], 12, 1))
+    ny, nx = np.asarray(base["B"][0]).shape
+    x, u, dxp, flags = state["x"], state["u"], state["dxp"], state["flags"]
+    n = flags.shape[0]
+    for a in (x, u, dxp):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    assert x.shape == (2, n) and u.shape == (3, n) and dxp.shape == (2, n)
+    jac = np.zeros((n, 7, M + 3))
+    rc = lib.orcg_push_jac(n, x.ctypes.data, u.ctypes.data, dxp.ctypes.data, flags.ctypes.data,
+                           nx, ny, float(base["dx"][0]), float(base["dx"][1]),
+                           rec.ctypes.data, pat.ctypes.data, M, amps.ctypes.data,
+                           C.byref(params), int(n_steps), int(nthreads), jac.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"orcg_push_jac failed ({rc})")
+    return jac

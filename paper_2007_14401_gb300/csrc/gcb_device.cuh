@@ -12,6 +12,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+#include <type_traits>
+
 namespace gcb {
 
 template <typename R>
@@ -159,30 +162,56 @@ __device__ __forceinline__ void gather(const DevGrid<R> &g, const int ib[ND], co
 // FP32 gather with Blackwell's packed FP32x2 FMA: the record is consumed as
 // float pairs, each node adds W * pair to a pair accumulator.  Same sums as
 // gather<float> (one rounding per FMA), half the FMA instructions.
+//
+// It is split in three steps -- locate the cell, load its nodes' records,
+// interpolate -- so that a particle whose next evaluation point lies in the
+// cell it already loaded (the fixed-point iterates of one step almost
+// always do) can interpolate again from the records it holds in registers:
+// CellRecs below.  Both routes run the same interpolation on the same
+// record values, so their results are bitwise equal.
 template <int ND, int GM>
-__device__ __forceinline__ void gather_x2(const DevGrid<float> &g, const int ib[ND],
-                                          const float l[ND], FieldPt<float, ND> &F)
+struct CellRecs {
+    // float pairs per node: E0E1 E2B0 B1B2, then the gradient block's 3 ND
+    // values (3D: the last pair's second half is the record's padding)
+    static constexpr int NP = (GM == 2) ? (6 + 3 * ND + 1) / 2 : 3;
+    static constexpr int NC = 1 << ND;
+    float2 pr[NC][NP];
+    int cell[ND];          // cell offsets from the base cell; INT_MIN: empty
+    __device__ __forceinline__ void clear() { cell[0] = INT_MIN; }
+};
+
+// Cell of local offset l (as cell_of, split): fractional position t and the
+// clamped cell offset c from the base cell.
+__device__ __forceinline__ void cell_split(const DevGrid<float> &g, int d, float l, float &t, int &c)
+{
+    const float s = l * g.inv_dx[d];
+    const float f = floorf(s);
+    t = s - f;
+    c = (int)fminf(fmaxf(f, -g.nR[d]), g.nR[d]);
+}
+
+// Load the records of the nodes of cell ib + c (periodic).
+template <int ND, int GM>
+__device__ __forceinline__ void load_cell(const DevGrid<float> &g, const int ib[ND], const int c[ND],
+                                          CellRecs<ND, GM> &cr)
 {
     int i0[ND], i1[ND];
-    float t[ND];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) cell_of(g, d, ib[d], l[d], t[d], i0[d], i1[d]);
-    constexpr int NEED = (GM == 2) ? 6 + 3 * ND : 6;
-    constexpr int NQ = (NEED + 3) / 4;          // float4 chunks read per record
-    constexpr int NP = 2 * NQ;                  // float pairs accumulated
-    float2 acc[NP];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) acc[k] = make_float2(0.f, 0.f);
-    float2 dacc[ND][2];                          // grad-W mode: d_i (B0,B1), d_i (B2,-)
-    if (GM == 1) {
-#pragma unroll
-        for (int i = 0; i < ND; ++i) dacc[i][0] = dacc[i][1] = make_float2(0.f, 0.f);
+    for (int d = 0; d < ND; ++d) {
+        const int n = g.n[d];
+        int i = ib[d] + c[d];
+        i += i < 0 ? n : 0;
+        i -= i >= n ? n : 0;
+        int j = i + 1;
+        j -= j >= n ? n : 0;
+        i0[d] = i;
+        i1[d] = j;
+        cr.cell[d] = c[d];
     }
-    constexpr int NC = 1 << ND;
+    constexpr int NQ = (2 * CellRecs<ND, GM>::NP + 3) / 4;   // float4 chunks read per record
 #pragma unroll
-    for (int o = 0; o < NC; ++o) {
+    for (int o = 0; o < CellRecs<ND, GM>::NC; ++o) {
         int node;
-        float w[ND];
         if (ND == 2) {
             int ix = (o & 1) ? i1[0] : i0[0];
             int iy = (o & 2) ? i1[1] : i0[1];
@@ -193,26 +222,45 @@ __device__ __forceinline__ void gather_x2(const DevGrid<float> &g, const int ib[
             int iz = (o & 4) ? i1[ND - 1] : i0[ND - 1];
             node = (iz * g.n[1] + iy) * g.n[0] + ix;
         }
+        const float4 *rp = reinterpret_cast<const float4 *>(g.rec + (size_t)node * g.stride);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float4 v = __ldg(rp + q);
+            if (2 * q < CellRecs<ND, GM>::NP) cr.pr[o][2 * q] = make_float2(v.x, v.y);
+            if (2 * q + 1 < CellRecs<ND, GM>::NP) cr.pr[o][2 * q + 1] = make_float2(v.z, v.w);
+        }
+    }
+}
+
+// Interpolate at fractional position t in the loaded cell.
+template <int ND, int GM>
+__device__ __forceinline__ void interp_cell(const DevGrid<float> &g, const CellRecs<ND, GM> &cr,
+                                            const float t[ND], FieldPt<float, ND> &F)
+{
+    constexpr int NP = CellRecs<ND, GM>::NP;
+    float2 acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = make_float2(0.f, 0.f);
+    float2 dacc[ND][2];                          // grad-W mode: d_i (B0,B1), d_i (B2,-)
+    if (GM == 1) {
+#pragma unroll
+        for (int i = 0; i < ND; ++i) dacc[i][0] = dacc[i][1] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int o = 0; o < CellRecs<ND, GM>::NC; ++o) {
+        float w[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) w[d] = ((o >> d) & 1) ? t[d] : 1.f - t[d];
         float W = w[0];
 #pragma unroll
         for (int d = 1; d < ND; ++d) W *= w[d];
         const float2 W2 = make_float2(W, W);
-        const float4 *rp = reinterpret_cast<const float4 *>(g.rec + (size_t)node * g.stride);
-        float2 pr[NP];
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) {
-            float4 q = __ldg(rp + c);
-            pr[2 * c] = make_float2(q.x, q.y);
-            pr[2 * c + 1] = make_float2(q.z, q.w);
-        }
-#pragma unroll
-        for (int k = 0; k < NP; ++k) acc[k] = __ffma2_rn(pr[k], W2, acc[k]);
+        for (int k = 0; k < NP; ++k) acc[k] = __ffma2_rn(cr.pr[o][k], W2, acc[k]);
         if (GM == 1) {
             // pairs 1 and 2 hold (E2, B0) and (B1, B2)
-            const float2 b01 = make_float2(pr[1].y, pr[2].x);
-            const float2 b2 = make_float2(pr[2].y, 0.f);
+            const float2 b01 = make_float2(cr.pr[o][1].y, cr.pr[o][2].x);
+            const float2 b2 = make_float2(cr.pr[o][2].y, 0.f);
 #pragma unroll
             for (int i = 0; i < ND; ++i) {
                 float gw = ((o >> i) & 1) ? g.inv_dx[i] : -g.inv_dx[i];
@@ -245,6 +293,38 @@ __device__ __forceinline__ void gather_x2(const DevGrid<float> &g, const int ib[
     }
 }
 
+template <int ND, int GM>
+__device__ __forceinline__ void gather_x2(const DevGrid<float> &g, const int ib[ND],
+                                          const float l[ND], FieldPt<float, ND> &F)
+{
+    float t[ND];
+    int c[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) cell_split(g, d, l[d], t[d], c[d]);
+    CellRecs<ND, GM> cr;
+    load_cell<ND, GM>(g, ib, c, cr);
+    interp_cell<ND, GM>(g, cr, t, F);
+}
+
+// Gather through the records held in cr: loaded again only when the point
+// lies in another cell than the one cr holds.
+template <int ND, int GM>
+__device__ __forceinline__ void gather_cached(const DevGrid<float> &g, const int ib[ND],
+                                              const float l[ND], FieldPt<float, ND> &F,
+                                              CellRecs<ND, GM> &cr)
+{
+    float t[ND];
+    int c[ND];
+    bool hit = true;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        cell_split(g, d, l[d], t[d], c[d]);
+        hit = hit && c[d] == cr.cell[d];
+    }
+    if (!hit) load_cell<ND, GM>(g, ib, c, cr);
+    interp_cell<ND, GM>(g, cr, t, F);
+}
+
 // The gather used by the kernels: packed FP32x2 for float, scalar for double.
 template <typename R, int ND, int GM>
 __device__ __forceinline__ void gather_any(const DevGrid<R> &g, const int ib[ND], const R l[ND],
@@ -275,10 +355,19 @@ __device__ __forceinline__ void cross3(const R a[3], const R b[3], R r[3])
 // d_i b_j = (d_i B_j - b_j (b . d_i B)) / B.
 template <typename R>
 struct Frame {
-    R Bmag, b[3], vE[3], kappa, Epar;
+    R Bmag, ib, b[3], vE[3], kappa, Epar;
     R bgb[3], vgb[3];
     bool ok;
 };
+
+// 1/sqrt(x): one reciprocal square root instruction in the arithmetic types
+// of the kernels, the quotient for other types (dual numbers).
+template <typename R>
+__device__ __forceinline__ R inv_sqrt(R x) { return R(1) / sqrt(x); }
+template <>
+__device__ __forceinline__ float inv_sqrt<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double inv_sqrt<double>(double x) { return rsqrt(x); }
 
 template <typename R>
 __device__ __forceinline__ R one_minus_beta2(const R E[3], const R B[3], R B2, R c, R beta2)
@@ -301,14 +390,20 @@ __device__ __forceinline__ float one_minus_beta2<float>(const float E[3], const 
     return (float)(1.0 - v2);
 }
 
-template <typename R, int ND, bool GRADS>
+// PROJ = false leaves out the projection of (b.grad)B and (v_E.grad)B onto
+// the plane normal to b: every use of (b.grad)b and (v_E.grad)b in the step
+// is b x (.) or v_E . (.), which annihilates the component along b (v_E is
+// normal to B), so the step's results are the same up to rounding.
+template <typename R, int ND, bool GRADS, bool PROJ = true>
 __device__ __forceinline__ void make_frame(const FieldPt<R, ND> &F, R c, R inv_c2, Frame<R> &f)
 {
     R B2 = dot3(F.B, F.B);
     f.ok = B2 > R(0);
     if (!f.ok) B2 = R(1);
-    f.Bmag = sqrt(B2);
-    R ib = R(1) / f.Bmag;
+    R ib = PROJ ? R(1) / sqrt(B2) : inv_sqrt(B2);
+    f.Bmag = PROJ ? sqrt(B2) : B2 * ib;
+    if (PROJ) ib = R(1) / f.Bmag;
+    f.ib = ib;
     R ib2 = ib * ib;
 #pragma unroll
     for (int k = 0; k < 3; ++k) f.b[k] = F.B[k] * ib;
@@ -319,7 +414,7 @@ __device__ __forceinline__ void make_frame(const FieldPt<R, ND> &F, R c, R inv_c
     R beta2 = dot3(f.vE, f.vE) * inv_c2;
     R om = one_minus_beta2<R>(F.E, F.B, B2, c, beta2);
     f.ok = f.ok && (om > R(0));
-    f.kappa = R(1) / sqrt(f.ok ? om : R(1));
+    f.kappa = PROJ ? R(1) / sqrt(f.ok ? om : R(1)) : inv_sqrt(f.ok ? om : R(1));
     f.Epar = dot3(F.E, f.b);
     if (GRADS) {
         // w = (b.grad)B, y = (v_E.grad)B; then (b.grad)b = (w - b (b.w))/B etc.
@@ -335,11 +430,19 @@ __device__ __forceinline__ void make_frame(const FieldPt<R, ND> &F, R c, R inv_c
             w[j] = sw;
             y[j] = sy;
         }
-        R bw = dot3(f.b, w), by = dot3(f.b, y);
+        if (PROJ) {
+            R bw = dot3(f.b, w), by = dot3(f.b, y);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            f.bgb[j] = fma(-f.b[j], bw, w[j]) * ib;
-            f.vgb[j] = fma(-f.b[j], by, y[j]) * ib;
+            for (int j = 0; j < 3; ++j) {
+                f.bgb[j] = fma(-f.b[j], bw, w[j]) * ib;
+                f.vgb[j] = fma(-f.b[j], by, y[j]) * ib;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                f.bgb[j] = w[j] * ib;
+                f.vgb[j] = y[j] * ib;
+            }
         }
     }
 }
@@ -396,6 +499,37 @@ __device__ __forceinline__ void gc_vel(const Frame<R> &f, const StepPar<R> &s, R
     for (int k = 0; k < 3; ++k) V[k] = fma(ig, f.b[k], f.vE[k] + vc[k]);
 }
 
+// The same two quantities from 1/Gamma and cq = c/(q/m), as the push
+// evaluates them: v_c with prefactor cq kappa^2/B, and u_par b/Gamma + v_E +
+// v_c with the one reciprocal of Gamma.
+template <typename R>
+__device__ __forceinline__ void vcurv_ig(const Frame<R> &f, const StepPar<R> &s, R cq, R upar, R iG,
+                                         R vc[3])
+{
+    if (!s.curvature) { vc[0] = vc[1] = vc[2] = R(0); return; }
+    R a[3];
+    R k2 = upar * upar * iG;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a[k] = fma(k2, f.bgb[k], upar * f.vgb[k]);
+    R x[3];
+    cross3(f.b, a, x);
+    R pref = cq * f.kappa * f.kappa * f.ib;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) vc[k] = pref * x[k];
+}
+
+template <typename R>
+__device__ __forceinline__ void gc_vel_ig(const Frame<R> &f, const StepPar<R> &s, R cq, R upar, R mu,
+                                          R uperp, R V[3])
+{
+    R iG = R(1) / gamma_gc(f, s, upar, mu, uperp);
+    R vc[3];
+    vcurv_ig(f, s, cq, upar, iG, vc);
+    R ig = upar * iG;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) V[k] = fma(ig, f.b[k], f.vE[k] + vc[k]);
+}
+
 // Relativistic Boris push (Sec. 2.1, Boris 1970) with E, B at x^n:
 // u- = u + hE, t = hB/(c gamma-), s = 2t/(1+t^2), u' = u- + u- x t,
 // u+ = u- + u' x s, u^{n+1/2} = u+ + hE (h = q dt/2m); disp = dt u/gamma.
@@ -433,37 +567,83 @@ __device__ __forceinline__ void boris(const R E[3], const R B[3], const StepPar<
 // Lorentz factor >= 1 solves the quadratic); u and disp are then untouched.
 // The gather the step uses: any callable gth(ib, l, F).  PlainGather is the
 // kernels' (the grid's records in the arithmetic type); the adjoint kernel
-// passes one that also records weights and seeds tangents.
+// passes one that also records weights and seeds tangents.  A gatherer with
+// kCellCache = true also offers gth.cached(ib, l, F, cr), which keeps the
+// records of the last cell it loaded in cr (FP32: CellRecs); the step then
+// passes every gather after the one at x^n through it.
+// Which FP32 kernels keep the cell's records between gathers: measured on
+// GB300, the 3D push (8 nodes of 2 record chunks per gather) gains 9%, the
+// 2D push with gradient records (4 nodes of 3 chunks) loses 2-4% to the
+// registers the records take.
+#ifndef GCB_CELL_CACHE_2D
+#define GCB_CELL_CACHE_2D 0
+#endif
+#ifndef GCB_CELL_CACHE_3D
+#define GCB_CELL_CACHE_3D 1
+#endif
 template <typename R, int ND, int GM>
 struct PlainGather {
+    static constexpr bool kCellCache =
+        sizeof(R) == 4 && (ND == 2 ? GCB_CELL_CACHE_2D : GCB_CELL_CACHE_3D);
     DevGrid<R> g;
     __device__ __forceinline__ void operator()(const int ib[ND], const R l[ND],
                                                FieldPt<R, ND> &F) const
     {
         gather_any<R, ND, GM>(g, ib, l, F);
     }
+    template <typename C>
+    __device__ __forceinline__ void cached(const int ib[ND], const R l[ND], FieldPt<R, ND> &F,
+                                           C &cr) const
+    {
+        if constexpr (kCellCache) gather_cached<ND, GM>(g, ib, l, F, cr);
+        else gather_any<R, ND, GM>(g, ib, l, F);
+    }
 };
 
+template <typename G, typename = void>
+struct HasCellCache : std::false_type {};
+template <typename G>
+struct HasCellCache<G, std::void_t<decltype(G::kCellCache)>>
+    : std::integral_constant<bool, G::kCellCache> {};
+
+struct NoCellRecs {
+    __device__ __forceinline__ void clear() {}
+};
+
+// The records a gatherer keeps between the gathers of one step.
+template <typename Gth, int ND, int GM>
+using StepRecs = std::conditional_t<HasCellCache<Gth>::value, CellRecs<ND, GM>, NoCellRecs>;
+
+// cr: the records the step's cached gathers start from (cleared, or those of
+// the cell of x^n when the caller gathered there through them).
 template <typename R, int ND, int GM, typename Gth>
-__device__ __forceinline__ bool gca_step(const Gth &gth, const StepPar<R> &s, const int ib[ND],
-                                         const R ln[ND], const R dxp[ND], const FieldPt<R, ND> &F0,
-                                         R u[3], R disp[ND], int &iters, bool &nonconv)
+__device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, const int ib[ND],
+                                           const R ln[ND], const R dxp[ND],
+                                           const FieldPt<R, ND> &F0, R u[3], R disp[ND],
+                                           int &iters, bool &nonconv, StepRecs<Gth, ND, GM> &cr)
 {
+    constexpr bool CACHE = HasCellCache<Gth>::value;
+    constexpr bool GR = (GM != 0);
+    auto gat = [&](const R p[ND], FieldPt<R, ND> &Fo) {
+        if constexpr (CACHE) gth.cached(ib, p, Fo, cr);
+        else gth(ib, p, Fo);
+    };
+    const R cq = s.c / s.qm;
     FieldPt<R, ND> F;
     Frame<R> f0, f;
-    make_frame<R, ND, (GM != 0)>(F0, s.c, s.inv_c2, f0);
+    make_frame<R, ND, GR, false>(F0, s.c, s.inv_c2, f0);
 
     // conversion at R^{n-1/2} = x^n - dxp/2 (Sec. 3.1)
     R pt[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) pt[d] = fma(R(-0.5), dxp[d], ln[d]);
-    gth(ib, pt, F);
-    make_frame<R, ND, (GM != 0)>(F, s.c, s.inv_c2, f);
+    gat(pt, F);
+    make_frame<R, ND, GR, false>(F, s.c, s.inv_c2, f);
     if (!(f0.ok && f.ok)) return false;
     R Gfull = sqrt(R(1) + dot3(u, u) * s.inv_c2);
     R upar = dot3(u, f.b);
     R vc[3];
-    vcurv(f, s, upar, Gfull, vc);
+    vcurv_ig(f, s, cq, upar, R(1) / Gfull, vc);
     R ug[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) ug[k] = u[k] - upar * f.b[k] - (f.vE[k] + vc[k]) * Gfull;
@@ -509,7 +689,7 @@ __device__ __forceinline__ bool gca_step(const Gth &gth, const StepPar<R> &s, co
     // fixed point on Eq. (dRdtcase2disc): R^{k+1} = R^n + dt/2 (V^n + V^k),
     // iterated on the displacement R^{k+1} - R^n from R^0 = R^n.
     R Vn[3];
-    gc_vel(f0, s, upn, mu, uperp, Vn);
+    gc_vel_ig(f0, s, cq, upn, mu, uperp, Vn);
     R dk[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) dk[d] = R(0);
@@ -537,27 +717,37 @@ __device__ __forceinline__ bool gca_step(const Gth &gth, const StepPar<R> &s, co
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) pt[d] = ln[d] + dk[d];
-        gth(ib, pt, F);
-        make_frame<R, ND, (GM != 0)>(F, s.c, s.inv_c2, f);
+        gat(pt, F);
+        make_frame<R, ND, GR, false>(F, s.c, s.inv_c2, f);
         okall = okall && f.ok;   // a bad frame fails the step after the loop
-        gc_vel(f, s, upn, mu, uperp, V);
+        gc_vel_ig(f, s, cq, upn, mu, uperp, V);
     }
     if (!okall) return false;
 
     // reconstruction at R^{n+1/2} = (R^{n+1} + R^n)/2 (Sec. 3.1)
 #pragma unroll
     for (int d = 0; d < ND; ++d) pt[d] = fma(R(0.5), dk[d], ln[d]);
-    gth(ib, pt, F);
-    make_frame<R, ND, (GM != 0)>(F, s.c, s.inv_c2, f);
+    gat(pt, F);
+    make_frame<R, ND, GR, false>(F, s.c, s.inv_c2, f);
     if (!f.ok) return false;
     R Gp = gamma_gc(f, s, upn, mu, uperp);
-    vcurv(f, s, upn, Gp, vc);
+    vcurv_ig(f, s, cq, upn, R(1) / Gp, vc);
     R un = s.mu_mode ? uperp : sqrt(R(2) * mu * f.Bmag * f.kappa);
 #pragma unroll
     for (int k = 0; k < 3; ++k) u[k] = fma(upn, f.b[k], fma(f.vE[k] + vc[k], Gp, un * bpg[k]));
 #pragma unroll
     for (int d = 0; d < ND; ++d) disp[d] = dk[d];
     return true;
+}
+
+template <typename R, int ND, int GM, typename Gth>
+__device__ __forceinline__ bool gca_step(const Gth &gth, const StepPar<R> &s, const int ib[ND],
+                                         const R ln[ND], const R dxp[ND], const FieldPt<R, ND> &F0,
+                                         R u[3], R disp[ND], int &iters, bool &nonconv)
+{
+    StepRecs<Gth, ND, GM> cr;
+    cr.clear();
+    return gca_step_c<R, ND, GM>(gth, s, ib, ln, dxp, F0, u, disp, iters, nonconv, cr);
 }
 
 }  // namespace gcb

@@ -40,6 +40,12 @@ struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : GCB_TILE_F32; };
 #ifndef GCB_MIN_BLOCKS_F32_3D
 #define GCB_MIN_BLOCKS_F32_3D 3
 #endif
+#ifndef GCB_SEED_CACHE
+#define GCB_SEED_CACHE 1
+#endif
+#ifndef GCB_REG2D
+#define GCB_REG2D 1
+#endif
 template <typename R, int ND>
 struct MinBlocks {
     static constexpr int n = sizeof(R) == 8 ? 1 : (ND == 3 ? GCB_MIN_BLOCKS_F32_3D : GCB_MIN_BLOCKS_F32);
@@ -190,6 +196,9 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
         R l[ND], uu[3], dd[ND];
         FieldPt<R, ND> F;
         int ib[ND];
+        using Gth = PlainGather<R, ND, GM>;
+        StepRecs<Gth, ND, GM> cr;
+        cr.clear();
         if (valid) {
             const bool from_smem = FUSE && stp > 0;   // the slot holds the previous step's output
             fl = from_smem ? s_fl[tid] : a.flagsin[i];
@@ -220,7 +229,8 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
                         l[d] = (R)lf;
                     }
                 }
-                gather_any<R, ND, GM>(a.g, ib, l, F);
+                if constexpr (GCB_SEED_CACHE && Gth::kCellCache) gather_cached<ND, GM>(a.g, ib, l, F, cr);
+                else gather_any<R, ND, GM>(a.g, ib, l, F);
                 // switch S (Sec. 3, Sec. 4.1) in division-free form:
                 // S = 0 iff c^2 Gamma < f_rho dl |q/m| B and |E| < f_E B.
                 R Q = fabs(a.qm[(fl >> GCB_SPECIES_SHIFT) & 3]);
@@ -257,7 +267,7 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
         // faster) or kept in the thread's slot and read where used (3D,
         // whose kernels hold more live values and whose tiles are more often
         // mixed, measured faster that way).
-        constexpr bool REG = (ND == 2);
+        constexpr bool REG = (ND == 2) && GCB_REG2D;
         int uni = 0;
         if (GCB_UNIFORM_TILES) {
             if (__syncthreads_and(!valid || cls == 0)) uni = 1;
@@ -330,6 +340,7 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
             if (cls == 1) s_perm[totG + offB + __popc(bbm & lt)] = (unsigned short)tid;
             __syncthreads();
             // this thread advances slot perm[tid]: [GCA ..., Boris ...]
+            cr.clear();   // the records loaded were those of the thread's own particle
             work = tid < totG + totB;
             isg = tid < totG;
             if (work) {
@@ -375,8 +386,7 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
             bool ncv = false, fail = false;
             bool done = false;
             if (isg) {
-                done = gca_step<R, ND, GM>(PlainGather<R, ND, GM>{a.g}, sp, ib, l, ds, F, us,
-                                           disp, it, ncv);
+                done = gca_step_c<R, ND, GM>(Gth{a.g}, sp, ib, l, ds, F, us, disp, it, ncv, cr);
                 if (!done) {
                     fail = true;
                     it = 0;

@@ -96,6 +96,42 @@ MUTANTS_KS = [
 ]
 
 
+# mistakes in the dual-number gradient oracle: its arithmetic on derivatives
+# and the seeding of the directions
+SRC_GRAD = os.path.join(ROOT, "oracle", "gcb_oracle_grad.cpp")
+MUTANTS_GRAD = [
+    ("dual_sqrt_half", "r.d[k] = a.d[k] / (2.0 * s);", "r.d[k] = a.d[k] / s;"),
+    ("dual_quotient_sign", "r.d[k] = (a.d[k] - q * b.d[k]) / b.v;",
+     "r.d[k] = (a.d[k] + q * b.d[k]) / b.v;"),
+    ("dual_product_term", "r.d[k] = a.d[k] * b.v + a.v * b.d[k];", "r.d[k] = a.d[k] * b.v;"),
+    ("mode_seed_dropped", "FN.d[m] = pm[m];", "FN.d[m] = 0.0;"),
+    ("momentum_seed_index", "ui[k].d[DU0 + k] = 1.0;", "ui[k].d[DU0] = 1.0;"),
+    ("weights_position_free", "t[d] = s - fl;", "t[d] = Dual(val(s) - fl);"),
+]
+
+
+def _build_grad_mutant(tmp, old, new):
+    text = open(SRC_GRAD).read()
+    assert text.count(old) == 1, old
+    with open(os.path.join(tmp, "gcb_oracle_grad.cpp"), "w") as fh:
+        fh.write(text.replace(old, new))
+    shutil.copy(HDR, os.path.join(tmp, "gcb_oracle.h"))
+    lib = os.path.join(tmp, "libmutgrad.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", lib,
+                    os.path.join(tmp, "gcb_oracle_grad.cpp"), "-lm"], check=True)
+    return lib
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS_GRAD, ids=[c[0] for c in MUTANTS_GRAD])
+def test_grad_pins_catch_planted_mistake(name, old, new, tmp_path):
+    lib = _build_grad_mutant(str(tmp_path), old, new)
+    env = dict(os.environ, GCB_ORACLE_GRAD_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_grad_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+
+
 def _build_mutant(tmp, src_path, old, new):
     names = {SRC: "gcb_oracle.c", SRC_KS: "gcb_oracle_ks.c"}
     for path, name in names.items():
