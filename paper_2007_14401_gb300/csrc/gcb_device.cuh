@@ -190,6 +190,28 @@ __device__ __forceinline__ void cell_split(const DevGrid<float> &g, int d, float
     c = (int)fminf(fmaxf(f, -g.nR[d]), g.nR[d]);
 }
 
+// One 16-byte chunk of a node record.  The records are read many times per
+// step (every particle of a cell, every gather of a step) while the particle
+// state streams past once; with GCB_FIELD_L2_LAST the chunk is read under an
+// L2 evict-last policy, so the state does not push the records out of L2.
+#ifndef GCB_FIELD_L2_LAST
+#define GCB_FIELD_L2_LAST 1
+#endif
+__device__ __forceinline__ float4 ld_record(const float4 *p)
+{
+    if constexpr (GCB_FIELD_L2_LAST) {
+        uint64_t pol;
+        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+        float4 v;
+        asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+            : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+            : "l"(__cvta_generic_to_global(p)), "l"(pol));
+        return v;
+    } else {
+        return __ldg(p);
+    }
+}
+
 // Load the records of the nodes of cell ib + c (periodic).
 template <int ND, int GM>
 __device__ __forceinline__ void load_cell(const DevGrid<float> &g, const int ib[ND], const int c[ND],
@@ -225,7 +247,7 @@ __device__ __forceinline__ void load_cell(const DevGrid<float> &g, const int ib[
         const float4 *rp = reinterpret_cast<const float4 *>(g.rec + (size_t)node * g.stride);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            float4 v = __ldg(rp + q);
+            float4 v = ld_record(rp + q);
             if (2 * q < CellRecs<ND, GM>::NP) cr.pr[o][2 * q] = make_float2(v.x, v.y);
             if (2 * q + 1 < CellRecs<ND, GM>::NP) cr.pr[o][2 * q + 1] = make_float2(v.z, v.w);
         }
@@ -615,12 +637,15 @@ template <typename Gth, int ND, int GM>
 using StepRecs = std::conditional_t<HasCellCache<Gth>::value, CellRecs<ND, GM>, NoCellRecs>;
 
 // cr: the records the step's cached gathers start from (cleared, or those of
-// the cell of x^n when the caller gathered there through them).
+// the cell of x^n when the caller gathered there through them).  Fh: the
+// fields at R^{n-1/2} = x^n - dxp/2 when the caller has gathered them already
+// (the same gather the step would make), else null.
 template <typename R, int ND, int GM, typename Gth>
 __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, const int ib[ND],
                                            const R ln[ND], const R dxp[ND],
                                            const FieldPt<R, ND> &F0, R u[3], R disp[ND],
-                                           int &iters, bool &nonconv, StepRecs<Gth, ND, GM> &cr)
+                                           int &iters, bool &nonconv, StepRecs<Gth, ND, GM> &cr,
+                                           const FieldPt<R, ND> *Fh = nullptr)
 {
     constexpr bool CACHE = HasCellCache<Gth>::value;
     constexpr bool GR = (GM != 0);
@@ -637,7 +662,8 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
     R pt[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) pt[d] = fma(R(-0.5), dxp[d], ln[d]);
-    gat(pt, F);
+    if (Fh) F = *Fh;
+    else gat(pt, F);
     make_frame<R, ND, GR, false>(F, s.c, s.inv_c2, f);
     if (!(f0.ok && f.ok)) return false;
     R Gfull = sqrt(R(1) + dot3(u, u) * s.inv_c2);

@@ -46,6 +46,11 @@ struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : GCB_TILE_F32; };
 #ifndef GCB_REG2D
 #define GCB_REG2D 1
 #endif
+// 1: phase 1 gathers at R^{n-1/2} = x^n - dxp/2 together with x^n (2D), so
+// that the two gathers' loads are in flight at once
+#ifndef GCB_HOIST_HALF
+#define GCB_HOIST_HALF 0
+#endif
 template <typename R, int ND>
 struct MinBlocks {
     static constexpr int n = sizeof(R) == 8 ? 1 : (ND == 3 ? GCB_MIN_BLOCKS_F32_3D : GCB_MIN_BLOCKS_F32);
@@ -81,6 +86,25 @@ struct PushArgs {
     int nsteps;               // steps of this launch (> 1 only for the fused kernel)
     unsigned long long *stats;
 };
+
+// Particle state is read and written once per step and the field records
+// many times: the state's loads and stores are marked streaming (evict
+// first), so that they do not push the records out of L1 and L2.
+#ifndef GCB_STREAM_STATE
+#define GCB_STREAM_STATE 1
+#endif
+template <typename T>
+__device__ __forceinline__ T ld_state(const T *p)
+{
+    if constexpr (GCB_STREAM_STATE) return __ldcs(p);
+    else return *p;
+}
+template <typename T>
+__device__ __forceinline__ void st_state(T *p, T v)
+{
+    if constexpr (GCB_STREAM_STATE) __stcs(p, v);
+    else *p = v;
+}
 
 template <int PM>
 struct PosType;
@@ -195,25 +219,27 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
         float xl[ND];
         R l[ND], uu[3], dd[ND];
         FieldPt<R, ND> F;
+        constexpr bool HOIST = GCB_HOIST_HALF && ND == 2;
+        FieldPt<R, ND> Fh;          // fields at R^{n-1/2} (HOIST)
         int ib[ND];
         using Gth = PlainGather<R, ND, GM>;
         StepRecs<Gth, ND, GM> cr;
         cr.clear();
         if (valid) {
             const bool from_smem = FUSE && stp > 0;   // the slot holds the previous step's output
-            fl = from_smem ? s_fl[tid] : a.flagsin[i];
-            if (!from_smem && a.pidin != a.pid) pid = a.pidin[i];
+            fl = from_smem ? s_fl[tid] : ld_state(a.flagsin + i);
+            if (!from_smem && a.pidin != a.pid) pid = ld_state(a.pidin + i);
             bool fin = true;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
-                xs[d] = from_smem ? s_x[d][tid] : reinterpret_cast<const PosT *>(a.xin[d])[i];
-                xl[d] = PM ? (from_smem ? s_xl[d][tid] : a.xloin[d][i]) : 0.0f;
-                dd[d] = from_smem ? s_d[d][tid] : a.dxpin[d][i];
+                xs[d] = from_smem ? s_x[d][tid] : ld_state(reinterpret_cast<const PosT *>(a.xin[d]) + i);
+                xl[d] = PM ? (from_smem ? s_xl[d][tid] : ld_state(a.xloin[d] + i)) : 0.0f;
+                dd[d] = from_smem ? s_d[d][tid] : ld_state(a.dxpin[d] + i);
                 fin = fin && finite_r(xs[d]) && finite_r(xl[d]) && finite_r(dd[d]);
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                uu[k] = from_smem ? s_u[k][tid] : a.uin[k][i];
+                uu[k] = from_smem ? s_u[k][tid] : ld_state(a.uin[k] + i);
                 fin = fin && finite_r(uu[k]);
             }
             if (fin) {
@@ -231,6 +257,12 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
                 }
                 if constexpr (GCB_SEED_CACHE && Gth::kCellCache) gather_cached<ND, GM>(a.g, ib, l, F, cr);
                 else gather_any<R, ND, GM>(a.g, ib, l, F);
+                if constexpr (HOIST) {
+                    R ph[ND];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) ph[d] = fma(R(-0.5), dd[d], l[d]);
+                    gather_any<R, ND, GM>(a.g, ib, ph, Fh);
+                }
                 // switch S (Sec. 3, Sec. 4.1) in division-free form:
                 // S = 0 iff c^2 Gamma < f_rho dl |q/m| B and |E| < f_E B.
                 R Q = fabs(a.qm[(fl >> GCB_SPECIES_SHIFT) & 3]);
@@ -249,16 +281,16 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
                 if (!FUSE) {
 #pragma unroll
                     for (int d = 0; d < ND; ++d) {
-                        reinterpret_cast<PosT *>(a.x[d])[i] = xs[d];
-                        if (PM) a.xlo[d][i] = xl[d];
-                        a.dxp[d][i] = dd[d];
+                        st_state(reinterpret_cast<PosT *>(a.x[d]) + i, xs[d]);
+                        if (PM) st_state(a.xlo[d] + i, xl[d]);
+                        st_state(a.dxp[d] + i, dd[d]);
                     }
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) a.u[k][i] = uu[k];
-                    a.flags[i] = fl;
+                    for (int k = 0; k < 3; ++k) st_state(a.u[k] + i, uu[k]);
+                    st_state(a.flags + i, fl);
                 }
             }
-            if (a.pidin != a.pid && (!FUSE || stp == 0)) a.pid[i] = pid;
+            if (a.pidin != a.pid && (!FUSE || stp == 0)) st_state(a.pid + i, pid);
         }
         // Tiles whose valid particles all take one branch (the common case in
         // strongly magnetized runs) skip the compaction and the staging of
@@ -386,7 +418,8 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
             bool ncv = false, fail = false;
             bool done = false;
             if (isg) {
-                done = gca_step_c<R, ND, GM>(Gth{a.g}, sp, ib, l, ds, F, us, disp, it, ncv, cr);
+                done = gca_step_c<R, ND, GM>(Gth{a.g}, sp, ib, l, ds, F, us, disp, it, ncv, cr,
+                                             (HOIST && uni) ? &Fh : nullptr);
                 if (!done) {
                     fail = true;
                     it = 0;
@@ -438,12 +471,12 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
                 } else {
 #pragma unroll
                     for (int d = 0; d < ND; ++d) {
-                        reinterpret_cast<PosT *>(a.x[d])[gi] = xn[d];
-                        if (PM) a.xlo[d][gi] = xln[d];
-                        a.dxp[d][gi] = disp[d];
+                        st_state(reinterpret_cast<PosT *>(a.x[d]) + gi, xn[d]);
+                        if (PM) st_state(a.xlo[d] + gi, xln[d]);
+                        st_state(a.dxp[d] + gi, disp[d]);
                     }
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) a.u[k][gi] = us[k];
+                    for (int k = 0; k < 3; ++k) st_state(a.u[k] + gi, us[k]);
                 }
                 if (done) ++ng; else ++nb;
                 if (Sprev && !Snew) ++tg;
@@ -471,18 +504,18 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
                         if (PM) s_xl[d][sl] = l0;
                         s_d[d][sl] = d0;
                     } else {
-                        reinterpret_cast<PosT *>(a.x[d])[gi] = x0;
-                        if (PM) a.xlo[d][gi] = l0;
-                        a.dxp[d][gi] = d0;
+                        st_state(reinterpret_cast<PosT *>(a.x[d]) + gi, x0);
+                        if (PM) st_state(a.xlo[d] + gi, l0);
+                        st_state(a.dxp[d] + gi, d0);
                     }
                 }
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const R u0 = REG ? uu[k] : s_u[k][sl];
-                    if (FUSE) s_u[k][sl] = u0; else a.u[k][gi] = u0;
+                    if (FUSE) s_u[k][sl] = u0; else st_state(a.u[k] + gi, u0);
                 }
             }
-            if (FUSE) s_fl[sl] = nfl; else a.flags[gi] = nfl;
+            if (FUSE) s_fl[sl] = nfl; else st_state(a.flags + gi, nfl);
         }
         if (FUSE) __syncthreads();   // the slots hold this step's output
       }
@@ -490,13 +523,13 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
           // the tile's state after its nsteps steps, coalesced
 #pragma unroll
           for (int d = 0; d < ND; ++d) {
-              reinterpret_cast<PosT *>(a.x[d])[i] = s_x[d][tid];
-              if (PM) a.xlo[d][i] = s_xl[d][tid];
-              a.dxp[d][i] = s_d[d][tid];
+              st_state(reinterpret_cast<PosT *>(a.x[d]) + i, s_x[d][tid]);
+              if (PM) st_state(a.xlo[d] + i, s_xl[d][tid]);
+              st_state(a.dxp[d] + i, s_d[d][tid]);
           }
 #pragma unroll
-          for (int k = 0; k < 3; ++k) a.u[k][i] = s_u[k][tid];
-          a.flags[i] = s_fl[tid];
+          for (int k = 0; k < 3; ++k) st_state(a.u[k] + i, s_u[k][tid]);
+          st_state(a.flags + i, s_fl[tid]);
       }
     }
 
