@@ -75,6 +75,9 @@ WORKLOADS = {
         prec="mixed: FP32 fields and arithmetic, FP32-pair positions",
         extra=dict(grid=[2048, 1024], dt=0.45, omega_c_dt_max=1e5, curvature=1,
                    grad_mode="grid", gca_tol=1e-7),
+        # FMA-pipe busy fraction of this kernel in its ncu capture
+        # (sm__pipe_fma_cycles_active, 2^21 particles; profiles/)
+        fma_pipe=0.288,
         # DRAM bytes (read + write) of one push launch at 2^24 particles, from
         # an ncu capture of this kernel (1 pass: dram__bytes_read.sum +
         # dram__bytes_write.sum = 722.54 MB + 562.74 MB)
@@ -94,17 +97,20 @@ WORKLOADS = {
         extra=dict(grid=[512, 512], dt=0.02, spin=0.9),
         # FP64-issue bound: FP64 flops per particle-step as executed (2 DFMA
         # + DMUL + DADD, ncu thread-instruction counts of this kernel at 2^18
-        # particles) against the FP64 FMA peak 152 SMs x 2 DFMA/clk x 2 flops
-        # x 2.07 GHz = 1.2586 TFLOP/s
-        alu=dict(flops=1724.4, peak=1.2586, peak_source="derived: 152 SMs x 2 DFMA/clk "
-                 "x 2 flop x 2.07 GHz (ncu peak_sustained dfma 304 inst/clk)")),
+        # particles) against the FP64 FMA rate measured live (libgcb_peak.so);
+        # the derived peak 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz = 1.2586
+        # TFLOP/s is the fallback
+        alu=dict(flops=1724.4, peak=1.2586, peak_kind="fp64",
+                 peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                             "(ncu peak_sustained dfma 304 inst/clk)")),
     "sheet3d": dict(
         gen=_gen_sheet3d, n=1 << 26, precision="mixed", grid="f32", sort_every=8,
         tile=(1, 1, 1), state_b=49, field_b=256 ** 3 * 32, fp64_b=(73, 256 ** 3 * 48),
         desc="3D kinked Harris sheet 256^3, guide 0.3, {n} particles (70% MJ upstream, 30% "
              "power law in the sheet), |q/m| = 20",
         prec="mixed: FP32 fields and arithmetic, FP32-pair positions",
-        extra=dict(grid=[256, 256, 256], dt=0.45, curvature=1, grad_mode="dw", gca_tol=1e-7)),
+        extra=dict(grid=[256, 256, 256], dt=0.45, curvature=1, grad_mode="dw", gca_tol=1e-7),
+        fma_pipe=0.329),
     "sheet3d_literal": dict(
         gen=_gen_sheet3d_literal, n=1 << 26, precision="mixed", grid="f32", sort_every=8,
         tile=(1, 1, 1), state_b=49, field_b=256 ** 3 * 32, fp64_b=(73, 256 ** 3 * 48),
@@ -201,6 +207,27 @@ def coupling_report(G, multi, ds, grid, gp, ws, ks, snap, step_first, steps, fie
                                         "max": float(om.max()),
                                         "particles": int(om.size)}
     return mix
+
+
+def alu_peaks():
+    """Fused multiply-add throughput of this GPU measured live (TFLOP/s):
+    scalar FP32, packed FP32x2 and FP64 (libgcb_peak.so, CUDA events)."""
+    import ctypes as C
+
+    import torch
+    from paper_2007_14401_gb300 import build as B
+    lib = C.CDLL(B.build_peak())
+    lib.gcb_peak_fma.argtypes = [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double)]
+    lib.gcb_peak_fma.restype = C.c_int
+    out = {}
+    for name, kind, iters in (("fp32", 0, 40000), ("fp32x2", 1, 20000), ("fp64", 2, 1500)):
+        v = C.c_double(0.0)
+        rc = lib.gcb_peak_fma(kind, iters, C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                              C.byref(v))
+        out[name] = v.value if rc == 0 else None
+    out["how"] = ("16 blocks x 256 threads per SM, 8 independent FMA chains a thread, "
+                  "second of two launches timed with CUDA events")
+    return out
 
 
 def workload_config(w, n_total, ngpu, sort_every, sort_tile):
@@ -614,14 +641,27 @@ def main():
                     "traffic": (w["traffic_b"] if "traffic_b" in w and n == w["n"] else None),
                     "kernel": kname, "alg_bytes_per_particle_step": alg / n,
                     "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+        try:
+            apk = alu_peaks()
+        except (OSError, RuntimeError) as exc:
+            apk = {"error": str(exc)[:200]}
         if "alu" in w:
             a_ = w["alu"]
             tf = a_["flops"] * n / (avg_launch * 1e-3) / 1e12
-            roofline = {"bound": "alu", "achieved": tf, "peak": a_["peak"], "unit": "TFLOP/s",
-                        "frac": tf / a_["peak"], "traffic": None, "kernel": kname,
+            live = apk.get(a_["peak_kind"])
+            peak_v, peak_src = (live, "measured live: " + apk["how"]) if live else \
+                (a_["peak"], a_["peak_source"])
+            roofline = {"bound": "alu", "achieved": tf, "peak": peak_v, "unit": "TFLOP/s",
+                        "frac": tf / peak_v, "traffic": None, "kernel": kname,
                         "fp64_flops_per_particle_step": a_["flops"],
-                        "peak_source": a_["peak_source"],
+                        "peak_source": peak_src, "derived_peak": a_["peak"],
                         "hbm": {"achieved_gbs": achieved, "frac": achieved / pk["hbm_gbs"]}}
+        elif "fma_pipe" in w:
+            roofline["alu"] = {"fma_pipe_busy_frac": w["fma_pipe"],
+                               "source": "ncu sm__pipe_fma_cycles_active of this kernel "
+                                         "(profiles/)",
+                               "measured_fma_tflops": {k: apk.get(k) for k in
+                                                       ("fp32", "fp32x2", "fp64")}}
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

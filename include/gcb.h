@@ -48,6 +48,7 @@ enum { GCB_POS_F64 = 0, GCB_POS_F32PAIR = 1 };           /* position storage */
 enum { GCB_GRAD_DW = 0, GCB_GRAD_GRID = 1 };             /* source of grad B */
 enum { GCB_FORCE_NONE = 0, GCB_FORCE_BORIS = 1, GCB_FORCE_GCA = 2 };
 enum { GCB_MU_CONSERVE = 0, GCB_UPERP_CONSERVE = 1 };
+enum { GCB_FRAME_SIMPLE = 0, GCB_FRAME_BT = 1 };
 
 /* Per-particle flag byte. */
 enum {
@@ -135,6 +136,16 @@ typedef struct {
                                 (the test-particle mode, fields static over the
                                 call); a fused launch never spans a sort.  The
                                 results are the same bit for bit. */
+    int32_t drift_frame;     /* GCB_FRAME_SIMPLE (0): the guiding-center step in
+                                the simplified frame b = B/B, v_E = c E x B/B^2
+                                that the paper's schemes use (Sec. 2.2);
+                                GCB_FRAME_BT: in the exact frame of Sec. 2.2
+                                (Beklemishev & Tessarotto): b* and the exact v_E
+                                (and kappa from it) in place of b and v_E, and
+                                E_par = E.b*, with the gradients of b taken for
+                                those of b* (the records carry no grad E).
+                                GCB_FRAME_BT: gcb_push_sr only, unfused, FP64 or
+                                FP32-pair positions; elsewhere GCB_EUNSUPPORTED. */
 } gcb_params;
 
 /* Counters of one gcb_push_sr call, summed over its steps. */

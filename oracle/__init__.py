@@ -27,6 +27,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
 FIELD_GRID, FIELD_UNIFORM, FIELD_HARRIS, FIELD_BOTTLE, FIELD_ROTOR = 0, 1, 2, 3, 4
+FRAME_SIMPLE, FRAME_BT = 0, 1
 GRAD_DW, GRAD_GRID = 0, 1
 FORCE_NONE, FORCE_BORIS, FORCE_GCA = 0, 1, 2
 MU_CONSERVE, UPERP_CONSERVE = 0, 1
@@ -92,7 +93,7 @@ class Params(C.Structure):
                 ("f_E", C.c_double), ("dl", C.c_double), ("qm", C.c_double * 4),
                 ("curvature", C.c_int), ("mu_mode", C.c_int), ("grad_mode", C.c_int),
                 ("force", C.c_int), ("max_iter", C.c_int), ("fixed_iters", C.c_int),
-                ("tol", C.c_double)]
+                ("tol", C.c_double), ("frame", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -133,6 +134,8 @@ def _load():
             lib.orc_switch.argtypes = [D3, D3, C.c_double, C.c_double, P(Params),
                                        P(C.c_double)]
             lib.orc_switch.restype = C.c_int
+            lib.orc_bt_frame.argtypes = [D3, D3, C.c_double, C.c_double * 9]
+            lib.orc_bt_frame.restype = C.c_int
             lib.orc_step_one.argtypes = [P(Field), P(Params), D3, D3, D3,
                                          P(C.c_ubyte), P(Detail)]
             lib.orc_decompose.argtypes = [P(Field), P(Params), C.c_double, D3, D3,
@@ -168,10 +171,10 @@ def _load():
 
 def make_params(*, c=1.0, dt, f_rho=0.4, f_E=1.0, dl=1.0, qm=(-1.0, 1.0, 0.0, 0.0),
                 curvature=1, mu_mode=MU_CONSERVE, grad_mode=GRAD_DW, force=FORCE_NONE,
-                max_iter=16, fixed_iters=0, tol=1e-7) -> Params:
+                max_iter=16, fixed_iters=0, tol=1e-7, frame=0) -> Params:
     q = list(qm) + [0.0] * (4 - len(qm))
     return Params(c, dt, f_rho, f_E, dl, (C.c_double * 4)(*q), curvature, mu_mode,
-                  grad_mode, force, max_iter, fixed_iters, tol)
+                  grad_mode, force, max_iter, fixed_iters, tol, frame)
 
 
 class OracleField:
@@ -229,6 +232,17 @@ def bottle_field(B0, L, E=(0.0, 0.0, 0.0)) -> OracleField:
 
 def rotor_field(B0, k, E0, ndim=3) -> OracleField:
     return OracleField(FIELD_ROTOR, ndim, par=[B0, k, E0])
+
+
+def bt_frame(E, B, c=1.0):
+    """The exact drift frame of (E, B): (v_E, b*, kappa, E', B')."""
+    lib = _load()
+    out = (C.c_double * 9)()
+    ok = lib.orc_bt_frame((C.c_double * 3)(*E), (C.c_double * 3)(*B), c, out)
+    if not ok:
+        raise ValueError("B = 0")
+    v = np.array(out[:])
+    return v[0:3], v[3:6], v[6], v[7], v[8]
 
 
 def eval_field(field: OracleField, params: Params, x) -> np.ndarray:

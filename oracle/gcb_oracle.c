@@ -167,6 +167,47 @@ typedef struct {
     int ok;            /* B > 0 and v_E < c */
 } point_t;
 
+/* Exact drift frame (Sec. 2.2, Beklemishev & Tessarotto 1999): the frame
+ * moving with v_E = (w_E / (2 w_E^2/c^2)) (1 - sqrt(1 - 4 w_E^2/c^2)),
+ * w_E = c E x B / (E^2 + B^2), sees E and B parallel, with magnitudes
+ * B' = sqrt((B^2 - E^2 + (B^2 + E^2) sqrt(1 - 4 w_E^2/c^2)) / 2) and
+ * E' = E.B / B'; its field direction is b* = xi E_perp + eta B with
+ * E_perp = E - (E.B) B/B^2, Psi = E'(B^2 - B'^2)/(B' E_perp^2),
+ * eta = (B sqrt(Psi^2 E_perp^2/B^2 + 1))^{-1}, xi = eta Psi.
+ * Written as given, with algebraic rewritings that avoid 0/0:
+ * 1 - 4 w_E^2/c^2 = ((B^2 - E^2)^2 + 4 (E.B)^2) / (E^2 + B^2)^2 (from
+ * |E x B|^2 = E^2 B^2 - (E.B)^2), and 1 - sqrt(1 - q) = q / (1 + sqrt(1 - q)),
+ * so v_E = 2 w_E / (1 + s) with s = sqrt(1 - 4 w_E^2/c^2); then
+ * B^2 - B'^2 = (E^2 + B^2)(1 - s)/2 = 2 |E x B|^2 / ((E^2 + B^2)(1 + s)) and
+ * |E x B|^2 = B^2 E_perp^2, so E_perp^2 cancels from Psi:
+ * Psi = 2 E' B^2 / (B' (E^2 + B^2)(1 + s)), regular as E turns parallel to B
+ * (where b* -> b). */
+int orc_bt_frame(const double E[3], const double B[3], double c, double out[9])
+{
+    double E2 = dot3(E, E), B2 = dot3(B, B), EB = dot3(E, B);
+    if (!(B2 > 0.0)) return 0;
+    double S = E2 + B2;
+    double sq = sqrt((B2 - E2) * (B2 - E2) + 4.0 * EB * EB) / S;   /* sqrt(1 - 4 w^2/c^2) */
+    double ExB[3];
+    cross3(E, B, ExB);
+    for (int k = 0; k < 3; ++k) out[k] = 2.0 * c * ExB[k] / (S * (1.0 + sq));
+    double vE2 = dot3(out, out) / (c * c);
+    out[6] = 1.0 / sqrt(1.0 - vE2);
+    double Bp = sqrt(0.5 * (B2 - E2 + S * sq));
+    double Ep = EB / Bp;
+    out[7] = Ep;
+    out[8] = Bp;
+    double Bm = sqrt(B2);
+    double Ep_[3];
+    for (int k = 0; k < 3; ++k) Ep_[k] = E[k] - EB / B2 * B[k];
+    double Ep2 = dot3(Ep_, Ep_);
+    double Psi = 2.0 * Ep * B2 / (Bp * S * (1.0 + sq));
+    double eta = 1.0 / (Bm * sqrt(Psi * Psi * Ep2 / B2 + 1.0));
+    double xi = eta * Psi;
+    for (int k = 0; k < 3; ++k) out[3 + k] = xi * Ep_[k] + eta * B[k];
+    return 1;
+}
+
 static void eval_point(const orc_field *f, const orc_params *p, const double R[3],
                        point_t *P)
 {
@@ -190,13 +231,23 @@ static void eval_point(const orc_field *f, const orc_params *p, const double R[3
     double beta2 = dot3(P->vE, P->vE) / (c * c);
     if (!(beta2 < 1.0)) { P->ok = 0; return; }
     P->kappa = 1.0 / sqrt(1.0 - beta2);
-    P->Epar = dot3(P->E, P->b);
+    /* d_i b_j of the lab-frame b (the records carry no grad E, so the
+     * gradient of b* is taken as that of b in the exact frame too) */
     for (int i = 0; i < 3; ++i) {
         double bdB = P->b[0] * P->dB[i][0] + P->b[1] * P->dB[i][1] +
                      P->b[2] * P->dB[i][2];
         for (int j = 0; j < 3; ++j)
             P->db[i][j] = (P->dB[i][j] - P->b[j] * bdB) / P->Bmag;
     }
+    if (p->frame == ORC_FRAME_BT) {
+        /* Sec. 2.2: the complete b* and v_E in place of the approximated forms */
+        double bt[9];
+        orc_bt_frame(P->E, P->B, c, bt);
+        for (int k = 0; k < 3; ++k) { P->vE[k] = bt[k]; P->b[k] = bt[3 + k]; }
+        if (!(dot3(P->vE, P->vE) / (c * c) < 1.0)) { P->ok = 0; return; }
+        P->kappa = bt[6];
+    }
+    P->Epar = dot3(P->E, P->b);
     for (int j = 0; j < 3; ++j) {
         P->bgb[j] = P->b[0] * P->db[0][j] + P->b[1] * P->db[1][j] +
                     P->b[2] * P->db[2][j];

@@ -34,6 +34,9 @@ enum { ORC_FIELD_GRID = 0, ORC_FIELD_UNIFORM = 1, ORC_FIELD_HARRIS = 2,
 enum { ORC_GRAD_DW = 0, ORC_GRAD_GRID = 1 };
 enum { ORC_FORCE_NONE = 0, ORC_FORCE_BORIS = 1, ORC_FORCE_GCA = 2 };
 enum { ORC_MU_CONSERVE = 0, ORC_UPERP_CONSERVE = 1 };
+/* drift frame of the guiding-center decomposition (Sec. 2.2): the simplified
+ * one the paper's schemes use, or the exact Beklemishev-Tessarotto one */
+enum { ORC_FRAME_SIMPLE = 0, ORC_FRAME_BT = 1 };
 
 enum { ORC_FLAG_S = 1, ORC_FLAG_SPREV = 2, ORC_FLAG_NONCONV = 4,
        ORC_FLAG_GCAFAIL = 8, ORC_FLAG_NONFINITE = 16, ORC_FLAG_EXITED = 32 };
@@ -64,6 +67,7 @@ typedef struct {
     int max_iter;        /* bound of the fixed-point iteration */
     int fixed_iters;     /* > 0: exactly this many iterations, no test */
     double tol;          /* absolute stopping tolerance on |R^{k+1}-R^k|_inf */
+    int frame;           /* ORC_FRAME_SIMPLE (b, v_E = cExB/B^2) or ORC_FRAME_BT */
 } orc_params;
 
 typedef struct {
@@ -105,6 +109,11 @@ typedef struct {
     double k1, k2, k3;
     double Rn[3], Rnp1[3], bpg[3];
 } orc_detail;
+
+/* The exact (Beklemishev-Tessarotto) drift frame of fields E, B (Sec. 2.2):
+ * out[0..2] v_E, out[3..5] b*, out[6] kappa, out[7] E', out[8] B'.
+ * Returns 0 when B = 0 (out untouched). */
+int orc_bt_frame(const double E[3], const double B[3], double c, double out[9]);
 
 /* E, B and d_i B_j (out[0..2] E, out[3..5] B, out[6+3i+j] d_i B_j). */
 void orc_eval_field(const orc_field *f, const orc_params *p,

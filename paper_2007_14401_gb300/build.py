@@ -17,6 +17,9 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libgcb.so")
 OBJ_DIR = os.path.join(HERE, "_build")
+# the measured arithmetic peaks of the benchmark (include/gcb_peak.h)
+PEAK_LIB = os.path.join(OUT_DIR, "libgcb_peak.so")
+PEAK_SRC = "peak_fma.cu"
 
 SOURCES = ["gcb_api.cu", "sort_sr.cu", "gcb_noalloc.cu", "gcb_ks.cu", "adjoint_sr.cu",
            "push_sr_f64.cu", "push_sr_f32.cu"]
@@ -43,8 +46,26 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
+def build_peak(force: bool = False) -> str:
+    """Build libgcb_peak.so (the FMA-rate measurement) if needed; returns its path."""
+    src = os.path.join(CSRC, PEAK_SRC)
+    deps = max(os.path.getmtime(src), os.path.getmtime(os.path.join(INCLUDE, "gcb_peak.h")))
+    if not force and os.path.exists(PEAK_LIB) and os.path.getmtime(PEAK_LIB) >= deps:
+        return PEAK_LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = PEAK_LIB + f".{os.getpid()}.tmp"
+    cmd = [_nvcc(), *ARCH, *NVFLAGS, "-shared", src, "-o", tmp, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PEAK_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PEAK_LIB)
+    return PEAK_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Build libgcb.so if it is missing or older than its sources; returns its path."""
+    """Build libgcb.so (and libgcb_peak.so) if missing or older than their
+    sources; returns the path of libgcb.so."""
+    build_peak(force)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)

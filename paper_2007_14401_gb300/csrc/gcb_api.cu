@@ -229,6 +229,14 @@ static gcb_status check_problem(const gcb_particles *p, const gcb_grid *g, const
         return GCB_EINVAL;
     }
     if (!(prm->gca_tol >= 0)) { set_error("gca_tol must be >= 0"); return GCB_EINVAL; }
+    if (prm->drift_frame != GCB_FRAME_SIMPLE && prm->drift_frame != GCB_FRAME_BT) {
+        set_error("drift_frame must be GCB_FRAME_SIMPLE or GCB_FRAME_BT");
+        return GCB_EINVAL;
+    }
+    if (prm->drift_frame == GCB_FRAME_BT && prm->fuse_steps > 1) {
+        set_error("drift_frame GCB_FRAME_BT runs one step per launch (fuse_steps <= 1)");
+        return GCB_EUNSUPPORTED;
+    }
     if (prm->sort_every < 0 || prm->sort_tile[0] < 0 || prm->sort_tile[1] < 0 ||
         prm->sort_tile[2] < 0 || prm->step_index < 0) {
         set_error("sort_every, sort_tile and step_index must be >= 0");
@@ -358,6 +366,10 @@ gcb_status gcb_push_ks(const gcb_particles *p, const gcb_grid_ks *gk, const gcb_
         return GCB_EUNSUPPORTED;
     }
     if (prm->c != 1.0) { set_error("the covariant scheme uses c = 1"); return GCB_EINVAL; }
+    if (prm->drift_frame != GCB_FRAME_SIMPLE) {
+        set_error("the covariant scheme uses the simplified drift frame only");
+        return GCB_EUNSUPPORTED;
+    }
     if (!(prm->dt > 0) || !(prm->f_rho > 0) || !(prm->f_E > 0)) { set_error("dt, f_rho, f_E must be > 0"); return GCB_EINVAL; }
     if (prm->mu_mode != GCB_MU_CONSERVE && prm->mu_mode != GCB_UPERP_CONSERVE) { set_error("mu_mode"); return GCB_EINVAL; }
     if (prm->force < GCB_FORCE_NONE || prm->force > GCB_FORCE_GCA) { set_error("force"); return GCB_EINVAL; }
@@ -651,6 +663,10 @@ static gcb_status check_adjoint(const gcb_particles *p, const gcb_grid *g, const
     if (s != GCB_OK) return s;
     if (g->ndim != 2 || !g->has_grad || prm->grad_mode != GCB_GRAD_GRID) {
         set_error("the adjoint supports 2D grids with gradient records (grad_mode GRID)");
+        return GCB_EUNSUPPORTED;
+    }
+    if (prm->drift_frame != GCB_FRAME_SIMPLE) {
+        set_error("the adjoint differentiates the simplified drift frame only");
         return GCB_EUNSUPPORTED;
     }
     if (n_steps < 1 || ckpt_every < 1) { set_error("n_steps and ckpt_every must be >= 1"); return GCB_EINVAL; }

@@ -412,13 +412,99 @@ __device__ __forceinline__ float one_minus_beta2<float>(const float E[3], const 
     return (float)(1.0 - v2);
 }
 
+// Exact drift frame of Sec. 2.2 (Beklemishev & Tessarotto): the frame moving
+// with v_E = (w_E/(2 w_E^2/c^2)) (1 - sqrt(1 - 4 w_E^2/c^2)), w_E = c E x B /
+// (E^2 + B^2), sees E and B parallel along b* = xi E_perp + eta B, with
+// E_perp = E - (E.B) B/B^2, B' = sqrt((B^2 - E^2 + (B^2 + E^2) s)/2),
+// E' = E.B/B', Psi = E'(B^2 - B'^2)/(B' E_perp^2), eta = (B sqrt(Psi^2
+// E_perp^2/B^2 + 1))^{-1}, xi = eta Psi.  Evaluated as
+// s = sqrt((B^2 - E^2)^2 + 4 (E.B)^2)/(E^2 + B^2) (= sqrt(1 - 4 w_E^2/c^2)),
+// v_E = 2 c E x B / ((E^2 + B^2)(1 + s)) and Psi = 2 E' B^2/(B' (E^2 + B^2)
+// (1 + s)): the same quantities, free of the 0/0 of the printed forms at
+// E x B = 0 and E_perp = 0.  om = 1 - v_E^2/c^2.
+template <typename T>
+__device__ __forceinline__ void bt_frame(const T E[3], const T B[3], T B2, T c, T vE[3], T bs[3],
+                                         T &om)
+{
+    const T E2 = dot3(E, E), EB = dot3(E, B);
+    const T S = E2 + B2, d = B2 - E2;
+    const T sq = sqrt(fma(d, d, T(4) * EB * EB)) / S;
+    T x[3];
+    cross3(E, B, x);
+    const T f = T(2) * c / (S * (T(1) + sq));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) vE[k] = f * x[k];
+    const T Bp = sqrt(T(0.5) * fma(S, sq, d));
+    const T Ep = EB / Bp;
+    const T ebb = EB / B2;
+    T ep[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ep[k] = fma(-ebb, B[k], E[k]);
+    const T Ep2 = dot3(ep, ep);
+    const T Psi = T(2) * Ep * B2 / (Bp * S * (T(1) + sq));
+    const T eta = T(1) / (sqrt(B2) * sqrt(Psi * Psi * Ep2 / B2 + T(1)));
+    const T xi = eta * Psi;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bs[k] = fma(xi, ep[k], eta * B[k]);
+    om = T(1) - dot3(vE, vE) / (c * c);
+}
+
 // PROJ = false leaves out the projection of (b.grad)B and (v_E.grad)B onto
 // the plane normal to b: every use of (b.grad)b and (v_E.grad)b in the step
 // is b x (.) or v_E . (.), which annihilates the component along b (v_E is
 // normal to B), so the step's results are the same up to rounding.
-template <typename R, int ND, bool GRADS, bool PROJ = true>
+// BT = true builds the exact frame (bt_frame) in place of the simplified
+// one: b*, the exact v_E and kappa from it, E_par = E.b*; the gradient terms
+// are (b*.grad)b and (v_E.grad)b with grad b that of the lab-frame b = B/B
+// (projected), the records carrying no grad E.
+template <typename R, int ND, bool GRADS, bool PROJ = true, bool BT = false>
 __device__ __forceinline__ void make_frame(const FieldPt<R, ND> &F, R c, R inv_c2, Frame<R> &f)
 {
+    if constexpr (BT) {
+        R B2 = dot3(F.B, F.B);
+        f.ok = B2 > R(0);
+        if (!f.ok) B2 = R(1);
+        f.Bmag = sqrt(B2);
+        const R ib = R(1) / f.Bmag;
+        f.ib = ib;
+        R bl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) bl[k] = F.B[k] * ib;
+        R om;
+        bt_frame<R>(F.E, F.B, B2, c, f.vE, f.b, om);
+        if constexpr (sizeof(R) == 4) {
+            if (!(om > R(0.01))) {   // near |v_E| -> c: 1 - v_E^2/c^2 again in FP64
+                double e[3] = {F.E[0], F.E[1], F.E[2]}, bb[3] = {F.B[0], F.B[1], F.B[2]};
+                double v[3], s_[3], o;
+                bt_frame<double>(e, bb, (double)B2, (double)c, v, s_, o);
+                om = (R)o;
+            }
+        }
+        f.ok = f.ok && (om > R(0));
+        f.kappa = R(1) / sqrt(f.ok ? om : R(1));
+        f.Epar = dot3(F.E, f.b);
+        if (GRADS) {
+            R w[3], y[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                R sw = R(0), sy = R(0);
+#pragma unroll
+                for (int i = 0; i < ND; ++i) {
+                    sw = fma(f.b[i], F.dB[i][j], sw);
+                    sy = fma(f.vE[i], F.dB[i][j], sy);
+                }
+                w[j] = sw;
+                y[j] = sy;
+            }
+            const R bw = dot3(bl, w), by = dot3(bl, y);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                f.bgb[j] = fma(-bl[j], bw, w[j]) * ib;
+                f.vgb[j] = fma(-bl[j], by, y[j]) * ib;
+            }
+        }
+        return;
+    }
     R B2 = dot3(F.B, F.B);
     f.ok = B2 > R(0);
     if (!f.ok) B2 = R(1);
@@ -640,7 +726,7 @@ using StepRecs = std::conditional_t<HasCellCache<Gth>::value, CellRecs<ND, GM>, 
 // the cell of x^n when the caller gathered there through them).  Fh: the
 // fields at R^{n-1/2} = x^n - dxp/2 when the caller has gathered them already
 // (the same gather the step would make), else null.
-template <typename R, int ND, int GM, typename Gth>
+template <typename R, int ND, int GM, typename Gth, bool BT = false>
 __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, const int ib[ND],
                                            const R ln[ND], const R dxp[ND],
                                            const FieldPt<R, ND> &F0, R u[3], R disp[ND],
@@ -656,7 +742,7 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
     const R cq = s.c / s.qm;
     FieldPt<R, ND> F;
     Frame<R> f0, f;
-    make_frame<R, ND, GR, false>(F0, s.c, s.inv_c2, f0);
+    make_frame<R, ND, GR, false, BT>(F0, s.c, s.inv_c2, f0);
 
     // conversion at R^{n-1/2} = x^n - dxp/2 (Sec. 3.1)
     R pt[ND];
@@ -664,7 +750,7 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
     for (int d = 0; d < ND; ++d) pt[d] = fma(R(-0.5), dxp[d], ln[d]);
     if (Fh) F = *Fh;
     else gat(pt, F);
-    make_frame<R, ND, GR, false>(F, s.c, s.inv_c2, f);
+    make_frame<R, ND, GR, false, BT>(F, s.c, s.inv_c2, f);
     if (!(f0.ok && f.ok)) return false;
     R Gfull = sqrt(R(1) + dot3(u, u) * s.inv_c2);
     R upar = dot3(u, f.b);
@@ -744,7 +830,7 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
 #pragma unroll
         for (int d = 0; d < ND; ++d) pt[d] = ln[d] + dk[d];
         gat(pt, F);
-        make_frame<R, ND, GR, false>(F, s.c, s.inv_c2, f);
+        make_frame<R, ND, GR, false, BT>(F, s.c, s.inv_c2, f);
         okall = okall && f.ok;   // a bad frame fails the step after the loop
         gc_vel_ig(f, s, cq, upn, mu, uperp, V);
     }
@@ -754,7 +840,7 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
 #pragma unroll
     for (int d = 0; d < ND; ++d) pt[d] = fma(R(0.5), dk[d], ln[d]);
     gat(pt, F);
-    make_frame<R, ND, GR, false>(F, s.c, s.inv_c2, f);
+    make_frame<R, ND, GR, false, BT>(F, s.c, s.inv_c2, f);
     if (!f.ok) return false;
     R Gp = gamma_gc(f, s, upn, mu, uperp);
     vcurv_ig(f, s, cq, upn, R(1) / Gp, vc);

@@ -18,27 +18,36 @@
 
 namespace gcb {
 
-// particles per tile (= threads per block): 128 (4 warps), so a tile waits at
-// its barriers for few warps; FP64 could not stage more in 48 KB anyway
-#ifndef GCB_TILE_F32
-#define GCB_TILE_F32 128
+// Particles per tile (= threads per block).  FP32 2D: one warp, so a
+// tile's vote and compaction stay within the warp and no block barrier
+// holds warps back (the GCA-dominated 2D push measured 4% faster than with
+// 128; GB300, 2^24 particles); FP32 3D and FP64: 128 (4 warps), so the
+// compaction of mixed tiles (both branches) leaves at most one mixed warp
+// (the 3D sheet measured 7% faster than with 32).
+#ifndef GCB_TILE_F32_2D
+#define GCB_TILE_F32_2D 32
 #endif
-template <typename R>
-struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : GCB_TILE_F32; };
+#ifndef GCB_TILE_F32_3D
+#define GCB_TILE_F32_3D 128
+#endif
+template <typename R, int ND>
+struct Tile {
+    static constexpr int n = sizeof(R) == 8 ? 128 : (ND == 2 ? GCB_TILE_F32_2D : GCB_TILE_F32_3D);
+};
 
 // 1: tiles whose particles all take one branch skip the staging (see k_push_sr)
 #ifndef GCB_UNIFORM_TILES
 #define GCB_UNIFORM_TILES 1
 #endif
-// minimum resident blocks per SM requested from the register allocator
-#ifndef GCB_MIN_BLOCKS_F32
-#define GCB_MIN_BLOCKS_F32 4
+// minimum resident threads per SM requested from the register allocator:
+// FP32 2D 512 (at most 128 registers a thread); FP32 3D 384 (at most 170
+// registers: 184 unconstrained leaves 256 threads, which measured 16% slower,
+// and 512 spills)
+#ifndef GCB_MIN_THREADS_F32_2D
+#define GCB_MIN_THREADS_F32_2D 512
 #endif
-// 3D FP32: three blocks (at most 170 registers a thread; 184 unconstrained,
-// which leaves two) take the 3D sheet push from 2.53 to 2.11 ms at 2^24
-// particles; four (128 registers) spill and gain nothing more
-#ifndef GCB_MIN_BLOCKS_F32_3D
-#define GCB_MIN_BLOCKS_F32_3D 3
+#ifndef GCB_MIN_THREADS_F32_3D
+#define GCB_MIN_THREADS_F32_3D 384
 #endif
 #ifndef GCB_SEED_CACHE
 #define GCB_SEED_CACHE 1
@@ -49,11 +58,13 @@ struct Tile { static constexpr int n = sizeof(R) == 8 ? 128 : GCB_TILE_F32; };
 // 1: phase 1 gathers at R^{n-1/2} = x^n - dxp/2 together with x^n (2D), so
 // that the two gathers' loads are in flight at once
 #ifndef GCB_HOIST_HALF
-#define GCB_HOIST_HALF 0
+#define GCB_HOIST_HALF 1
 #endif
 template <typename R, int ND>
 struct MinBlocks {
-    static constexpr int n = sizeof(R) == 8 ? 1 : (ND == 3 ? GCB_MIN_BLOCKS_F32_3D : GCB_MIN_BLOCKS_F32);
+    static constexpr int n = sizeof(R) == 8
+        ? 1
+        : (ND == 3 ? GCB_MIN_THREADS_F32_3D : GCB_MIN_THREADS_F32_2D) / Tile<R, ND>::n;
 };
 
 template <typename R>
@@ -180,10 +191,10 @@ __device__ __forceinline__ bool finite_r(R v) { return isfinite(v); }
 // step).  FUSE = true: a.nsteps steps per launch, each tile's state kept in
 // its shared-memory slots between the steps and written once at the end (the
 // test-particle mode); every step's arithmetic is the unfused step's.
-template <typename R, int ND, int PM, int GM, bool FUSE>
-__global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(const PushArgs<R> a)
+template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false>
+__global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND>::n) k_push_sr(const PushArgs<R> a)
 {
-    constexpr int TPB = Tile<R>::n;
+    constexpr int TPB = Tile<R, ND>::n;
     constexpr int NWARP = TPB / 32;
     constexpr int NF = (GM != 0) ? 6 + 3 * ND : 6;   // staged field values at x^n
     using PosT = typename PosType<PM>::T;
@@ -418,8 +429,8 @@ __global__ void __launch_bounds__(Tile<R>::n, MinBlocks<R, ND>::n) k_push_sr(con
             bool ncv = false, fail = false;
             bool done = false;
             if (isg) {
-                done = gca_step_c<R, ND, GM>(Gth{a.g}, sp, ib, l, ds, F, us, disp, it, ncv, cr,
-                                             (HOIST && uni) ? &Fh : nullptr);
+                done = gca_step_c<R, ND, GM, Gth, BT>(Gth{a.g}, sp, ib, l, ds, F, us, disp, it,
+                                                      ncv, cr, (HOIST && uni) ? &Fh : nullptr);
                 if (!done) {
                     fail = true;
                     it = 0;
@@ -609,7 +620,7 @@ static void fill_args(PushArgs<R> &a, const gcb_particles *p, const gcb_particle
     a.stats = stats;
 }
 
-template <typename R, int ND, int PM, int GM, bool FUSE>
+template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false>
 static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
 {
     static int grid_cache[64] = {0};
@@ -622,7 +633,8 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     if (grid == 0) {
         int nsm = 0, occ = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM, FUSE>, Tile<R>::n, 0) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM, FUSE, BT>,
+                                                          Tile<R, ND>::n, 0) !=
                 cudaSuccess) {
             set_error("occupancy query failed: %s", cudaGetErrorString(cudaGetLastError()));
             return GCB_ECUDA;
@@ -630,11 +642,11 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
         grid = nsm * (occ > 0 ? occ : 1);
         grid_cache[dev] = grid;
     }
-    constexpr int TPB = Tile<R>::n;
+    constexpr int TPB = Tile<R, ND>::n;
     int64_t ntiles = (a.np + TPB - 1) / TPB;
     if (ntiles == 0) return GCB_OK;
     int nb = (int)(ntiles < grid ? ntiles : grid);
-    k_push_sr<R, ND, PM, GM, FUSE><<<nb, TPB, 0, st>>>(a);
+    k_push_sr<R, ND, PM, GM, FUSE, BT><<<nb, TPB, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));
@@ -643,15 +655,22 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     return GCB_OK;
 }
 
-template <typename R, int PM, bool FUSE>
+template <typename R, int PM, bool FUSE, bool BT = false>
 static gcb_status dispatch_dims(const PushArgs<R> &a, const gcb_grid *g, const gcb_params *prm,
                                 cudaStream_t st)
 {
     const bool grid_grad = prm->grad_mode == GCB_GRAD_GRID;
     if (g->ndim == 2)
-        return grid_grad ? launch_push<R, 2, PM, 2, FUSE>(a, st) : launch_push<R, 2, PM, 1, FUSE>(a, st);
-    return grid_grad ? launch_push<R, 3, PM, 2, FUSE>(a, st) : launch_push<R, 3, PM, 1, FUSE>(a, st);
+        return grid_grad ? launch_push<R, 2, PM, 2, FUSE, BT>(a, st)
+                         : launch_push<R, 2, PM, 1, FUSE, BT>(a, st);
+    return grid_grad ? launch_push<R, 3, PM, 2, FUSE, BT>(a, st)
+                     : launch_push<R, 3, PM, 1, FUSE, BT>(a, st);
 }
+
+// Which (arithmetic, position) pairs carry kernels of the exact drift frame:
+// FP64 and the FP32-pair positions of the mixed path.
+template <typename R, int PM>
+struct BtInstantiated : std::integral_constant<bool, sizeof(R) == 8 || PM == 1> {};
 
 // nsteps > 1: that many steps in one launch (test-particle mode)
 template <typename R, int PM>
@@ -661,6 +680,12 @@ static gcb_status dispatch_push(const gcb_particles *p, const gcb_particles *in,
 {
     PushArgs<R> a;
     fill_args<R>(a, p, in, g, prm, stats);
+    if (prm->drift_frame == GCB_FRAME_BT) {
+        // the exact drift frame: unfused launches only (checked by the caller)
+        if constexpr (BtInstantiated<R, PM>::value) return dispatch_dims<R, PM, false, true>(a, g, prm, st);
+        set_error("drift_frame GCB_FRAME_BT needs FP64 or FP32-pair positions");
+        return GCB_EUNSUPPORTED;
+    }
     if (nsteps <= 1) return dispatch_dims<R, PM, false>(a, g, prm, st);
     a.nsteps = nsteps;
     return dispatch_dims<R, PM, true>(a, g, prm, st);

@@ -19,6 +19,7 @@ POS_F64, POS_F32PAIR = 0, 1
 GRAD_DW, GRAD_GRID = 0, 1
 FORCE_NONE, FORCE_BORIS, FORCE_GCA = 0, 1, 2
 MU_CONSERVE, UPERP_CONSERVE = 0, 1
+FRAME_SIMPLE, FRAME_BT = 0, 1
 FLAG_S, FLAG_SPREV, FLAG_NONCONV, FLAG_GCAFAIL, FLAG_NONFINITE, FLAG_EXITED = 1, 2, 4, 8, 16, 32
 SPECIES_SHIFT = 6
 STATUS = {0: "GCB_OK", 1: "GCB_EINVAL", 2: "GCB_ECUDA", 3: "GCB_EUNSUPPORTED", 4: "GCB_ENOMEM"}
@@ -44,7 +45,8 @@ class GcbParams(C.Structure):
                 ("force", C.c_int32), ("gca_max_iter", C.c_int32),
                 ("gca_fixed_iters", C.c_int32), ("gca_tol", C.c_double),
                 ("sort_every", C.c_int32), ("sort_tile", C.c_int32 * 3),
-                ("step_index", C.c_int64), ("fuse_steps", C.c_int32)]
+                ("step_index", C.c_int64), ("fuse_steps", C.c_int32),
+                ("drift_frame", C.c_int32)]
 
 
 class GcbStats(C.Structure):
@@ -343,7 +345,7 @@ def make_params(p: dict, **over) -> GcbParams:
                      int(q.get("gca_max_iter", 16)), int(q.get("gca_fixed_iters", 0)),
                      float(q.get("gca_tol", 1e-7)), int(q.get("sort_every", 0)),
                      (C.c_int32 * 3)(*tile[:3]), int(q.get("step_index", 0)),
-                     int(q.get("fuse_steps", 0)))
+                     int(q.get("fuse_steps", 0)), int(q.get("drift_frame", 0)))
 
 
 class Workspace:

@@ -19,7 +19,8 @@ def oracle_params(p, **over):
                          curvature=q.get("curvature", 1), mu_mode=q.get("mu_mode", 0),
                          grad_mode=q.get("grad_mode", 0), force=q.get("force", 0),
                          max_iter=q.get("gca_max_iter", 16),
-                         fixed_iters=q.get("gca_fixed_iters", 0), tol=q.get("gca_tol", 1e-7))
+                         fixed_iters=q.get("gca_fixed_iters", 0), tol=q.get("gca_tol", 1e-7),
+                         frame=q.get("drift_frame", 0))
 
 
 def copy_state(st):

@@ -46,7 +46,8 @@ def test_struct_layout_matches_header(G, tmp_path):
     fields = [("gcb_grid", "rec", G.GcbGrid), ("gcb_grid", "stride", G.GcbGrid),
               ("gcb_particles", "flags", G.GcbParticles), ("gcb_particles", "pid", G.GcbParticles),
               ("gcb_params", "gca_tol", G.GcbParams), ("gcb_params", "step_index", G.GcbParams),
-              ("gcb_params", "fuse_steps", G.GcbParams), ("gcb_stats", "sum_ekin", G.GcbStats),
+              ("gcb_params", "fuse_steps", G.GcbParams), ("gcb_params", "drift_frame", G.GcbParams),
+              ("gcb_stats", "sum_ekin", G.GcbStats),
               ("gcb_grid_ks", "dl", G.GcbGridKs), ("gcb_ks_params", "r_out", G.GcbKsParams),
               ("gcb_ks_params", "kick_basis", G.GcbKsParams)]
     lines = "".join(f'printf("%zu %zu\\n", sizeof({t}), offsetof({t}, {f}));\n'
@@ -115,3 +116,24 @@ def test_binding_fails_loudly_without_the_library():
             "sys.exit(3)\n") % ROOT
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "is not built" in r.stdout, r.stdout + r.stderr
+
+
+def test_peak_library_exports_its_declared_symbol():
+    """include/gcb_peak.h's entry point is exported by libgcb_peak.so (the
+    benchmark's FMA-rate measurement), and answers invalid arguments without a
+    GPU."""
+    from paper_2007_14401_gb300 import build
+    path = build.build_peak()
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "gcb_peak.h")).read(),
+                 flags=re.S)
+    names = sorted(set(re.findall(r"\b(gcb_[a-z0-9_]+)\s*\(", txt)))
+    assert names == ["gcb_peak_fma"]
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True,
+                         text=True).stdout
+    assert set(names) <= set(re.findall(r" T (gcb_\w+)", out))
+    lib = C.CDLL(path)
+    lib.gcb_peak_fma.argtypes = [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double)]
+    v = C.c_double(0.0)
+    assert lib.gcb_peak_fma(7, 10, None, C.byref(v)) == 1
+    assert lib.gcb_peak_fma(0, 0, None, C.byref(v)) == 1
+    assert lib.gcb_peak_fma(0, 10, None, None) == 1

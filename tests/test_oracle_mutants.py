@@ -96,6 +96,32 @@ MUTANTS_KS = [
 ]
 
 
+# mistakes in the oracle's exact drift frame (Sec. 2.2), run against its own pins
+MUTANTS_BT = [
+    ("bt_vE_half", "out[k] = 2.0 * c * ExB[k] / (S * (1.0 + sq));",
+     "out[k] = c * ExB[k] / (S * (1.0 + sq));"),
+    ("bt_Bprime_sign", "double Bp = sqrt(0.5 * (B2 - E2 + S * sq));",
+     "double Bp = sqrt(0.5 * (B2 + E2 + S * sq));"),
+    ("bt_Psi_sign", "double Psi = 2.0 * Ep * B2 / (Bp * S * (1.0 + sq));",
+     "double Psi = -2.0 * Ep * B2 / (Bp * S * (1.0 + sq));"),
+    ("bt_eta_unrooted", "double eta = 1.0 / (Bm * sqrt(Psi * Psi * Ep2 / B2 + 1.0));",
+     "double eta = 1.0 / (Bm * (Psi * Psi * Ep2 / B2 + 1.0));"),
+    ("bt_bstar_unused", "for (int k = 0; k < 3; ++k) { P->vE[k] = bt[k]; P->b[k] = bt[3 + k]; }",
+     "for (int k = 0; k < 3; ++k) { P->vE[k] = bt[k]; }"),
+    ("bt_kappa_simplified", "P->kappa = bt[6];", "P->kappa = P->kappa;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS_BT, ids=[c[0] for c in MUTANTS_BT])
+def test_frame_pins_catch_planted_mistake(name, old, new, tmp_path):
+    lib = _build_mutant(str(tmp_path), SRC, old, new)
+    env = dict(os.environ, GCB_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_frame_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+
+
 # mistakes in the dual-number gradient oracle: its arithmetic on derivatives
 # and the seeding of the directions
 SRC_GRAD = os.path.join(ROOT, "oracle", "gcb_oracle_grad.cpp")
