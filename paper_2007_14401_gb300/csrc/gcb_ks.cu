@@ -450,27 +450,30 @@ __device__ __forceinline__ double gr_perp2(const GFrame &F, const StepCfg &c, do
 
 // GRGCA: half kick of u_par by D_par, implicit midpoint on (R, u_par) with the
 // full velocity rebuilt at the midpoint, half kick (Sec. 2.4 steps 1-3).
+// (sF, sl: the shared-memory rows and slot holding F0, reloaded for the
+// first iterate rather than kept in registers through the iteration)
 template <typename FT>
 __device__ bool grgca_step(const KsGrid<FT> &g, const StepCfg &c, double qm, const GFrame &F0,
-                           const TrigLog &t0, double R[3], double &upar, double mu, double uperp,
-                           const double bpg[3], int &iters, bool &nonconv, GFrame &F1)
+                           const double (*sF)[TPB], int sl, const TrigLog &t0, double R[3],
+                           double &upar, double mu, double uperp, const double bpg[3], int &iters,
+                           bool &nonconv, GFrame &F1)
 {
     const double ir0 = 1.0 / R[0];
     const double u1 = fma(0.5 * c.dt * F0.m.alpha * qm, F0.Dpar, upar);
     double Rk[3] = {R[0], R[1], R[2]}, wk = u1;
     iters = 0;
     nonconv = false;
-    bool okall = true;
+    // the frame at the current midpoint (Rk + R)/2.  The first iterate's
+    // midpoint is R^n itself (Rk = R): its frame is the switch's frame F0,
+    // reloaded from its shared-memory slot, with only the metric derivatives
+    // added (the same values a fresh gr_frame there would give)
+    GFrame Fb;
+    frame_load(sF, sl, Fb);
+    Fb.ok = F0.ok;
+    ks_metric(c.a, R[0], t0, true, Fb.m);
+    bool okall = Fb.ok;
     for (;;) {
-        double Rb[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Rb[k] = 0.5 * (Rk[k] + R[k]);
         const double ub = 0.5 * (wk + u1);
-        TrigLog tb;
-        trig_log_near(t0, R[0], ir0, R[1], Rb[0], Rb[1], tb);
-        GFrame Fb;
-        gr_frame(g, c.a, Rb, tb, true, Fb);
-        okall = okall && Fb.ok;
         const double Gam = Fb.kappa * sqrt(1.0 + ub * ub + gr_perp2(Fb, c, mu, uperp));
         const double iGam = 1.0 / Gam;
         const double ug = sqrt(gr_perp2(Fb, c, mu, uperp));
@@ -498,6 +501,14 @@ __device__ bool grgca_step(const KsGrid<FT> &g, const StepCfg &c, double qm, con
         wk = wn;
         ++iters;
         if (imr_done(c, iters, res, nonconv)) break;
+        // the next iterate's midpoint and its frame
+        double Rb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Rb[k] = 0.5 * (Rk[k] + R[k]);
+        TrigLog tb;
+        trig_log_near(t0, R[0], ir0, R[1], Rb[0], Rb[1], tb);
+        gr_frame(g, c.a, Rb, tb, true, Fb);
+        okall = okall && Fb.ok;
     }
     if (!okall) return false;
     TrigLog t1;
@@ -529,8 +540,8 @@ struct Args {
 // leaves it unchanged: it depends on theta through sin^2 and cos^2 only)
 template <typename FT>
 __device__ int ks_particle(const KsGrid<FT> &g, const StepCfg &c, double qm, int S, const GFrame &F0,
-                           const TrigLog &t0, double x[3], double u[3], int &iters, bool &nonconv,
-                           bool &fail, Metric &mfin)
+                           const double (*sF)[TPB], int sl, const TrigLog &t0, double x[3],
+                           double u[3], int &iters, bool &nonconv, bool &fail, Metric &mfin)
 {
     fail = false;
     if (S == 0) {
@@ -557,7 +568,7 @@ __device__ int ks_particle(const KsGrid<FT> &g, const StepCfg &c, double qm, int
                 for (int i = 0; i < 3; ++i) bpg[i] = ug[i] * iu;
                 mu = uperp * uperp / (2.0 * F0.Bmag * F0.kappa);
             }
-            ok = grgca_step(g, c, qm, F0, t0, R, upar, mu, uperp, bpg, iters, nonconv, F1);
+            ok = grgca_step(g, c, qm, F0, sF, sl, t0, R, upar, mu, uperp, bpg, iters, nonconv, F1);
         }
         if (ok) {
             // reconstruction at R^{n+1} (frame F1 from the step), gyration
@@ -694,7 +705,7 @@ __global__ void __launch_bounds__(TPB, 3) k_push_ks(const KsGrid<FT> g, const Ar
             int it = 0;
             bool ncv = false, fail = false;
             Metric mfin;
-            const int br = ks_particle(g, a.c, qm, S, F0, t0, x, u, it, ncv, fail, mfin);
+            const int br = ks_particle(g, a.c, qm, S, F0, s_F, sl, t0, x, u, it, ncv, fail, mfin);
             // poles: reflect theta, rotate phi by pi, flip u_theta
             if (x[1] < 0.0) { x[1] = -x[1]; x[2] += PI; u[1] = -u[1]; }
             if (x[1] > PI) { x[1] = 2.0 * PI - x[1]; x[2] += PI; u[1] = -u[1]; }
