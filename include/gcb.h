@@ -49,6 +49,7 @@ enum { GCB_GRAD_DW = 0, GCB_GRAD_GRID = 1 };             /* source of grad B */
 enum { GCB_FORCE_NONE = 0, GCB_FORCE_BORIS = 1, GCB_FORCE_GCA = 2 };
 enum { GCB_MU_CONSERVE = 0, GCB_UPERP_CONSERVE = 1 };
 enum { GCB_FRAME_SIMPLE = 0, GCB_FRAME_BT = 1 };
+enum { GCB_PHASE_KEEP = 0, GCB_PHASE_EVOLVE = 1 };
 
 /* Per-particle flag byte. */
 enum {
@@ -85,7 +86,7 @@ typedef struct {
 } gcb_grid;
 
 /*
- * Particle state, structure of arrays (device pointers), staggered as in
+ * Particle state, structure of arrays, staggered as in
  * Sec. 2.1: positions x^n at integer steps, u^{n-1/2} at half steps, and the
  * unwrapped displacement dxp = x^n - x^{n-1} of the previous step (the
  * decomposition point R^{n-1/2} = x^n - dxp/2 of Sec. 3.1 needs it).
@@ -94,7 +95,15 @@ typedef struct {
  *                             "lo" arrays, position = hi + lo (|lo| <= ulp(hi)/2).
  *   mom_dtype GCB_F64 / GCB_F32: element type of u[0..2] and dxp[0..ndim-1].
  * Positions are kept in [0, L_d) (periodic wrap after every step).
- * Each array must be aligned to its element size.
+ * Each array must be aligned to its element size and reachable from the
+ * current device at its own address: the device's memory, managed memory,
+ * or pinned / registered host memory (cudaHostAlloc, cudaHostRegister; with
+ * unified addressing the host address itself).  A particle state left in
+ * pinned host memory is pushed in place: the kernels read and write it
+ * across the host link every step (NVLink-C2C on a Grace host), with no
+ * staging copies.  Every entry point that takes particles checks each array
+ * with cudaPointerGetAttributes before any launch and returns GCB_EINVAL for
+ * one the device cannot reach (plain pageable host memory included).
  */
 typedef struct {
     int64_t n;               /* number of particles (>= 0) */
@@ -146,6 +155,13 @@ typedef struct {
                                 those of b* (the records carry no grad E).
                                 GCB_FRAME_BT: gcb_push_sr only, unfused, FP64 or
                                 FP32-pair positions; elsewhere GCB_EUNSUPPORTED. */
+    int32_t gyro_phase;      /* GCB_PHASE_KEEP (0): the reconstruction keeps the
+                                gyration direction of the decomposition (Sec. 3.1);
+                                GCB_PHASE_EVOLVE: it turns that direction about b
+                                by the step's gyro-phase -(q/m) B dt/(c kappa
+                                Gamma) at R^{n+1/2} (the extra equation Sec. 3.1
+                                says could be added).  gcb_push_sr only; the
+                                covariant push and the adjoint refuse it. */
 } gcb_params;
 
 /* Counters of one gcb_push_sr call, summed over its steps. */

@@ -382,6 +382,13 @@ static int decompose_at(const point_t *P, const orc_params *p, double qm,
 /* u = u_par b + (v_E + v_c(R, u_par)) Gamma(R, u_par) + u_perp,g b_perp,g, */
 /* u_perp,g = sqrt(2 mu B kappa / m) (or the held u_perp,g), the direction  */
 /* b_perp,g kept from the decomposition.                                    */
+/* With gyro_phase = 1 the phase is evolved instead (the extra equation     */
+/* Sec. 3.1 says could be added): d phi/dt = the gyro-frequency, which in   */
+/* the frame drifting with v_E is |q| B'/(m c gamma') with B' = B/kappa and  */
+/* gamma' = Gamma/kappa, and in lab time (divided by kappa) |q| B/(m c kappa */
+/* Gamma).  A charge gyrates about B in the sense of -q: b_perp,g turns      */
+/* about b by phi = -(q/m) B dt/(c kappa Gamma), evaluated at R^{n+1/2} with */
+/* Gamma(R^{n+1/2}, u_par^{n+1/2}).                                          */
 static void reconstruct_at(const point_t *P, const orc_params *p, double qm,
                            double upar, double mu, double uperp,
                            const double bpg[3], double u[3])
@@ -390,8 +397,16 @@ static void reconstruct_at(const point_t *P, const orc_params *p, double qm,
     double vc[3];
     v_curv(P, p, qm, upar, G, vc);
     double ug = sqrt(perp_sq(P, p, mu, uperp));
+    double dir[3] = {bpg[0], bpg[1], bpg[2]};
+    if (p->gyro_phase) {
+        double phi = -qm * P->Bmag * p->dt / (p->c * P->kappa * G);
+        double bxd[3];
+        cross3(P->b, bpg, bxd);
+        double cs = cos(phi), sn = sin(phi);
+        for (int k = 0; k < 3; ++k) dir[k] = cs * bpg[k] + sn * bxd[k];
+    }
     for (int k = 0; k < 3; ++k)
-        u[k] = upar * P->b[k] + (P->vE[k] + vc[k]) * G + ug * bpg[k];
+        u[k] = upar * P->b[k] + (P->vE[k] + vc[k]) * G + ug * dir[k];
 }
 
 int orc_decompose(const orc_field *f, const orc_params *p, double qm,

@@ -68,6 +68,8 @@ typedef struct {
     int fixed_iters;     /* > 0: exactly this many iterations, no test */
     double tol;          /* absolute stopping tolerance on |R^{k+1}-R^k|_inf */
     int frame;           /* ORC_FRAME_SIMPLE (b, v_E = cExB/B^2) or ORC_FRAME_BT */
+    int gyro_phase;      /* 0: gyration direction kept (Sec. 3.1); 1: advanced by
+                            the gyro-frequency over the step */
 } orc_params;
 
 typedef struct {

@@ -463,15 +463,16 @@ extern "C" {
  *   with the final one (values, as the oracle's push).
  *   jac: (n, 7, nm + 3), row-major: d(final x0, x1, u0, u1, u2, dxp0, dxp1)
  *   / d(a_0 .. a_{nm-1}, u0_x, u0_y, u0_z) of each particle.
- * Returns 0, or 1 for invalid arguments (the exact drift frame is not
- * differentiated here).
+ * Returns 0, or 1 for invalid arguments (the exact drift frame and the
+ * evolved gyration phase are not differentiated here).
  */
 int orcg_push_jac(long n, double *x, double *u, double *dxp, unsigned char *flags,
                   long nx, long ny, double dx, double dy, const double *base, const double *pat,
                   int nm, const double *amps, const orc_params *p, int n_steps, int nthreads,
                   double *jac)
 {
-    if (nm < 0 || nm > NM_MAX || n < 0 || nx < 1 || ny < 1 || p->frame != ORC_FRAME_SIMPLE)
+    if (nm < 0 || nm > NM_MAX || n < 0 || nx < 1 || ny < 1 || p->frame != ORC_FRAME_SIMPLE ||
+        p->gyro_phase != 0)
         return 1;
     ModeField f{{nx, ny}, {dx, dy}, base, pat, nm, amps};
 #ifdef _OPENMP

@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(TPB) k_adjoint_sr(const AdjArgs<T> a)
         sd.qm = D(sp.qm);
         sd.curvature = sp.curvature;
         sd.mu_mode = sp.mu_mode;
+        sd.phase = 0;
         sd.max_iter = sp.max_iter;
         sd.fixed_iters = gca ? iters : sp.fixed_iters;   // replay exactly this many
         sd.tol = D(T(-1));
@@ -760,6 +761,7 @@ gcb_status adjoint_step(const gcb_particles *s, const gcb_grid *g, const gcb_par
         a.sp.qm = T(0);
         a.sp.curvature = prm->curvature;
         a.sp.mu_mode = prm->mu_mode;
+        a.sp.phase = 0;   // the adjoint differentiates the step with the direction kept
         a.sp.max_iter = prm->gca_max_iter;
         a.sp.fixed_iters = prm->gca_fixed_iters;
         a.sp.tol = (T)prm->gca_tol;

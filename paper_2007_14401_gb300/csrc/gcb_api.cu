@@ -27,6 +27,50 @@ void set_error(const char *fmt, ...)
 
 static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+// Whether the current device can dereference ptr at that address: its own
+// device memory, managed memory, or pinned / registered host memory (mapped
+// at the same address under unified addressing).  Checked before any launch,
+// so that a pointer the GPU cannot reach is refused instead of faulting a
+// kernel.  Plain (unregistered) host memory is refused even where the GPU
+// could read it coherently.
+static bool reachable(const void *ptr)
+{
+    if (!ptr) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
+    switch (at.type) {
+    case cudaMemoryTypeDevice: return at.device == dev;
+    case cudaMemoryTypeManaged: return true;
+    case cudaMemoryTypeHost: return at.devicePointer == ptr;
+    default: return false;
+    }
+}
+
+// (staggered = false: the covariant state, which has no displacement arrays)
+static gcb_status check_reachable(const gcb_particles *p, int nd, bool staggered = true)
+{
+    if (p->n == 0) return GCB_OK;
+    const void *arrs[16];
+    int k = 0;
+    for (int d = 0; d < nd; ++d) {
+        arrs[k++] = p->x[d];
+        if (staggered) arrs[k++] = p->dxp[d];
+        if (p->pos_mode == GCB_POS_F32PAIR) arrs[k++] = p->x_lo[d];
+    }
+    for (int c = 0; c < 3; ++c) arrs[k++] = p->u[c];
+    arrs[k++] = p->flags;
+    if (p->pid) arrs[k++] = p->pid;
+    for (int i = 0; i < k; ++i)
+        if (!reachable(arrs[i])) {
+            set_error("a particle array (pointer %p) is not reachable from the current device "
+                      "(device, managed or pinned host memory)", arrs[i]);
+            return GCB_EINVAL;
+        }
+    return GCB_OK;
+}
+
 static gcb_status check_grid(const gcb_grid *g)
 {
     if (!g) { set_error("grid is NULL"); return GCB_EINVAL; }
@@ -170,6 +214,10 @@ gcb_status gcb_pos_split(int64_t n, const double *x, float *hi, float *lo, void 
 {
     if (n < 0 || (n > 0 && (!x || !hi || !lo))) { set_error("gcb_pos_split: bad arguments"); return GCB_EINVAL; }
     if (n == 0) return GCB_OK;
+    if (!reachable(x) || !reachable(hi) || !reachable(lo)) {
+        set_error("gcb_pos_split: an array is not reachable from the current device");
+        return GCB_EINVAL;
+    }
     k_split<<<grid_for(n), 256, 0, (cudaStream_t)cuda_stream>>>(n, x, hi, lo);
     return launch_check("gcb_pos_split");
 }
@@ -178,6 +226,10 @@ gcb_status gcb_pos_join(int64_t n, const float *hi, const float *lo, double *x, 
 {
     if (n < 0 || (n > 0 && (!x || !hi || !lo))) { set_error("gcb_pos_join: bad arguments"); return GCB_EINVAL; }
     if (n == 0) return GCB_OK;
+    if (!reachable(x) || !reachable(hi) || !reachable(lo)) {
+        set_error("gcb_pos_join: an array is not reachable from the current device");
+        return GCB_EINVAL;
+    }
     k_join<<<grid_for(n), 256, 0, (cudaStream_t)cuda_stream>>>(n, hi, lo, x);
     return launch_check("gcb_pos_join");
 }
@@ -233,6 +285,10 @@ static gcb_status check_problem(const gcb_particles *p, const gcb_grid *g, const
         set_error("drift_frame must be GCB_FRAME_SIMPLE or GCB_FRAME_BT");
         return GCB_EINVAL;
     }
+    if (prm->gyro_phase != GCB_PHASE_KEEP && prm->gyro_phase != GCB_PHASE_EVOLVE) {
+        set_error("gyro_phase must be GCB_PHASE_KEEP or GCB_PHASE_EVOLVE");
+        return GCB_EINVAL;
+    }
     if (prm->drift_frame == GCB_FRAME_BT && prm->fuse_steps > 1) {
         set_error("drift_frame GCB_FRAME_BT runs one step per launch (fuse_steps <= 1)");
         return GCB_EUNSUPPORTED;
@@ -282,6 +338,11 @@ static gcb_status check_problem(const gcb_particles *p, const gcb_grid *g, const
             if (!p->u[k] || !aligned(p->u[k], me)) { set_error("u[%d] NULL or misaligned", k); return GCB_EINVAL; }
         if (!p->flags) { set_error("flags NULL"); return GCB_EINVAL; }
         if (p->pid && !aligned(p->pid, 8)) { set_error("pid misaligned"); return GCB_EINVAL; }
+        if (!reachable(g->rec)) {
+            set_error("the grid records are not reachable from the current device");
+            return GCB_EINVAL;
+        }
+        return check_reachable(p, p->ndim);
     }
     return GCB_OK;
 }
@@ -366,8 +427,9 @@ gcb_status gcb_push_ks(const gcb_particles *p, const gcb_grid_ks *gk, const gcb_
         return GCB_EUNSUPPORTED;
     }
     if (prm->c != 1.0) { set_error("the covariant scheme uses c = 1"); return GCB_EINVAL; }
-    if (prm->drift_frame != GCB_FRAME_SIMPLE) {
-        set_error("the covariant scheme uses the simplified drift frame only");
+    if (prm->drift_frame != GCB_FRAME_SIMPLE || prm->gyro_phase != GCB_PHASE_KEEP) {
+        set_error("the covariant scheme uses the simplified drift frame and keeps the "
+                  "gyration direction");
         return GCB_EUNSUPPORTED;
     }
     if (!(prm->dt > 0) || !(prm->f_rho > 0) || !(prm->f_E > 0)) { set_error("dt, f_rho, f_E must be > 0"); return GCB_EINVAL; }
@@ -388,6 +450,8 @@ gcb_status gcb_push_ks(const gcb_particles *p, const gcb_grid_ks *gk, const gcb_
             }
         if (!p->flags) { set_error("flags NULL"); return GCB_EINVAL; }
         if (p->pid && !aligned(p->pid, 8)) { set_error("pid misaligned"); return GCB_EINVAL; }
+        s = check_reachable(p, 3, false);
+        if (s != GCB_OK) return s;
     }
     if (!ws || !aligned(ws, 256)) { set_error("workspace NULL or not 256-byte aligned"); return GCB_EINVAL; }
     if (ws_bytes < kStatsBytes) { set_error("workspace too small"); return GCB_ENOMEM; }
@@ -665,8 +729,9 @@ static gcb_status check_adjoint(const gcb_particles *p, const gcb_grid *g, const
         set_error("the adjoint supports 2D grids with gradient records (grad_mode GRID)");
         return GCB_EUNSUPPORTED;
     }
-    if (prm->drift_frame != GCB_FRAME_SIMPLE) {
-        set_error("the adjoint differentiates the simplified drift frame only");
+    if (prm->drift_frame != GCB_FRAME_SIMPLE || prm->gyro_phase != GCB_PHASE_KEEP) {
+        set_error("the adjoint differentiates the simplified drift frame with the gyration "
+                  "direction kept only");
         return GCB_EUNSUPPORTED;
     }
     if (n_steps < 1 || ckpt_every < 1) { set_error("n_steps and ckpt_every must be >= 1"); return GCB_EINVAL; }

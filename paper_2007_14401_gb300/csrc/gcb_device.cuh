@@ -561,6 +561,7 @@ struct StepPar {
     R c, inv_c2, dt, half_dt, qm;
     int curvature, mu_mode, max_iter, fixed_iters;
     R tol;
+    int phase;   // 1: the gyration phase advances over the step (GCB_PHASE_EVOLVE)
 };
 
 // Gyration energy term of Eq. (lfacgca2): 2 mu B kappa / m, or u_perp,g^2
@@ -845,6 +846,27 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
     R Gp = gamma_gc(f, s, upn, mu, uperp);
     vcurv_ig(f, s, cq, upn, R(1) / Gp, vc);
     R un = s.mu_mode ? uperp : sqrt(R(2) * mu * f.Bmag * f.kappa);
+    if constexpr (std::is_floating_point<R>::value) {
+        if (s.phase) {
+            // evolved gyration phase: b_perp,g turns about b by the step's
+            // gyro-phase phi = -(q/m) B dt/(c kappa Gamma) (the lab-time rate of
+            // the gyration in the frame drifting with v_E), taken in FP64 (the
+            // angle reaches Omega_C dt ~ 1e5 rad in strongly magnetized runs)
+            const double phi = -(double)s.qm * (double)f.Bmag * (double)s.dt /
+                               ((double)s.c * (double)f.kappa * (double)Gp);
+            // the angle in half turns, wrapped into [-1, 1] (exact for the
+            // multiples of 2 removed), then sin and cos of pi times it
+            const double t = phi * 0.31830988618379067;   // 1/pi
+            const double r = fma(-2.0, rint(0.5 * t), t);
+            R sn, cs;
+            if constexpr (sizeof(R) == 4) sincospif((float)r, &sn, &cs);
+            else sincospi(r, &sn, &cs);
+            R bxd[3];
+            cross3(f.b, bpg, bxd);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) bpg[k] = fma(cs, bpg[k], sn * bxd[k]);
+        }
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) u[k] = fma(upn, f.b[k], fma(f.vE[k] + vc[k], Gp, un * bpg[k]));
 #pragma unroll

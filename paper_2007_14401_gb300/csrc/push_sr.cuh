@@ -608,6 +608,7 @@ static void fill_args(PushArgs<R> &a, const gcb_particles *p, const gcb_particle
     a.sp.qm = R(0);
     a.sp.curvature = prm->curvature;
     a.sp.mu_mode = prm->mu_mode;
+    a.sp.phase = prm->gyro_phase;
     a.sp.max_iter = prm->gca_max_iter;
     a.sp.fixed_iters = prm->gca_fixed_iters;
     a.sp.tol = (R)prm->gca_tol;

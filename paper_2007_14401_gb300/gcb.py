@@ -20,6 +20,7 @@ GRAD_DW, GRAD_GRID = 0, 1
 FORCE_NONE, FORCE_BORIS, FORCE_GCA = 0, 1, 2
 MU_CONSERVE, UPERP_CONSERVE = 0, 1
 FRAME_SIMPLE, FRAME_BT = 0, 1
+PHASE_KEEP, PHASE_EVOLVE = 0, 1
 FLAG_S, FLAG_SPREV, FLAG_NONCONV, FLAG_GCAFAIL, FLAG_NONFINITE, FLAG_EXITED = 1, 2, 4, 8, 16, 32
 SPECIES_SHIFT = 6
 STATUS = {0: "GCB_OK", 1: "GCB_EINVAL", 2: "GCB_ECUDA", 3: "GCB_EUNSUPPORTED", 4: "GCB_ENOMEM"}
@@ -46,7 +47,7 @@ class GcbParams(C.Structure):
                 ("gca_fixed_iters", C.c_int32), ("gca_tol", C.c_double),
                 ("sort_every", C.c_int32), ("sort_tile", C.c_int32 * 3),
                 ("step_index", C.c_int64), ("fuse_steps", C.c_int32),
-                ("drift_frame", C.c_int32)]
+                ("drift_frame", C.c_int32), ("gyro_phase", C.c_int32)]
 
 
 class GcbStats(C.Structure):
@@ -189,29 +190,52 @@ class Grid:
 # particle state
 # --------------------------------------------------------------------------
 class State:
-    """Particle state on the device in the library's SoA layout.
+    """Particle state in the library's SoA layout.
 
     precision "fp64": float64 positions and momenta;  "mixed": float32
     momenta and displacements, positions float64 (pos_mode "f64") or float32
-    pairs (pos_mode "pair")."""
+    pairs (pos_mode "pair").  device "cuda" (or "cuda:k") keeps it in device
+    memory; "pinned" in pinned host memory, which the kernels read and write
+    in place across the host link (include/gcb.h: host-resident particles)."""
 
     def __init__(self, n, ndim, precision="mixed", pos_mode="pair", device="cuda",
                  with_pid=False):
         self.n, self.ndim, self.precision = int(n), int(ndim), precision
+        self.host = device == "pinned"
         self.pos_mode = POS_F32PAIR if (precision == "mixed" and pos_mode == "pair") else POS_F64
         self.mom_dtype = F64 if precision == "fp64" else F32
         mdt = torch.float64 if self.mom_dtype == F64 else torch.float32
         if self.pos_mode == POS_F64:
-            self.x = torch.empty((ndim, self.n), dtype=torch.float64, device=device)
+            self.x = self._alloc((ndim, self.n), torch.float64, device)
             self.x_lo = None
         else:
-            self.x = torch.empty((ndim, self.n), dtype=torch.float32, device=device)
-            self.x_lo = torch.empty((ndim, self.n), dtype=torch.float32, device=device)
-        self.u = torch.empty((3, self.n), dtype=mdt, device=device)
-        self.dxp = torch.empty((ndim, self.n), dtype=mdt, device=device)
-        self.flags = torch.empty((self.n,), dtype=torch.uint8, device=device)
-        self.pid = torch.arange(self.n, dtype=torch.int64, device=device) if with_pid else None
+            self.x = self._alloc((ndim, self.n), torch.float32, device)
+            self.x_lo = self._alloc((ndim, self.n), torch.float32, device)
+        self.u = self._alloc((3, self.n), mdt, device)
+        self.dxp = self._alloc((ndim, self.n), mdt, device)
+        self.flags = self._alloc((self.n,), torch.uint8, device)
+        self.pid = None
+        if with_pid:
+            self.pid = self._alloc((self.n,), torch.int64, device)
+            self.pid.copy_(torch.arange(self.n, dtype=torch.int64))
         self._make_struct()
+
+    def _alloc(self, shape, dtype, device=None):
+        """A buffer the library's kernels can reach for this state: pinned host
+        memory for a host-resident state, device memory otherwise."""
+        if getattr(self, "host", False):
+            return torch.empty(shape, dtype=dtype, device="cpu", pin_memory=True)
+        return torch.empty(shape, dtype=dtype, device=device if device else self.u.device)
+
+    def _reachable(self, t: torch.Tensor) -> torch.Tensor:
+        """t as a contiguous tensor the kernels can reach (copied if needed)."""
+        if self.host:
+            if t.is_cuda or not t.is_pinned() or not t.is_contiguous():
+                out = self._alloc(tuple(t.shape), t.dtype)
+                out.copy_(t)
+                return out
+            return t
+        return t.to(self.u.device).contiguous()
 
     def _make_struct(self):
         s = GcbParticles()
@@ -242,9 +266,9 @@ class State:
         return self
 
     def load(self, st: dict, stream=None):
-        """Copy a plain float64 state (oracle layout) into this device state."""
+        """Copy a plain float64 state (oracle layout) into this state."""
         mdt = self.u.dtype
-        x64 = torch.as_tensor(np.ascontiguousarray(st["x"], dtype=np.float64)).to(self.x.device)
+        x64 = self._reachable(torch.as_tensor(np.ascontiguousarray(st["x"], dtype=np.float64)))
         if self.pos_mode == POS_F64:
             self.x.copy_(x64)
         elif self.n:
@@ -260,8 +284,8 @@ class State:
 
     def set_tensors(self, x64: torch.Tensor, u: torch.Tensor, dxp: torch.Tensor,
                     flags: torch.Tensor, stream=None):
-        """Fill from device tensors: x float64 (ndim, n), u (3, n), dxp (ndim, n)."""
-        x64 = x64.to(torch.float64).contiguous()
+        """Fill from tensors: x float64 (ndim, n), u (3, n), dxp (ndim, n)."""
+        x64 = self._reachable(x64.to(torch.float64))
         if self.pos_mode == POS_F64:
             self.x.copy_(x64)
         elif self.n:
@@ -279,7 +303,7 @@ class State:
         streaming particle ranges through the GPU; lo a multiple of 64 keeps
         every array 256-byte aligned)."""
         v = State.__new__(State)
-        v.n, v.ndim, v.precision = int(hi - lo), self.ndim, self.precision
+        v.n, v.ndim, v.precision, v.host = int(hi - lo), self.ndim, self.precision, self.host
         v.pos_mode, v.mom_dtype = self.pos_mode, self.mom_dtype
         v.x, v.u, v.dxp, v.flags = (self.x[:, lo:hi], self.u[:, lo:hi], self.dxp[:, lo:hi],
                                     self.flags[lo:hi])
@@ -290,20 +314,26 @@ class State:
 
     def clone(self) -> "State":
         c = State.__new__(State)
-        c.n, c.ndim, c.precision = self.n, self.ndim, self.precision
+        c.n, c.ndim, c.precision, c.host = self.n, self.ndim, self.precision, self.host
+
+        def cp(t):
+            if t is None:
+                return None
+            if self.host:
+                return self._alloc(tuple(t.shape), t.dtype).copy_(t)
+            return t.clone()
+
         c.pos_mode, c.mom_dtype = self.pos_mode, self.mom_dtype
-        c.x, c.u, c.dxp, c.flags = (self.x.clone(), self.u.clone(), self.dxp.clone(),
-                                    self.flags.clone())
-        c.x_lo = self.x_lo.clone() if self.x_lo is not None else None
-        c.pid = self.pid.clone() if self.pid is not None else None
+        c.x, c.u, c.dxp, c.flags = cp(self.x), cp(self.u), cp(self.dxp), cp(self.flags)
+        c.x_lo, c.pid = cp(self.x_lo), cp(self.pid)
         c._make_struct()
         return c
 
     def x_f64(self, stream=None) -> torch.Tensor:
-        """Positions as a float64 (ndim, n) device tensor (pairs joined)."""
+        """Positions as a float64 (ndim, n) tensor, on the state's side (pairs joined)."""
         if self.pos_mode == POS_F64:
             return self.x.clone()
-        x = torch.empty((self.ndim, self.n), dtype=torch.float64, device=self.x.device)
+        x = self._alloc((self.ndim, self.n), torch.float64, self.x.device)
         for d in range(self.ndim if self.n else 0):
             _check(_lib.gcb_pos_join(self.n, C.c_void_p(self.x[d].data_ptr()),
                                      C.c_void_p(self.x_lo[d].data_ptr()),
@@ -316,7 +346,7 @@ class State:
         if self.pos_mode == POS_F64:
             x = self.x.double()
         else:
-            x = torch.empty((self.ndim, self.n), dtype=torch.float64, device=self.x.device)
+            x = self._alloc((self.ndim, self.n), torch.float64, self.x.device)
             if self.n:
                 for d in range(self.ndim):
                     _check(_lib.gcb_pos_join(self.n, C.c_void_p(self.x[d].data_ptr()),
@@ -345,7 +375,13 @@ def make_params(p: dict, **over) -> GcbParams:
                      int(q.get("gca_max_iter", 16)), int(q.get("gca_fixed_iters", 0)),
                      float(q.get("gca_tol", 1e-7)), int(q.get("sort_every", 0)),
                      (C.c_int32 * 3)(*tile[:3]), int(q.get("step_index", 0)),
-                     int(q.get("fuse_steps", 0)), int(q.get("drift_frame", 0)))
+                     int(q.get("fuse_steps", 0)), int(q.get("drift_frame", 0)),
+                     int(q.get("gyro_phase", 0)))
+
+
+def _work_device(state):
+    """The device of a state's workspace (a host-resident state's: the current GPU)."""
+    return "cuda" if getattr(state, "host", False) else state.x.device
 
 
 class Workspace:
@@ -361,7 +397,7 @@ def sort(state: State, grid: Grid, params: GcbParams, stream=None,
     if workspace is None:
         q = GcbParams.from_buffer_copy(params)
         q.sort_every = max(1, q.sort_every)
-        workspace = Workspace(state, grid, q, state.x.device)
+        workspace = Workspace(state, grid, q, _work_device(state))
     rc = _lib.gcb_sort_sr(C.byref(state.s), C.byref(grid.s), C.byref(params), _stream_ptr(stream),
                           C.c_void_p(workspace.buf.data_ptr()), workspace.nbytes)
     _check(rc, "gcb_sort_sr")
@@ -371,7 +407,7 @@ def push(state: State, grid: Grid, params: GcbParams, n_steps: int = 1, stream=N
          workspace: Workspace | None = None, stats: bool = True):
     """Advance ``state`` by n_steps coupled steps in place; returns the stats
     dict (synchronizing the stream) when ``stats`` is true, else None."""
-    ws = workspace or Workspace(state, grid, params, state.x.device)
+    ws = workspace or Workspace(state, grid, params, _work_device(state))
     out = GcbStats() if stats else None
     rc = _lib.gcb_push_sr(C.byref(state.s), C.byref(grid.s), C.byref(params), int(n_steps),
                           _stream_ptr(stream), C.c_void_p(ws.buf.data_ptr()), ws.nbytes,
@@ -566,7 +602,7 @@ def push_ks(state: State, grid: KsGrid, params: GcbParams, n_steps: int = 1, str
             workspace: Workspace | None = None, stats: bool = True):
     """n_steps covariant coupled steps of ``state`` (FP64, ndim 3) in place."""
     if workspace is None:
-        workspace = ks_workspace(state.x.device)
+        workspace = ks_workspace(_work_device(state))
     out = GcbStats() if stats else None
     rc = _lib.gcb_push_ks(C.byref(state.s), C.byref(grid.s), C.byref(grid.kp), C.byref(params),
                           int(n_steps), _stream_ptr(stream), C.c_void_p(workspace.buf.data_ptr()),

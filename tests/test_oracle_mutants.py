@@ -122,6 +122,28 @@ def test_frame_pins_catch_planted_mistake(name, old, new, tmp_path):
     assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
 
 
+# mistakes in the evolved gyration phase, run against its own pins
+MUTANTS_PHASE = [
+    ("phase_sign", "double phi = -qm * P->Bmag * p->dt / (p->c * P->kappa * G);",
+     "double phi = qm * P->Bmag * p->dt / (p->c * P->kappa * G);"),
+    ("phase_kappa_dropped", "double phi = -qm * P->Bmag * p->dt / (p->c * P->kappa * G);",
+     "double phi = -qm * P->Bmag * p->dt / (p->c * G);"),
+    ("phase_gamma_dropped", "double phi = -qm * P->Bmag * p->dt / (p->c * P->kappa * G);",
+     "double phi = -qm * P->Bmag * p->dt / (p->c * P->kappa);"),
+    ("phase_axis_reversed", "cross3(P->b, bpg, bxd);", "cross3(bpg, P->b, bxd);"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS_PHASE, ids=[c[0] for c in MUTANTS_PHASE])
+def test_phase_pins_catch_planted_mistake(name, old, new, tmp_path):
+    lib = _build_mutant(str(tmp_path), SRC, old, new)
+    env = dict(os.environ, GCB_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_phase_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+
+
 # mistakes in the dual-number gradient oracle: its arithmetic on derivatives
 # and the seeding of the directions
 SRC_GRAD = os.path.join(ROOT, "oracle", "gcb_oracle_grad.cpp")
