@@ -110,7 +110,12 @@ class Detail(C.Structure):
                 ("upar_new", C.c_double), ("mu", C.c_double), ("uperp", C.c_double),
                 ("Gamma_full", C.c_double), ("Gamma1", C.c_double), ("k1", C.c_double),
                 ("k2", C.c_double), ("k3", C.c_double), ("Rn", C.c_double * 3),
-                ("Rnp1", C.c_double * 3), ("bpg", C.c_double * 3)]
+                ("Rnp1", C.c_double * 3), ("bpg", C.c_double * 3), ("vstep", C.c_double * 3)]
+
+
+class DepositT(C.Structure):
+    _fields_ = [("q", C.c_double * 4), ("w", C.c_void_p), ("J", C.c_void_p * 3),
+                ("Jabs", C.c_void_p * 3), ("n_skipped", C.c_long)]
 
 
 class KsField(C.Structure):
@@ -148,6 +153,13 @@ def _load():
                                         C.c_void_p * 3, C.c_void_p, P(Field), P(Params),
                                         C.c_int, C.c_int, P(Stats)]
             lib.orc_push_sr.restype = C.c_int
+            lib.orc_push_sr_dep.argtypes = [C.c_long, C.c_void_p * 3, C.c_void_p * 3,
+                                            C.c_void_p * 3, C.c_void_p, P(Field), P(Params),
+                                            C.c_int, C.c_int, P(Stats), P(DepositT)]
+            lib.orc_push_sr_dep.restype = C.c_int
+            lib.orc_deposit.argtypes = [P(Field), D3, D3, C.c_double, C.c_double, C.c_double,
+                                        C.c_void_p * 3, C.c_void_p]
+            lib.orc_deposit.restype = C.c_int
             lib.orc_push_resolved.argtypes = [C.c_long, C.c_void_p * 3, C.c_void_p * 3,
                                               C.c_void_p, P(Field), P(Params), C.c_double,
                                               C.c_double, C.c_int]
@@ -303,9 +315,52 @@ def _ptrs(arrs, k):
     return p
 
 
+DEP_MAX_CELLS = 64
+
+
+class Current:
+    """Current grid of the oracle's deposition: J[a] float64 node arrays of
+    the field's shape, J_x at (i+1/2, j, k), J_y at (i, j+1/2, k), J_z at
+    (i, j, k+1/2) (2D: at the node), each stored at its lower node's index;
+    Jabs[a] the sum of the absolute contributions (the scale of its rounding).
+    q: charge of one macro-particle per species; w: per-particle weights or
+    None (1)."""
+
+    def __init__(self, shape, q, w=None):
+        self.J = [np.zeros(shape) for _ in range(3)]
+        self.Jabs = [np.zeros(shape) for _ in range(3)]
+        self.q = tuple(q) + (0.0,) * (4 - len(q))
+        self.w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        self.n_skipped = 0
+
+    def struct(self):
+        d = DepositT()
+        for k in range(4):
+            d.q[k] = self.q[k]
+        d.w = None if self.w is None else self.w.ctypes.data
+        for a in range(3):
+            d.J[a] = self.J[a].ctypes.data
+            d.Jabs[a] = self.Jabs[a].ctypes.data
+        return d
+
+
+def deposit(field: OracleField, x0, disp, vz, Qw, dt, cur: Current) -> bool:
+    """Add one particle-step's current (path x0 -> x0 + disp, out-of-plane
+    velocity vz in 2D) to ``cur``; False when the path is too long."""
+    lib = _load()
+    nd = field.ndim
+    J = (C.c_void_p * 3)(*[cur.J[a].ctypes.data for a in range(3)])
+    Ja = (C.c_void_p * 3)(*[cur.Jabs[a].ctypes.data for a in range(3)])
+    rc = lib.orc_deposit(C.byref(field.s), (C.c_double * 3)(*(list(x0[:nd]) + [0.0] * (3 - nd))),
+                         (C.c_double * 3)(*(list(disp[:nd]) + [0.0] * (3 - nd))), vz, Qw, dt, J,
+                         C.cast(Ja, C.c_void_p))
+    return rc == 0
+
+
 def push_sr(state: dict, field: OracleField, params: Params, n_steps: int,
-            nthreads: int = 0) -> dict:
-    """Advance ``state`` (dict x, u, dxp, flags; modified in place) by n_steps."""
+            nthreads: int = 0, current: Current | None = None) -> dict:
+    """Advance ``state`` (dict x, u, dxp, flags; modified in place) by n_steps;
+    with ``current``, every step's current is added to it."""
     lib = _load()
     x, u, dxp, flags = state["x"], state["u"], state["dxp"], state["flags"]
     nd = field.ndim
@@ -316,9 +371,17 @@ def push_sr(state: dict, field: OracleField, params: Params, n_steps: int,
     us = [u[k] for k in range(3)]
     ds = [dxp[k] for k in range(nd)]
     st = Stats()
-    rc = lib.orc_push_sr(n, _ptrs(xs, nd), _ptrs(us, 3), _ptrs(ds, nd),
-                         flags.ctypes.data, C.byref(field.s), C.byref(params),
-                         n_steps, nthreads, C.byref(st))
+    if current is None:
+        rc = lib.orc_push_sr(n, _ptrs(xs, nd), _ptrs(us, 3), _ptrs(ds, nd),
+                             flags.ctypes.data, C.byref(field.s), C.byref(params),
+                             n_steps, nthreads, C.byref(st))
+    else:
+        assert current.w is None or current.w.shape == (n,)
+        d = current.struct()
+        rc = lib.orc_push_sr_dep(n, _ptrs(xs, nd), _ptrs(us, 3), _ptrs(ds, nd),
+                                 flags.ctypes.data, C.byref(field.s), C.byref(params),
+                                 n_steps, nthreads, C.byref(st), C.byref(d))
+        current.n_skipped += d.n_skipped
     if rc != 0:
         raise RuntimeError(f"orc_push_sr failed ({rc})")
     return {k: getattr(st, k) for k, _ in Stats._fields_}

@@ -14,6 +14,7 @@
 #include "gcb_oracle.h"
 
 #include <math.h>
+#include <stdlib.h>
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
 #endif
@@ -337,11 +338,14 @@ static void boris_kick(const double E[3], const double B[3], double qm,
 }
 
 static void boris_step(const double E[3], const double B[3], double qm,
-                       const orc_params *p, int nd, double u[3], double disp[3])
+                       const orc_params *p, int nd, double u[3], double disp[3],
+                       double v[3])
 {
     boris_kick(E, B, qm, p, 0.5 * p->dt, u);
     double g = sqrt(1.0 + dot3(u, u) / (p->c * p->c));
     for (int d = 0; d < 3; ++d) disp[d] = d < nd ? p->dt * u[d] / g : 0.0;
+    if (v)
+        for (int d = 0; d < 3; ++d) v[d] = u[d] / g;
 }
 
 /* ---------------------------------------------------------------------- */
@@ -569,6 +573,8 @@ void orc_step_one(const orc_field *f, const orc_params *p, double x[3],
                 gc_velocity(&Pk, p, qm, upn, mu, uperp, Vk);
                 for (int k = 0; k < 3; ++k)
                     Rk1[k] = k < nd ? xn[k] + 0.5 * p->dt * (Vn[k] + Vk[k]) : 0.0;
+                /* the step's guiding-center velocity (all three components) */
+                for (int k = 0; k < 3; ++k) d->vstep[k] = 0.5 * (Vn[k] + Vk[k]);
                 ++iters;
                 double res = 0.0;
                 for (int k = 0; k < nd; ++k) {
@@ -622,7 +628,7 @@ void orc_step_one(const orc_field *f, const orc_params *p, double x[3],
         }
     }
     if (use_boris) {
-        boris_step(P0.E, P0.B, qm, p, nd, unew, disp);
+        boris_step(P0.E, P0.B, qm, p, nd, unew, disp, d->vstep);
         d->branch = 1;
     } else {
         d->branch = 0;
@@ -649,16 +655,118 @@ void orc_step_one(const orc_field *f, const orc_params *p, double x[3],
 }
 
 /* ---------------------------------------------------------------------- */
+/* Current deposition (PiC coupling).  The paper's point (Sec. 1, 5) is     */
+/* that the coupled scheme hands a PiC code x and u at the usual staggered   */
+/* times, so the code deposits the step's current as for any particle; the  */
+/* paper gives no deposition of its own.  Reading: the particle is a         */
+/* cloud-in-cell cloud moving along the straight path x^n -> x^{n+1} at the  */
+/* step's constant velocity, and J is the exact time average of that cloud's */
+/* current on the staggered (Yee) points (definition in gcb_oracle.h).  With */
+/* the cloud-in-cell charge rho_i = sum Qw S(s - i)/V it satisfies the       */
+/* discrete continuity equation.  The time integral is split at every cell   */
+/* face the path crosses; inside a piece each factor is linear in t, the     */
+/* integrand a polynomial of degree <= 2, which Simpson's rule integrates    */
+/* exactly.                                                                 */
+/* ---------------------------------------------------------------------- */
+static double hat(double s)
+{
+    double a = fabs(s);
+    return a < 1.0 ? 1.0 - a : 0.0;
+}
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+int orc_deposit(const orc_field *f, const double x0[3], const double disp[3], double vz,
+                double Qw, double dt, double *const J[3], double *const Jabs[3])
+{
+    int nd = f->ndim;
+    double s0[3] = {0, 0, 0}, ds[3] = {0, 0, 0};
+    double V = 1.0;
+    for (int a = 0; a < nd; ++a) {
+        s0[a] = x0[a] / f->dx[a];
+        ds[a] = disp[a] / f->dx[a];
+        if (!(fabs(ds[a]) <= ORC_DEP_MAX_CELLS)) return 1;
+        V *= f->dx[a];
+    }
+    /* times (in units of dt) at which the path crosses a face s_a = integer */
+    double t[2 + 3 * (ORC_DEP_MAX_CELLS + 2)];
+    int nt = 0;
+    t[nt++] = 0.0;
+    t[nt++] = 1.0;
+    for (int a = 0; a < nd; ++a) {
+        if (ds[a] == 0.0) continue;
+        double lo = fmin(s0[a], s0[a] + ds[a]), hi = fmax(s0[a], s0[a] + ds[a]);
+        for (double m = floor(lo) + 1.0; m < hi; m += 1.0) t[nt++] = (m - s0[a]) / ds[a];
+    }
+    qsort(t, (size_t)nt, sizeof(double), cmp_double);
+    long nn[3] = {f->n[0], f->n[1], nd == 3 ? f->n[2] : 1};
+    for (int k = 0; k + 1 < nt; ++k) {
+        double ta = t[k], tb = t[k + 1];
+        if (!(tb > ta)) continue;
+        double tau = tb - ta;
+        /* the piece lies in one cell; positions at its start, middle, end */
+        long cell[3] = {0, 0, 0};
+        double sq[3][3] = {{0}};
+        for (int a = 0; a < nd; ++a) {
+            cell[a] = (long)floor(s0[a] + ds[a] * 0.5 * (ta + tb));
+            sq[0][a] = s0[a] + ds[a] * ta;
+            sq[1][a] = s0[a] + ds[a] * 0.5 * (ta + tb);
+            sq[2][a] = s0[a] + ds[a] * tb;
+        }
+        /* component a (in 2D also the out-of-plane one, a = 2): over the
+         * corners o of the cell along the axes other than a, the average
+         * over the piece of the product of those axes' hats */
+        int ncomp = 3;
+        for (int a = 0; a < ncomp; ++a) {
+            int oth[2], no = 0;
+            for (int b = 0; b < nd; ++b)
+                if (b != a) oth[no++] = b;
+            double pref = a < nd ? Qw * disp[a] * tau / (dt * V) : Qw * vz * tau / V;
+            for (int o = 0; o < (1 << no); ++o) {
+                long idx[3] = {cell[0], cell[1], cell[2]};
+                for (int r = 0; r < no; ++r) idx[oth[r]] += (o >> r) & 1;
+                double g[3];
+                for (int q = 0; q < 3; ++q) {
+                    g[q] = 1.0;
+                    for (int r = 0; r < no; ++r)
+                        g[q] *= hat(sq[q][oth[r]] - (double)idx[oth[r]]);
+                }
+                double avg = (g[0] + 4.0 * g[1] + g[2]) / 6.0;
+                double val = pref * avg;
+                long ii = wrap_index(idx[0], nn[0]), jj = wrap_index(idx[1], nn[1]),
+                     kk = wrap_index(idx[2], nn[2]);
+                long lin = (kk * nn[1] + jj) * nn[0] + ii;
+                J[a][lin] += val;
+                if (Jabs) Jabs[a][lin] += fabs(val);
+            }
+        }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Loops over steps and particles.                                          */
 /* ---------------------------------------------------------------------- */
-int orc_push_sr(long n, double *const x[3], double *const u[3],
-                double *const dxp[3], unsigned char *flags, const orc_field *f,
-                const orc_params *p, int n_steps, int nthreads, orc_stats *st)
+static int push_sr_impl(long n, double *const x[3], double *const u[3],
+                        double *const dxp[3], unsigned char *flags, const orc_field *f,
+                        const orc_params *p, int n_steps, int nthreads, orc_stats *st,
+                        orc_deposit_t *dep)
 {
     int nd = f->ndim;
     if (nd != 2 && nd != 3) return 1;
     orc_stats acc;
     memset(&acc, 0, sizeof(acc));
+    /* per-particle path of the step, deposited after the parallel loop */
+    double *path = NULL;
+    if (dep) {
+        dep->n_skipped = 0;
+        path = (double *)malloc(sizeof(double) * 8 * (size_t)(n > 0 ? n : 1));
+        if (!path) return 2;
+    }
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -677,10 +785,17 @@ int orc_push_sr(long n, double *const x[3], double *const u[3],
             for (int k = 0; k < 3; ++k) ui[k] = u[k][i];
             unsigned char fl = flags[i];
             orc_detail d;
+            double x0[3] = {xi[0], xi[1], xi[2]};
             orc_step_one(f, p, xi, ui, di, &fl, &d);
             for (int k = 0; k < nd; ++k) { x[k][i] = xi[k]; dxp[k][i] = di[k]; }
             for (int k = 0; k < 3; ++k) u[k][i] = ui[k];
             flags[i] = fl;
+            if (path) {
+                double *q = path + 8 * i;
+                for (int k = 0; k < 3; ++k) { q[k] = x0[k]; q[3 + k] = k < nd ? di[k] : 0.0; }
+                q[6] = d.vstep[2];
+                q[7] = d.branch;
+            }
             if (d.branch < 0) { ++nf; continue; }
             if (d.branch == 1) ++nb; else ++ng;
             int sp = (fl & ORC_FLAG_SPREV) ? 1 : 0, sn = (fl & ORC_FLAG_S) ? 1 : 0;
@@ -698,9 +813,34 @@ int orc_push_sr(long n, double *const x[3], double *const u[3],
         acc.sum_iter += si;
         if (mi > acc.max_iter) acc.max_iter = mi;
         acc.sum_ekin += ek;
+        if (dep) {
+            for (long i = 0; i < n; ++i) {
+                const double *q = path + 8 * i;
+                if (q[7] < 0.0) continue;   /* frozen: no step, no current */
+                double Qw = dep->q[(flags[i] >> 6) & 3] * (dep->w ? dep->w[i] : 1.0);
+                if (orc_deposit(f, q, q + 3, q[6], Qw, p->dt, dep->J, dep->Jabs))
+                    ++dep->n_skipped;
+            }
+        }
     }
+    free(path);
     if (st) *st = acc;
     return 0;
+}
+
+int orc_push_sr(long n, double *const x[3], double *const u[3],
+                double *const dxp[3], unsigned char *flags, const orc_field *f,
+                const orc_params *p, int n_steps, int nthreads, orc_stats *st)
+{
+    return push_sr_impl(n, x, u, dxp, flags, f, p, n_steps, nthreads, st, NULL);
+}
+
+int orc_push_sr_dep(long n, double *const x[3], double *const u[3],
+                    double *const dxp[3], unsigned char *flags,
+                    const orc_field *f, const orc_params *p, int n_steps,
+                    int nthreads, orc_stats *st, orc_deposit_t *dep)
+{
+    return push_sr_impl(n, x, u, dxp, flags, f, p, n_steps, nthreads, st, dep);
 }
 
 /* Gyro-resolved Boris reference (Sec. 4.1): the step is adapted every       */
@@ -740,7 +880,7 @@ int orc_push_resolved(long n, double *const x[3], double *const u[3],
             if (t + dt > t_end) dt = t_end - t;
             q.dt = dt;
             double disp[3];
-            boris_step(F, F + 3, qm, &q, nd, ui, disp);
+            boris_step(F, F + 3, qm, &q, nd, ui, disp, NULL);
             for (int k = 0; k < nd; ++k) xi[k] += disp[k];
             t += dt;
         }

@@ -110,6 +110,10 @@ typedef struct {
     double Gamma1;       /* Gamma(R^n, u_par^{n+1/2}) from the quadratic */
     double k1, k2, k3;
     double Rn[3], Rnp1[3], bpg[3];
+    double vstep[3];     /* velocity of the step's straight path: x^{n+1} - x^n
+                            = dt vstep (Boris: u^{n+1/2}/Gamma; GCA: the
+                            guiding-center velocity (V^n + V^K)/2); in 2D
+                            vstep[2] is its out-of-plane component */
 } orc_detail;
 
 /* The exact (Beklemishev-Tessarotto) drift frame of fields E, B (Sec. 2.2):
@@ -183,6 +187,37 @@ void orc_ks_step_one(const orc_ks_field *f, const orc_ks_params *kp, const orc_p
 int orc_push_ks(long n, double *const x[3], double *const u[3], unsigned char *flags,
                 const orc_ks_field *f, const orc_ks_params *kp, const orc_params *p,
                 const double *dl, int n_steps, int nthreads, orc_stats *st);
+
+/* ---- Current deposition (PiC coupling).  A particle-step is a linear-weight
+ * (cloud-in-cell) cloud of charge Qw moving from x^n to x^{n+1} = x^n + disp
+ * along a straight line at constant velocity; J is the time average over the
+ * step of its current on the staggered points of the node grid:
+ *   J_a at (i + e_a/2) = Qw/(dt V) int_0^dt v_a Pi(s_a - i_a - 1/2)
+ *                            prod_{b != a} S(s_b - i_b) dt,
+ * s = x/dx, S the unit hat, Pi the unit box, V the cell volume; in 2D J_z
+ * sits on the nodes, Qw/V int_0^dt v_z S(s_x - i) S(s_y - j) dt / dt.
+ * J_a is stored at the index of the point's lower node, node index
+ * (k*ny + j)*nx + i, periodic.  Paths longer than ORC_DEP_MAX_CELLS cells
+ * along an axis are left out (return 1). */
+#define ORC_DEP_MAX_CELLS 64
+
+typedef struct {
+    double q[4];         /* charge of one macro-particle per species */
+    const double *w;     /* per-particle weight (NULL: 1) */
+    double *J[3];        /* current, accumulated */
+    double *Jabs[3];     /* optional (NULL): sum of |contribution| per point */
+    long n_skipped;      /* out: particle-steps left out (path too long) */
+} orc_deposit_t;
+
+int orc_deposit(const orc_field *f, const double x0[3], const double disp[3], double vz,
+                double Qw, double dt, double *const J[3], double *const Jabs[3]);
+
+/* orc_push_sr that also deposits every advanced particle-step's current into
+ * dep (in particle order after each step's parallel loop). */
+int orc_push_sr_dep(long n, double *const x[3], double *const u[3],
+                    double *const dxp[3], unsigned char *flags,
+                    const orc_field *f, const orc_params *p, int n_steps,
+                    int nthreads, orc_stats *st, orc_deposit_t *dep);
 
 #ifdef __cplusplus
 }

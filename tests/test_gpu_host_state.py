@@ -1,9 +1,10 @@
 """Particle states left in pinned host memory (include/gcb.h: host-resident
 particles): the push reads and writes them in place across the host link.
 The results equal those of the same state in device memory bit for bit
-(flat FP64 and mixed paths with sorting and particle ids; the covariant
-push), and arrays the device cannot reach at their address (plain pageable
-host memory) are refused before any launch."""
+(flat FP64 and mixed paths with sorting and particle ids, compared particle
+by particle through the ids since the order inside a sort tile is not
+specified; the covariant push), and arrays the device cannot reach at their
+address (plain pageable host memory) are refused before any launch."""
 import ctypes as C
 
 import numpy as np
@@ -41,9 +42,13 @@ def test_host_state_equals_device_state(G, precision, pos_mode, gdt):
             s = G.push(ds, grid, gp, 1, workspace=ws)
         out.append((ds.to_numpy(), s))
     (a, sa), (b, sb) = out
+    oa, ob = np.argsort(a["pid"]), np.argsort(b["pid"])
     for k in a:
-        assert np.array_equal(a[k], b[k]), k
-    assert sa == sb
+        assert np.array_equal(a[k][..., oa], b[k][..., ob]), k
+    # the kinetic-energy sum is reduced with atomics in an unspecified order
+    assert {k: v for k, v in sa.items() if k != "sum_ekin"} == \
+        {k: v for k, v in sb.items() if k != "sum_ekin"}
+    assert sa["sum_ekin"] == pytest.approx(sb["sum_ekin"], rel=1e-12)
 
 
 def test_host_state_covariant(G):

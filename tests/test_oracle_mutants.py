@@ -144,6 +144,46 @@ def test_phase_pins_catch_planted_mistake(name, old, new, tmp_path):
     assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
 
 
+# mistakes in the oracle's current deposition and in the step velocity it uses
+MUTANTS_DEP = [
+    ("dep_midpoint_only", "double avg = (g[0] + 4.0 * g[1] + g[2]) / 6.0;",
+     "double avg = g[1];"),
+    ("dep_face_time_sign", "t[nt++] = (m - s0[a]) / ds[a];", "t[nt++] = (s0[a] - m) / ds[a];"),
+    ("dep_cell_at_piece_start", "cell[a] = (long)floor(s0[a] + ds[a] * 0.5 * (ta + tb));",
+     "cell[a] = (long)floor(s0[a] + ds[a] * ta);"),
+    ("dep_piece_duration_dropped",
+     "double pref = a < nd ? Qw * disp[a] * tau / (dt * V) : Qw * vz * tau / V;",
+     "double pref = a < nd ? Qw * disp[a] / (dt * V) : Qw * vz * tau / V;"),
+    ("dep_vz_over_dt",
+     "double pref = a < nd ? Qw * disp[a] * tau / (dt * V) : Qw * vz * tau / V;",
+     "double pref = a < nd ? Qw * disp[a] * tau / (dt * V) : Qw * vz * tau / (dt * V);"),
+    ("dep_corner_offset", "for (int r = 0; r < no; ++r) idx[oth[r]] += (o >> r) & 1;",
+     "for (int r = 0; r < no; ++r) idx[oth[r]] += o & 1;"),
+    ("dep_path_from_new_x", "for (int k = 0; k < 3; ++k) { q[k] = x0[k]; q[3 + k] = k < nd ? di[k] : 0.0; }",
+     "for (int k = 0; k < 3; ++k) { q[k] = xi[k]; q[3 + k] = k < nd ? di[k] : 0.0; }"),
+    ("dep_species_charge", "double Qw = dep->q[(flags[i] >> 6) & 3] * (dep->w ? dep->w[i] : 1.0);",
+     "double Qw = dep->q[0] * (dep->w ? dep->w[i] : 1.0);"),
+    ("dep_weight_dropped", "double Qw = dep->q[(flags[i] >> 6) & 3] * (dep->w ? dep->w[i] : 1.0);",
+     "double Qw = dep->q[(flags[i] >> 6) & 3];"),
+    ("vstep_gca_last_iterate", "for (int k = 0; k < 3; ++k) d->vstep[k] = 0.5 * (Vn[k] + Vk[k]);",
+     "for (int k = 0; k < 3; ++k) d->vstep[k] = Vk[k];"),
+    ("vstep_boris_gamma_dropped", "for (int d = 0; d < 3; ++d) v[d] = u[d] / g;",
+     "for (int d = 0; d < 3; ++d) v[d] = u[d];"),
+    ("dep_frozen_deposits", "if (q[7] < 0.0) continue;   /* frozen: no step, no current */",
+     "/* frozen particles not skipped */"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS_DEP, ids=[c[0] for c in MUTANTS_DEP])
+def test_deposit_pins_catch_planted_mistake(name, old, new, tmp_path):
+    lib = _build_mutant(str(tmp_path), SRC, old, new)
+    env = dict(os.environ, GCB_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_deposit_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+
+
 # mistakes in the dual-number gradient oracle: its arithmetic on derivatives
 # and the seeding of the directions
 SRC_GRAD = os.path.join(ROOT, "oracle", "gcb_oracle_grad.cpp")
