@@ -245,6 +245,65 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
                        gcb_stats *out);
 
 /*
+ * ---- Push with current deposition (PiC coupling).
+ * The paper presents the coupled scheme as usable inside a PiC code (Sec. 1,
+ * 5): each step returns x^{n+1} and u^{n+1/2} at the usual staggered times,
+ * whichever branch advanced the particle, and the code deposits the step's
+ * current.  The paper gives no deposition of its own; this one is the exact
+ * current of a linear-weight (cloud-in-cell) particle of charge Q w moving
+ * from x^n to x^{n+1} along a straight line at constant velocity, averaged
+ * over the step, on the staggered (Yee) points of the field's node grid:
+ *
+ *   J_a(i + e_a/2) = Q w / (dt V) int_0^dt v_a Pi(s_a(t) - i_a - 1/2)
+ *                        prod_{b != a} S(s_b(t) - i_b) dt,
+ *
+ * s = x/dx in cells, S(s) = max(0, 1 - |s|), Pi the unit box, V the cell
+ * volume.  In 2D the out-of-plane component sits on the nodes:
+ * J_z(i, j) = Q w v_z / (dt V) int_0^dt S(s_x - i) S(s_y - j) dt, with v_z
+ * the step's out-of-plane velocity (Boris: u_z^{n+1/2}/Gamma; guiding
+ * center: the z component of (V^n + V^K)/2, the velocity whose in-plane part
+ * moved it).  With the cloud-in-cell charge density rho_i = sum Q w S(s - i)/V
+ * the deposited J satisfies the discrete continuity equation
+ * (rho^{n+1} - rho^n)/dt + sum_a (J_a(i + e_a/2) - J_a(i - e_a/2))/dx_a = 0
+ * up to rounding, for paths crossing any number of cells.
+ */
+#define GCB_DEPOSIT_MAX_CELLS 64  /* longer paths (cells along an axis in one
+                                     step) are left out and counted */
+
+typedef struct {
+    int32_t dtype;           /* GCB_F32 (mixed path) or GCB_F64 (FP64 path): the
+                                type of J and w, equal to mom_dtype */
+    int32_t reserved;        /* 0 */
+    double q[4];             /* charge of one macro-particle per species */
+    const void *w;           /* optional per-particle weights, n elements of dtype
+                                (NULL: 1); not permuted by sorting, so a call with
+                                w and prm->sort_every > 0 is GCB_EUNSUPPORTED */
+    void *J[3];              /* device arrays of n[0] n[1] n[2] elements of dtype,
+                                node index (k n[1] + j) n[0] + i, aligned to dtype:
+                                J_x at (i+1/2, j, k), J_y at (i, j+1/2, k), J_z at
+                                (i, j, k+1/2) (2D: at node (i, j)), each stored at
+                                its lower node's index, periodic.  The call ADDS
+                                the current of every step (zero them first). */
+} gcb_current;
+
+/*
+ * gcb_push_sr that also deposits every advanced particle-step's current into
+ * cur->J with atomic additions (the order of the additions is not
+ * specified, so J's rounding varies from run to run; FP32 J for the mixed
+ * path).  Frozen (non-finite) particles deposit nothing.  Unfused launches
+ * only: prm->fuse_steps > 1 or prm->drift_frame != GCB_FRAME_SIMPLE is
+ * GCB_EUNSUPPORTED.  n_skipped (host, optional): when non-NULL the call
+ * synchronizes `stream` and stores the number of particle-steps whose path
+ * was longer than GCB_DEPOSIT_MAX_CELLS cells along an axis (left out of J).
+ * Other arguments, checks and errors as gcb_push_sr; GCB_EINVAL for a NULL,
+ * misaligned or unreachable J or w, a dtype other than the particles'
+ * mom_dtype, or a non-finite charge.
+ */
+gcb_status gcb_push_deposit_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                               const gcb_current *cur, int n_steps, void *cuda_stream, void *ws,
+                               size_t ws_bytes, gcb_stats *out, int64_t *n_skipped);
+
+/*
  * ---- Adjoint of the flat-space push (2D, gradient-grid records, no sorting).
  * Gradients of an observable L of the final state with respect to the
  * initial state and to every field-record value.  Not part of the paper: a

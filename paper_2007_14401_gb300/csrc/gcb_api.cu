@@ -234,16 +234,20 @@ gcb_status gcb_pos_join(int64_t n, const float *hi, const float *lo, double *x, 
     return launch_check("gcb_pos_join");
 }
 
-// Copy the device counters to `out` (synchronizing the stream) when non-NULL.
-static gcb_status read_stats(const unsigned long long *stats, cudaStream_t st, gcb_stats *out)
+// Copy the device counters to `out` and the deposition's skip count to
+// `nskip` (synchronizing the stream) when either is non-NULL.
+static gcb_status read_stats(const unsigned long long *stats, cudaStream_t st, gcb_stats *out,
+                             int64_t *nskip = nullptr)
 {
-    if (!out) return GCB_OK;
+    if (!out && !nskip) return GCB_OK;
     unsigned long long h[ST_COUNT];
     if (cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("stats readback: %s", cudaGetErrorString(cudaGetLastError()));
         return GCB_ECUDA;
     }
+    if (nskip) *nskip = (int64_t)h[ST_DEPSKIP];
+    if (!out) return GCB_OK;
     out->n_boris = (int64_t)h[ST_BORIS];
     out->n_gca = (int64_t)h[ST_GCA];
     out->n_to_gca = (int64_t)h[ST_TO_GCA];
@@ -468,12 +472,71 @@ gcb_status gcb_push_ks(const gcb_particles *p, const gcb_grid_ks *gk, const gcb_
     return read_stats(stats, st, out);
 }
 
+// The current of gcb_push_deposit_sr: types, alignment and reachability of
+// its arrays, and the options the deposition supports.
+static gcb_status check_current(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                                const gcb_current *cur)
+{
+    if (!cur) { set_error("current NULL"); return GCB_EINVAL; }
+    if (cur->dtype != p->mom_dtype || cur->reserved != 0) {
+        set_error("current dtype must equal the particles' mom_dtype (reserved 0)");
+        return GCB_EINVAL;
+    }
+    for (int k = 0; k < 4; ++k)
+        if (!isfinite(cur->q[k])) { set_error("non-finite species charge"); return GCB_EINVAL; }
+    const size_t es = cur->dtype == GCB_F64 ? 8 : 4;
+    for (int k = 0; k < 3; ++k) {
+        if (!cur->J[k] || !aligned(cur->J[k], es) || !reachable(cur->J[k])) {
+            set_error("current component %d NULL, misaligned or not device-reachable", k);
+            return GCB_EINVAL;
+        }
+    }
+    if (cur->w && p->n > 0 && (!aligned(cur->w, es) || !reachable(cur->w))) {
+        set_error("weights misaligned or not device-reachable");
+        return GCB_EINVAL;
+    }
+    if (cur->w && prm->sort_every > 0) {
+        set_error("per-particle weights are not permuted by sorting: sort_every must be 0");
+        return GCB_EUNSUPPORTED;
+    }
+    if (prm->fuse_steps > 1 || prm->drift_frame != GCB_FRAME_SIMPLE) {
+        set_error("deposition: unfused steps (fuse_steps <= 1) in the simplified drift frame");
+        return GCB_EUNSUPPORTED;
+    }
+    (void)g;
+    return GCB_OK;
+}
+
+static gcb_status push_sr_impl(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                               const gcb_current *cur, int n_steps, void *cuda_stream, void *ws,
+                               size_t ws_bytes, gcb_stats *out, int64_t *nskip);
+
 gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
                        int n_steps, void *cuda_stream, void *ws, size_t ws_bytes, gcb_stats *out)
+{
+    return push_sr_impl(p, g, prm, nullptr, n_steps, cuda_stream, ws, ws_bytes, out, nullptr);
+}
+
+gcb_status gcb_push_deposit_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                               const gcb_current *cur, int n_steps, void *cuda_stream, void *ws,
+                               size_t ws_bytes, gcb_stats *out, int64_t *n_skipped)
+{
+    g_err[0] = 0;
+    if (!cur) { set_error("current NULL"); return GCB_EINVAL; }
+    return push_sr_impl(p, g, prm, cur, n_steps, cuda_stream, ws, ws_bytes, out, n_skipped);
+}
+
+static gcb_status push_sr_impl(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
+                               const gcb_current *cur, int n_steps, void *cuda_stream, void *ws,
+                               size_t ws_bytes, gcb_stats *out, int64_t *nskip)
 {
     g_err[0] = 0;
     gcb_status s = check_problem(p, g, prm);
     if (s != GCB_OK) return s;
+    if (cur) {
+        s = check_current(p, g, prm, cur);
+        if (s != GCB_OK) return s;
+    }
     if (n_steps < 0) { set_error("n_steps < 0"); return GCB_EINVAL; }
     if (!ws || !aligned(ws, 256)) { set_error("workspace NULL or not 256-byte aligned"); return GCB_EINVAL; }
     if (ws_bytes < kStatsBytes) { set_error("workspace too small"); return GCB_ENOMEM; }
@@ -506,12 +569,16 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
                 k = k < to_sort ? k : to_sort;
             }
         }
-        s = fp64 ? push_step_f64(p, in, g, prm, st, stats, k)
-                 : push_step_f32(p, in, g, prm, st, stats, k);
+        if (cur)
+            s = fp64 ? push_dep_step_f64(p, in, g, prm, cur, st, stats)
+                     : push_dep_step_f32(p, in, g, prm, cur, st, stats);
+        else
+            s = fp64 ? push_step_f64(p, in, g, prm, st, stats, k)
+                     : push_step_f32(p, in, g, prm, st, stats, k);
         if (s != GCB_OK) return s;
         step += k;
     }
-    return read_stats(stats, st, out);
+    return read_stats(stats, st, out, nskip);
 }
 
 }  // extern "C"

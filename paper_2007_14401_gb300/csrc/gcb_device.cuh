@@ -732,7 +732,7 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
                                            const R ln[ND], const R dxp[ND],
                                            const FieldPt<R, ND> &F0, R u[3], R disp[ND],
                                            int &iters, bool &nonconv, StepRecs<Gth, ND, GM> &cr,
-                                           const FieldPt<R, ND> *Fh = nullptr)
+                                           const FieldPt<R, ND> *Fh = nullptr, R *vz = nullptr)
 {
     constexpr bool CACHE = HasCellCache<Gth>::value;
     constexpr bool GR = (GM != 0);
@@ -871,6 +871,9 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
     for (int k = 0; k < 3; ++k) u[k] = fma(upn, f.b[k], fma(f.vE[k] + vc[k], Gp, un * bpg[k]));
 #pragma unroll
     for (int d = 0; d < ND; ++d) disp[d] = dk[d];
+    // out-of-plane component of the step's guiding-center velocity (V^n + V^K)/2
+    // (2D current deposition); the in-plane ones are disp/dt
+    if (vz) *vz = R(0.5) * (Vn[2] + V[2]);
     return true;
 }
 

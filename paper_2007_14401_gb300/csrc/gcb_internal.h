@@ -12,7 +12,9 @@ namespace gcb {
 // Device workspace layout of gcb_push_sr (unsigned long long slots).
 enum {
     ST_BORIS = 0, ST_GCA, ST_TO_GCA, ST_TO_BORIS, ST_NONCONV, ST_GCAFAIL, ST_NONFINITE,
-    ST_SUM_ITER, ST_MAX_ITER, ST_EKIN, ST_COUNT
+    ST_SUM_ITER, ST_MAX_ITER, ST_EKIN,
+    ST_DEPSKIP,   // particle-steps left out of the current (path too long)
+    ST_COUNT
 };
 constexpr size_t kStatsBytes = 256;
 
@@ -28,6 +30,13 @@ gcb_status push_step_f64(const gcb_particles *p, const gcb_particles *in, const 
 gcb_status push_step_f32(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
                          const gcb_params *prm, cudaStream_t st, unsigned long long *stats,
                          int nsteps = 1);
+// One unfused step that also adds the step's current to cur->J (push_dep_*.cu).
+gcb_status push_dep_step_f64(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
+                             const gcb_params *prm, const gcb_current *cur, cudaStream_t st,
+                             unsigned long long *stats);
+gcb_status push_dep_step_f32(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
+                             const gcb_params *prm, const gcb_current *cur, cudaStream_t st,
+                             unsigned long long *stats);
 
 // Adjoint (adjoint_sr.cu): one backward step for all particles whose
 // pre-step state is `s`; lam[7] (x0 x1 u0 u1 u2 dxp0 dxp1) is updated in

@@ -60,11 +60,16 @@ struct Tile {
 #ifndef GCB_HOIST_HALF
 #define GCB_HOIST_HALF 1
 #endif
-template <typename R, int ND>
+// FP32 3D with current deposition: 256 (the deposition's 3D walk spills at 384)
+#ifndef GCB_MIN_THREADS_F32_3D_DEP
+#define GCB_MIN_THREADS_F32_3D_DEP 256
+#endif
+template <typename R, int ND, bool DEP = false>
 struct MinBlocks {
     static constexpr int n = sizeof(R) == 8
         ? 1
-        : (ND == 3 ? GCB_MIN_THREADS_F32_3D : GCB_MIN_THREADS_F32_2D) / Tile<R, ND>::n;
+        : (ND == 3 ? (DEP ? GCB_MIN_THREADS_F32_3D_DEP : GCB_MIN_THREADS_F32_3D)
+                   : GCB_MIN_THREADS_F32_2D) / Tile<R, ND>::n;
 };
 
 template <typename R>
@@ -96,6 +101,12 @@ struct PushArgs {
     int force;
     int nsteps;               // steps of this launch (> 1 only for the fused kernel)
     unsigned long long *stats;
+    // current deposition (kernels with DEP)
+    R *J[3];
+    const R *w;               // per-particle weights or NULL
+    R dq[4];                  // charge per species
+    R jc[3];                  // dx_a / (dt V): J_a per cell of displacement along a
+    R jz;                     // 1 / V: 2D J_z per unit v_z and step fraction
 };
 
 // Particle state is read and written once per step and the field records
@@ -187,13 +198,150 @@ __device__ __forceinline__ double wrap_f64(double x, double L)
 template <typename R>
 __device__ __forceinline__ bool finite_r(R v) { return isfinite(v); }
 
+// ---------------------------------------------------------------------------
+// Current deposition (gcb_push_deposit_sr): the current of a cloud-in-cell
+// particle moving along the straight path x^n -> x^{n+1}, averaged over the
+// step, on the staggered points.  The path is walked cell by cell (the face
+// each axis crosses next, the nearest first).  Inside one cell every hat is
+// linear in time, so a piece's average of one hat is its value at the
+// piece's midpoint, and the average of the product of two hats adds the
+// product of the piece's extents (in cells) along those axes over 12.
+// ---------------------------------------------------------------------------
+template <typename R, int ND>
+__device__ __forceinline__ void dep_piece(const PushArgs<R> &a, const int cell[ND], const R p0[ND],
+                                          const R p1[ND], R tau, R Qw, R vz)
+{
+    const int nx = a.g.n[0], ny = a.g.n[1];
+    int I[2], Jn[2];
+    I[0] = cell[0];
+    I[1] = cell[0] + 1 == nx ? 0 : cell[0] + 1;
+    Jn[0] = cell[1];
+    Jn[1] = cell[1] + 1 == ny ? 0 : cell[1] + 1;
+    R d[ND], m[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+        d[k] = p1[k] - p0[k];
+        m[k] = R(0.5) * (p0[k] + p1[k]);
+    }
+    if constexpr (ND == 2) {
+        const int64_t r0 = (int64_t)Jn[0] * nx, r1 = (int64_t)Jn[1] * nx;
+        if (d[0] != R(0)) {   // J_x at (i+1/2, j) and (i+1/2, j+1)
+            const R f = Qw * a.jc[0] * d[0];
+            atomicAdd(a.J[0] + r0 + I[0], f * (R(1) - m[1]));
+            atomicAdd(a.J[0] + r1 + I[0], f * m[1]);
+        }
+        if (d[1] != R(0)) {   // J_y at (i, j+1/2) and (i+1, j+1/2)
+            const R f = Qw * a.jc[1] * d[1];
+            atomicAdd(a.J[1] + r0 + I[0], f * (R(1) - m[0]));
+            atomicAdd(a.J[1] + r0 + I[1], f * m[0]);
+        }
+        if (vz != R(0) && tau > R(0)) {   // J_z at the cell's four nodes
+            const R f = Qw * a.jz * vz * tau;
+            const R cr = d[0] * d[1] * R(1.0 / 12.0);
+            atomicAdd(a.J[2] + r0 + I[0], f * fma(R(1) - m[0], R(1) - m[1], cr));
+            atomicAdd(a.J[2] + r0 + I[1], f * fma(m[0], R(1) - m[1], -cr));
+            atomicAdd(a.J[2] + r1 + I[0], f * fma(R(1) - m[0], m[1], -cr));
+            atomicAdd(a.J[2] + r1 + I[1], f * fma(m[0], m[1], cr));
+        }
+    } else {
+        const int nz = a.g.n[2];
+        int K[2];
+        K[0] = cell[2];
+        K[1] = cell[2] + 1 == nz ? 0 : cell[2] + 1;
+        auto lin = [&](int i, int j, int k) { return ((int64_t)k * ny + j) * nx + i; };
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (d[c] == R(0)) continue;
+            // the other two axes in cyclic order, b then e
+            const int b = c == 2 ? 0 : c + 1, e = c == 0 ? 2 : c - 1;
+            const R f = Qw * a.jc[c] * d[c];
+            const R cr = d[b] * d[e] * R(1.0 / 12.0);
+#pragma unroll
+            for (int oe = 0; oe < 2; ++oe)
+#pragma unroll
+                for (int ob = 0; ob < 2; ++ob) {
+                    const R wb = ob ? m[b] : R(1) - m[b];
+                    const R we = oe ? m[e] : R(1) - m[e];
+                    const R v = f * fma(wb, we, (ob == oe) ? cr : -cr);
+                    int64_t idx;
+                    if (c == 0) idx = lin(I[0], Jn[ob], K[oe]);
+                    else if (c == 1) idx = lin(I[oe], Jn[0], K[ob]);
+                    else idx = lin(I[ob], Jn[oe], K[0]);
+                    atomicAdd(a.J[c] + idx, v);
+                }
+        }
+    }
+}
+
+// false: the path is longer than GCB_DEPOSIT_MAX_CELLS cells along an axis
+// and nothing is deposited.  ib, l: cell and offset of x^n; disp = x^{n+1} - x^n.
+template <typename R, int ND>
+__device__ __forceinline__ bool deposit_path(const PushArgs<R> &a, const int ib[ND], const R l[ND],
+                                             const R disp[ND], R Qw, R vz)
+{
+    R s0[ND], ds[ND], p0[ND], tn[ND], td[ND];
+    int cell[ND], stp[ND], off[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+        ds[k] = disp[k] * a.g.inv_dx[k];
+        if (!(fabs(ds[k]) <= R(GCB_DEPOSIT_MAX_CELLS))) return false;
+        s0[k] = fmin(fmax(l[k] * a.g.inv_dx[k], R(0)), R(1));
+        p0[k] = s0[k];
+        cell[k] = ib[k];
+        off[k] = 0;
+        if (ds[k] > R(0)) {
+            stp[k] = 1;
+            td[k] = R(1) / ds[k];
+            tn[k] = (R(1) - s0[k]) * td[k];
+        } else if (ds[k] < R(0)) {
+            stp[k] = -1;
+            td[k] = R(-1) / ds[k];
+            tn[k] = s0[k] * td[k];
+        } else {
+            stp[k] = 0;
+            td[k] = R(0);
+            tn[k] = R(2);
+        }
+    }
+    R t = R(0);
+    // every piece but the last ends on a face; each axis crosses at most
+    // GCB_DEPOSIT_MAX_CELLS + 1 faces
+    constexpr int kMaxPieces = ND * (GCB_DEPOSIT_MAX_CELLS + 2) + 1;
+    for (int it = 0; it < kMaxPieces; ++it) {
+        R te = R(1);
+#pragma unroll
+        for (int k = 0; k < ND; ++k) te = fmin(te, tn[k]);
+        R p1[ND];
+#pragma unroll
+        for (int k = 0; k < ND; ++k)
+            p1[k] = fmin(fmax(fma(ds[k], te, s0[k]) - R(off[k]), R(0)), R(1));
+        dep_piece<R, ND>(a, cell, p0, p1, te - t, Qw, vz);
+        if (te >= R(1)) break;
+#pragma unroll
+        for (int k = 0; k < ND; ++k) {
+            if (stp[k] != 0 && tn[k] <= te) {   // enters the next cell along k
+                int c = cell[k] + stp[k];
+                cell[k] = c < 0 ? a.g.n[k] - 1 : (c == a.g.n[k] ? 0 : c);
+                off[k] += stp[k];
+                tn[k] += td[k];
+                p1[k] = stp[k] > 0 ? R(0) : R(1);
+            }
+            p0[k] = p1[k];
+        }
+        t = te;
+    }
+    return true;
+}
+
 // FUSE = false: one step per launch (the PiC mode: state through HBM every
 // step).  FUSE = true: a.nsteps steps per launch, each tile's state kept in
 // its shared-memory slots between the steps and written once at the end (the
 // test-particle mode); every step's arithmetic is the unfused step's.
-template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false>
-__global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND>::n) k_push_sr(const PushArgs<R> a)
+// DEP (unfused only): each advanced particle-step also adds its current to a.J.
+template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false, bool DEP = false>
+__global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND, DEP>::n) k_push_sr(const PushArgs<R> a)
 {
+    static_assert(!(DEP && FUSE), "deposition runs in unfused launches");
     constexpr int TPB = Tile<R, ND>::n;
     constexpr int NWARP = TPB / 32;
     constexpr int NF = (GM != 0) ? 6 + 3 * ND : 6;   // staged field values at x^n
@@ -216,6 +364,7 @@ __global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND>::n) k_push_sr
     if (tid == 0) s_ek = 0.0;
 
     unsigned nb = 0, ng = 0, tg = 0, tb = 0, nc = 0, gf = 0, nf = 0, si = 0, mi = 0;
+    unsigned nds = 0;   // particle-steps left out of the current (DEP)
     double ek = 0.0;
 
     const int64_t ntiles = (a.np + TPB - 1) / TPB;
@@ -428,9 +577,11 @@ __global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND>::n) k_push_sr
             int it = 0;
             bool ncv = false, fail = false;
             bool done = false;
+            R vzg = R(0);   // out-of-plane guiding-center velocity of the step (2D DEP)
             if (isg) {
                 done = gca_step_c<R, ND, GM, Gth, BT>(Gth{a.g}, sp, ib, l, ds, F, us, disp, it,
-                                                      ncv, cr, (HOIST && uni) ? &Fh : nullptr);
+                                                      ncv, cr, (HOIST && uni) ? &Fh : nullptr,
+                                                      (DEP && ND == 2) ? &vzg : nullptr);
                 if (!done) {
                     fail = true;
                     it = 0;
@@ -488,6 +639,16 @@ __global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND>::n) k_push_sr
                     }
 #pragma unroll
                     for (int k = 0; k < 3; ++k) st_state(a.u[k] + gi, us[k]);
+                }
+                if constexpr (DEP) {
+                    // the step's out-of-plane velocity (2D): the guiding
+                    // center's, or u_z^{n+1/2}/Gamma after a Boris step
+                    R vz = R(0);
+                    if constexpr (ND == 2)
+                        vz = done ? vzg : us[2] / sqrt(R(1) + dot3(us, us) * sp.inv_c2);
+                    R Qw = a.dq[(f0 >> GCB_SPECIES_SHIFT) & 3];
+                    if (a.w) Qw *= ld_state(a.w + gi);
+                    if (!deposit_path<R, ND>(a, ib, l, disp, Qw, vz)) ++nds;
                 }
                 if (done) ++ng; else ++nb;
                 if (Sprev && !Snew) ++tg;
@@ -550,6 +711,10 @@ __global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND>::n) k_push_sr
     for (int k = 0; k < 8; ++k) {
         unsigned v = __reduce_add_sync(0xffffffffu, vals[k]);
         if (lane == 0 && v) atomicAdd(&s_acc[k], (unsigned long long)v);
+    }
+    if constexpr (DEP) {
+        const unsigned v = __reduce_add_sync(0xffffffffu, nds);
+        if (lane == 0 && v) atomicAdd(&a.stats[ST_DEPSKIP], (unsigned long long)v);
     }
     unsigned m = __reduce_max_sync(0xffffffffu, vals[8]);
 #pragma unroll
@@ -621,7 +786,7 @@ static void fill_args(PushArgs<R> &a, const gcb_particles *p, const gcb_particle
     a.stats = stats;
 }
 
-template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false>
+template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false, bool DEP = false>
 static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
 {
     static int grid_cache[64] = {0};
@@ -634,7 +799,7 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     if (grid == 0) {
         int nsm = 0, occ = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM, FUSE, BT>,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM, FUSE, BT, DEP>,
                                                           Tile<R, ND>::n, 0) !=
                 cudaSuccess) {
             set_error("occupancy query failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -647,7 +812,7 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     int64_t ntiles = (a.np + TPB - 1) / TPB;
     if (ntiles == 0) return GCB_OK;
     int nb = (int)(ntiles < grid ? ntiles : grid);
-    k_push_sr<R, ND, PM, GM, FUSE, BT><<<nb, TPB, 0, st>>>(a);
+    k_push_sr<R, ND, PM, GM, FUSE, BT, DEP><<<nb, TPB, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));
@@ -656,16 +821,16 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     return GCB_OK;
 }
 
-template <typename R, int PM, bool FUSE, bool BT = false>
+template <typename R, int PM, bool FUSE, bool BT = false, bool DEP = false>
 static gcb_status dispatch_dims(const PushArgs<R> &a, const gcb_grid *g, const gcb_params *prm,
                                 cudaStream_t st)
 {
     const bool grid_grad = prm->grad_mode == GCB_GRAD_GRID;
     if (g->ndim == 2)
-        return grid_grad ? launch_push<R, 2, PM, 2, FUSE, BT>(a, st)
-                         : launch_push<R, 2, PM, 1, FUSE, BT>(a, st);
-    return grid_grad ? launch_push<R, 3, PM, 2, FUSE, BT>(a, st)
-                     : launch_push<R, 3, PM, 1, FUSE, BT>(a, st);
+        return grid_grad ? launch_push<R, 2, PM, 2, FUSE, BT, DEP>(a, st)
+                         : launch_push<R, 2, PM, 1, FUSE, BT, DEP>(a, st);
+    return grid_grad ? launch_push<R, 3, PM, 2, FUSE, BT, DEP>(a, st)
+                     : launch_push<R, 3, PM, 1, FUSE, BT, DEP>(a, st);
 }
 
 // Which (arithmetic, position) pairs carry kernels of the exact drift frame:
@@ -690,6 +855,28 @@ static gcb_status dispatch_push(const gcb_particles *p, const gcb_particles *in,
     if (nsteps <= 1) return dispatch_dims<R, PM, false>(a, g, prm, st);
     a.nsteps = nsteps;
     return dispatch_dims<R, PM, true>(a, g, prm, st);
+}
+
+// One unfused step with current deposition into cur (simplified drift frame;
+// checked by the caller).
+template <typename R, int PM>
+static gcb_status dispatch_push_dep(const gcb_particles *p, const gcb_particles *in,
+                                    const gcb_grid *g, const gcb_params *prm,
+                                    const gcb_current *cur, cudaStream_t st,
+                                    unsigned long long *stats)
+{
+    PushArgs<R> a;
+    fill_args<R>(a, p, in, g, prm, stats);
+    double V = 1.0;
+    for (int d = 0; d < g->ndim; ++d) V *= g->dx[d];
+    for (int k = 0; k < 3; ++k) {
+        a.J[k] = static_cast<R *>(cur->J[k]);
+        a.jc[k] = k < g->ndim ? (R)(g->dx[k] / (prm->dt * V)) : R(0);
+    }
+    a.jz = (R)(1.0 / V);
+    a.w = static_cast<const R *>(cur->w);
+    for (int k = 0; k < 4; ++k) a.dq[k] = (R)cur->q[k];
+    return dispatch_dims<R, PM, false, false, true>(a, g, prm, st);
 }
 
 }  // namespace gcb

@@ -69,11 +69,19 @@ class GcbKsParams(C.Structure):
 KS_TETRAD, KS_GLOBAL = 0, 1   # GREOM half kicks in the local frame / the global basis
 
 
+class GcbCurrent(C.Structure):
+    _fields_ = [("dtype", C.c_int32), ("reserved", C.c_int32), ("q", C.c_double * 4),
+                ("w", C.c_void_p), ("J", C.c_void_p * 3)]
+
+
+DEPOSIT_MAX_CELLS = 64   # GCB_DEPOSIT_MAX_CELLS
+
+
 EXPORTS = ["gcb_version", "gcb_status_string", "gcb_last_error", "gcb_grid_stride",
            "gcb_grid_pack", "gcb_pos_split", "gcb_pos_join", "gcb_workspace_bytes",
            "gcb_sort_sr", "gcb_push_sr", "gcb_push_sr_noalloc", "gcb_adjoint_workspace_bytes",
            "gcb_adjoint_sr", "gcb_push_sr_ckpt", "gcb_grid_combine", "gcb_grad_project", "gcb_ks_cell_size",
-           "gcb_push_ks"]
+           "gcb_push_ks", "gcb_push_deposit_sr"]
 
 
 def load_library(path: str | None = None):
@@ -127,6 +135,10 @@ def load_library(path: str | None = None):
     lib.gcb_push_ks.argtypes = [P(GcbParticles), P(GcbGridKs), P(GcbKsParams), P(GcbParams),
                                 C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, P(GcbStats)]
     lib.gcb_push_ks.restype = C.c_int
+    lib.gcb_push_deposit_sr.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams),
+                                        P(GcbCurrent), C.c_int, C.c_void_p, C.c_void_p,
+                                        C.c_size_t, P(GcbStats), P(C.c_int64)]
+    lib.gcb_push_deposit_sr.restype = C.c_int
     return lib
 
 
@@ -184,6 +196,55 @@ class Grid:
     @property
     def L(self):
         return tuple(self.n[d] * self.dx[d] for d in range(self.ndim))
+
+    @property
+    def shape(self):
+        """Node-array shape, (ny, nx) or (nz, ny, nx)."""
+        return tuple(reversed(self.n[:self.ndim]))
+
+    def update(self, fields: dict, stream=None):
+        """Repack new field values (same grid) into the records in place: the
+        time-dependent fields of a PiC step, read by the next push."""
+        E, B, dB = fields["E"], fields["B"], fields.get("dB")
+        assert np.asarray(E[0]).shape == self.shape and (dB is not None) == bool(self.has_grad)
+        comps = list(E) + list(B) + (list(dB) if dB is not None else [])
+        dev = [torch.as_tensor(c).reshape(-1).to(self.rec.device, torch.float64)
+               for c in comps]
+        ptrs = (C.c_void_p * len(dev))(*[t.data_ptr() for t in dev])
+        _check(_lib.gcb_grid_pack(C.byref(self.s), ptrs, _stream_ptr(stream)), "gcb_grid_pack")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+
+class Current:
+    """Current of gcb_push_deposit_sr on a grid's staggered points: J of shape
+    (3,) + grid.shape in the particles' momentum type (J_x at (i+1/2, j, k),
+    J_y at (i, j+1/2, k), J_z at (i, j, k+1/2), in 2D at the node; each at
+    its lower node's index).  q: charge of one macro-particle per species;
+    w: optional per-particle weights (tensor of n elements).  Pushes add to J;
+    zero() clears it.  n_skipped counts particle-steps left out (paths longer
+    than DEPOSIT_MAX_CELLS cells along an axis)."""
+
+    def __init__(self, grid: Grid, q, precision: str = "mixed", w=None, device="cuda"):
+        tdt = torch.float64 if precision == "fp64" else torch.float32
+        self.dtype = F64 if precision == "fp64" else F32
+        self.J = torch.zeros((3,) + grid.shape, dtype=tdt, device=device)
+        self.q = tuple(float(v) for v in q) + (0.0,) * (4 - len(q))
+        self.w = None if w is None else torch.as_tensor(w).to(device, tdt).contiguous()
+        self.n_skipped = 0
+
+    def zero(self):
+        self.J.zero_()
+        self.n_skipped = 0
+
+    def struct(self) -> GcbCurrent:
+        s = GcbCurrent()
+        s.dtype, s.reserved = self.dtype, 0
+        for k in range(4):
+            s.q[k] = self.q[k]
+        s.w = None if self.w is None else self.w.data_ptr()
+        for a in range(3):
+            s.J[a] = self.J[a].data_ptr()
+        return s
 
 
 # --------------------------------------------------------------------------
@@ -404,15 +465,29 @@ def sort(state: State, grid: Grid, params: GcbParams, stream=None,
 
 
 def push(state: State, grid: Grid, params: GcbParams, n_steps: int = 1, stream=None,
-         workspace: Workspace | None = None, stats: bool = True):
+         workspace: Workspace | None = None, stats: bool = True,
+         current: Current | None = None):
     """Advance ``state`` by n_steps coupled steps in place; returns the stats
-    dict (synchronizing the stream) when ``stats`` is true, else None."""
+    dict (synchronizing the stream) when ``stats`` is true, else None.  With
+    ``current`` every step's current is added to current.J
+    (gcb_push_deposit_sr; its skip count is read when ``stats``)."""
     ws = workspace or Workspace(state, grid, params, _work_device(state))
     out = GcbStats() if stats else None
-    rc = _lib.gcb_push_sr(C.byref(state.s), C.byref(grid.s), C.byref(params), int(n_steps),
-                          _stream_ptr(stream), C.c_void_p(ws.buf.data_ptr()), ws.nbytes,
-                          C.byref(out) if stats else None)
-    _check(rc, "gcb_push_sr")
+    if current is None:
+        rc = _lib.gcb_push_sr(C.byref(state.s), C.byref(grid.s), C.byref(params), int(n_steps),
+                              _stream_ptr(stream), C.c_void_p(ws.buf.data_ptr()), ws.nbytes,
+                              C.byref(out) if stats else None)
+        _check(rc, "gcb_push_sr")
+    else:
+        cs = current.struct()
+        nsk = C.c_int64(0)
+        rc = _lib.gcb_push_deposit_sr(C.byref(state.s), C.byref(grid.s), C.byref(params),
+                                      C.byref(cs), int(n_steps), _stream_ptr(stream),
+                                      C.c_void_p(ws.buf.data_ptr()), ws.nbytes,
+                                      C.byref(out) if stats else None,
+                                      C.byref(nsk) if stats else None)
+        _check(rc, "gcb_push_deposit_sr")
+        current.n_skipped += int(nsk.value)
     if stats:
         return {k: getattr(out, k) for k, _ in GcbStats._fields_}
     return None

@@ -5,8 +5,11 @@ nothing between ranks.  What crosses ranks is bookkeeping: the step time (the
 whole job is as slow as its slowest rank: max), the particle count (sum),
 the push statistics (counters and the kinetic-energy sum: sum; the largest
 fixed-point iteration count: max), and, after an adjoint sweep, the gradients
-with respect to shared inputs such as the field-mode amplitudes (sum).  Each
-function is a no-op reduction when no process group is initialised.
+with respect to shared inputs such as the field-mode amplitudes (sum).  With
+current deposition (the PiC coupling) there is one real exchange per step:
+every rank deposits its own particles' current on its replica of the grid,
+and the field solve needs their sum (reduce_current).  Each function is a
+no-op reduction when no process group is initialised.
 """
 from __future__ import annotations
 
@@ -64,3 +67,13 @@ def reduce_stats(stats: dict, device="cpu") -> dict:
            for k, v in zip(STATS_SUM, s.tolist())}
     out["max_iter"] = int(m.item())
     return {k: out[k] for k in stats}
+
+
+def reduce_current(J: torch.Tensor) -> torch.Tensor:
+    """In-place sum over ranks of each rank's deposited current (one SUM
+    allreduce of the whole grid, 3 x nodes values): afterwards every rank
+    holds the current of all particles, as the field solve of the next PiC
+    step needs.  The identity without a process group."""
+    if _group_size() > 1:
+        dist.all_reduce(J, op=dist.ReduceOp.SUM)
+    return J

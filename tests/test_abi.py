@@ -50,7 +50,9 @@ def test_struct_layout_matches_header(G, tmp_path):
               ("gcb_params", "gyro_phase", G.GcbParams),
               ("gcb_stats", "sum_ekin", G.GcbStats),
               ("gcb_grid_ks", "dl", G.GcbGridKs), ("gcb_ks_params", "r_out", G.GcbKsParams),
-              ("gcb_ks_params", "kick_basis", G.GcbKsParams)]
+              ("gcb_ks_params", "kick_basis", G.GcbKsParams),
+              ("gcb_current", "q", G.GcbCurrent), ("gcb_current", "w", G.GcbCurrent),
+              ("gcb_current", "J", G.GcbCurrent)]
     lines = "".join(f'printf("%zu %zu\\n", sizeof({t}), offsetof({t}, {f}));\n'
                     for t, f, _ in fields)
     src = tmp_path / "layout.c"
@@ -95,6 +97,12 @@ def test_argument_errors_without_gpu(G):
     rc = lib.gcb_push_sr(C.byref(p), C.byref(g), C.byref(prm), 1, None, None, 0, None)
     assert rc == 1 and b"stride" in lib.gcb_last_error()
     assert lib.gcb_pos_split(-1, None, None, None, None) == 1
+    # the deposition refuses a missing current before anything else
+    rc = lib.gcb_push_deposit_sr(C.byref(p), C.byref(g), C.byref(prm), None, 1, None, None, 0,
+                                 None, None)
+    assert rc == 1 and b"current" in lib.gcb_last_error()
+    cap = re.search(r"#define GCB_DEPOSIT_MAX_CELLS (\d+)", open(HEADER).read())
+    assert int(cap.group(1)) == G.DEPOSIT_MAX_CELLS
     # Kerr-Schild: an unknown kick basis is refused before any launch
     gk = G.GcbGrid(2, G.F32, (C.c_int64 * 3)(16, 17, 1), (C.c_double * 3)(0.1, 3.141592653589793 / 16, 1), 0,
                    lib.gcb_grid_stride(2, G.F32, 0), 4096)

@@ -113,3 +113,54 @@ def test_reduce_stats_single_process_is_identity():
     s = {"n_boris": 3, "n_gca": 5, "n_to_gca": 1, "n_to_boris": 0, "n_nonconv": 0,
          "n_gcafail": 0, "n_nonfinite": 0, "sum_iter": 15, "max_iter": 4, "sum_ekin": 0.25}
     assert multi.reduce_stats(s) == s
+
+
+def _current_worker(rank, world, port, out):
+    """Each rank pushes its contiguous shard with the oracle, depositing its
+    particles' current, and sums the current over the ranks."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle as O
+        from paper_2007_14401_gb300 import inputs, multi
+        from tests.helpers import oracle_field, oracle_params
+        fields, st, p = inputs.reconnection_2d(nx=32, ny=16, n_particles=301, seed=6,
+                                               omega_dt_max=50.0)
+        n = st["flags"].size
+        lo, hi = n * rank // world, n * (rank + 1) // world
+        shard = inputs.subset(st, np.arange(lo, hi))
+        cur = O.Current(fields["E"][0].shape, q=(-1.0, 1.0))
+        O.push_sr(shard, oracle_field(fields), oracle_params(p), 2, nthreads=1, current=cur)
+        J = torch.as_tensor(np.stack(cur.J))
+        out[rank] = multi.reduce_current(J).numpy()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_current_reduced_over_rank_shards_equals_one_process(orc):
+    """Two gloo ranks deposit the current of their halves of one particle set
+    (two pushes each); after reduce_current both hold the current one process
+    deposits for the whole set, to rounding."""
+    from paper_2007_14401_gb300 import inputs
+    from tests.helpers import oracle_field, oracle_params
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_current_worker, args=(world, _free_port(), out), nprocs=world,
+                       start_method="spawn")
+    fields, st, p = inputs.reconnection_2d(nx=32, ny=16, n_particles=301, seed=6,
+                                           omega_dt_max=50.0)
+    cur = orc.Current(fields["E"][0].shape, q=(-1.0, 1.0))
+    orc.push_sr(st, oracle_field(fields), oracle_params(p), 2, nthreads=1, current=cur)
+    want = np.stack(cur.J)
+    scale = np.abs(np.stack(cur.Jabs)).max()
+    for r in range(world):
+        assert np.abs(out[r] - want).max() <= 1e-13 * scale
+    assert np.array_equal(out[0], out[1]) and np.abs(want).max() > 0
+
+
+def test_reduce_current_single_process_is_identity():
+    from paper_2007_14401_gb300 import multi
+    J = torch.arange(12.0).reshape(3, 2, 2)
+    assert torch.equal(multi.reduce_current(J.clone()), J)
