@@ -230,6 +230,96 @@ def alu_peaks():
     return out
 
 
+def red_peaks():
+    """Rate of scattered atomic additions of this GPU measured live (G ops/s,
+    FP32 and FP64; libgcb_peak.so, CUDA events)."""
+    import ctypes as C
+
+    import torch
+    from paper_2007_14401_gb300 import build as B
+    lib = C.CDLL(B.build_peak())
+    lib.gcb_peak_red.argtypes = [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double)]
+    lib.gcb_peak_red.restype = C.c_int
+    out = {}
+    for name, dt in (("f32", 0), ("f64", 1)):
+        v = C.c_double(0.0)
+        rc = lib.gcb_peak_red(dt, 2000, C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                              C.byref(v))
+        out[name] = v.value if rc == 0 else None
+    out["how"] = ("8 blocks x 256 threads per SM, 2000 atomic additions a thread, the 32 lanes "
+                  "of an instruction on 32 different sectors of an L2-resident buffer; second "
+                  "of two launches timed with CUDA events")
+    return out
+
+
+def pic_deposit(G, multi, ds, grid, p, sort_every, tile, ws, step, w, args, barrier, stream, n):
+    """The PiC step with current deposition (gcb_push_deposit_sr): each step
+    zeroes J, pushes with deposition and sums J over the ranks
+    (multi.reduce_current); timed in blocks of K steps against the same
+    number of plain pushes with the same sort schedule.  The deposition's
+    cost is the difference; its atomic additions per second over that time
+    are set against the measured scattered-atomic rate."""
+    import torch
+    prec = "fp64" if w["precision"] == "fp64" else "mixed"
+    cur = G.Current(grid, (-1.0, 1.0), precision=prec)
+    gp = G.make_params(p, sort_every=sort_every, sort_tile=tile)
+    K = max(8, args.steps // 2)
+
+    def block(dep):
+        # start on a sort step so that both blocks sort alike
+        k0 = step[0] + (-step[0]) % max(1, sort_every)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(K):
+            gp.step_index = k0 + k
+            if dep:
+                cur.J.zero_()
+                G.push(ds, grid, gp, 1, workspace=ws, stats=False, current=cur)
+                multi.reduce_current(cur.J)
+            else:
+                G.push(ds, grid, gp, 1, workspace=ws, stats=False)
+        e1.record(stream)
+        barrier()
+        step[0] = k0 + K
+        return e0.elapsed_time(e1)
+
+    block(True)   # warm-up of the deposition kernels
+    ms_dep = block(True)
+    ms_push = block(False)
+    value, ms_dep_max, _ = multi.whole_job_rate(n, K, ms_dep, device="cuda")
+    _, ms_push_max, _ = multi.whole_job_rate(n, K, ms_push, device="cuda")
+    # counts of one more step (statistics on)
+    cur.zero()
+    gp.step_index = step[0]
+    G.push(ds, grid, gp, 1, workspace=ws, stats=True, current=cur)
+    step[0] += 1
+    n_sorts = sum(1 for k in range(K) if sort_every > 0 and k % sort_every == 0)
+    dep_ms = (ms_dep_max - ms_push_max) / K
+    try:
+        rp = red_peaks()
+    except (OSError, RuntimeError) as exc:
+        rp = {"error": str(exc)[:200]}
+    f = "f64" if prec == "fp64" else "f32"
+    atom = cur.n_atomics / n
+    out = {"value": value, "unit": METRIC, "steps": K, "ms_per_step": ms_dep_max / K,
+           "ms_per_step_push_only": ms_push_max / K, "deposit_ms_per_step": dep_ms,
+           "vs_push_only": ms_push_max / ms_dep_max,
+           "pieces_per_particle_step": cur.n_pieces / n, "atomics_per_particle_step": atom,
+           "skipped": cur.n_skipped, "j_dtype": f,
+           "gpu_launches": K + 6 * n_sorts,
+           "method": "per step: J zeroed (torch), push with deposition (one kernel), J summed "
+                     "over ranks; same sort schedule as the push-only block it is set against"}
+    if dep_ms > 0 and rp.get(f):
+        ach = atom * n / (dep_ms * 1e-3) / 1e9
+        out["roofline"] = {"bound": "l2_atomics", "achieved": ach, "peak": rp[f],
+                           "unit": "Gop/s", "frac": ach / rp[f],
+                           "note": "atomic additions of one step over the time the deposition "
+                                   "adds to the push; peak: " + rp["how"]}
+    return out
+
+
 def workload_config(w, n_total, ngpu, sort_every, sort_tile):
     cfg = {"workload": w["desc"].format(n=n_total), "particles": n_total,
            "particles_per_gpu": n_total // ngpu, "steps_per_call": 1,
@@ -505,6 +595,8 @@ def main():
                     help="skip the test-particle (fused-step) measurement")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint / forward cost ratio of the default line")
+    ap.add_argument("--no-deposit", action="store_true",
+                    help="skip the PiC step with current deposition")
     ap.add_argument("--e2e-chunks", type=int, default=8,
                     help="particle chunks streamed through the GPU in the end-to-end timing")
     ap.add_argument("--sort-every", type=int, default=None)
@@ -648,6 +740,13 @@ def main():
                "note": "state kept on chip across the fused steps; bound by instruction "
                        "issue (the ALU side), not HBM"}
 
+    # the PiC step: push with current deposition and the current summed over
+    # the ranks (reported beside the graded push)
+    pic = None
+    if not ks and not args.no_deposit:
+        pic = pic_deposit(G, multi, ds, grid, p, sort_every, tile, ws, step, w, args, barrier,
+                          stream, n)
+
     fp64 = None
     if not args.no_fp64 and rank == 0 and w["fp64_b"] is not None:
         n64 = min(n, 1 << 22)
@@ -727,7 +826,7 @@ def main():
                          "ms_push_kernel": avg_launch},
                 "clocks": clocks,
                 "branch_mix": mix,
-                "fp64": fp64, "test_particle_mode": tpm}
+                "fp64": fp64, "test_particle_mode": tpm, "pic_deposit": pic}
         if not args.no_adjoint and args.workload == "reconnection2d":
             line["adjoint_vs_forward"] = adjoint_vs_forward(G)
         if not args.no_cpu_baseline:

@@ -286,22 +286,30 @@ typedef struct {
                                 the current of every step (zero them first). */
 } gcb_current;
 
+typedef struct {
+    int64_t n_skipped;       /* particle-steps whose path was longer than
+                                GCB_DEPOSIT_MAX_CELLS cells along an axis
+                                (left out of J) */
+    int64_t n_pieces;        /* path pieces deposited (one per cell crossed into,
+                                plus one per particle-step) */
+    int64_t n_atomics;       /* atomic additions into J issued (non-zero values) */
+} gcb_deposit_stats;
+
 /*
  * gcb_push_sr that also deposits every advanced particle-step's current into
  * cur->J with atomic additions (the order of the additions is not
  * specified, so J's rounding varies from run to run; FP32 J for the mixed
  * path).  Frozen (non-finite) particles deposit nothing.  Unfused launches
  * only: prm->fuse_steps > 1 or prm->drift_frame != GCB_FRAME_SIMPLE is
- * GCB_EUNSUPPORTED.  n_skipped (host, optional): when non-NULL the call
- * synchronizes `stream` and stores the number of particle-steps whose path
- * was longer than GCB_DEPOSIT_MAX_CELLS cells along an axis (left out of J).
+ * GCB_EUNSUPPORTED.  dst (host, optional): when non-NULL the call
+ * synchronizes `stream` and fills it (counts over all the call's steps).
  * Other arguments, checks and errors as gcb_push_sr; GCB_EINVAL for a NULL,
  * misaligned or unreachable J or w, a dtype other than the particles'
  * mom_dtype, or a non-finite charge.
  */
 gcb_status gcb_push_deposit_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
                                const gcb_current *cur, int n_steps, void *cuda_stream, void *ws,
-                               size_t ws_bytes, gcb_stats *out, int64_t *n_skipped);
+                               size_t ws_bytes, gcb_stats *out, gcb_deposit_stats *dst);
 
 /*
  * ---- Adjoint of the flat-space push (2D, gradient-grid records, no sorting).

@@ -5,7 +5,8 @@
  * has no counterpart.  The pushes are reported against the HBM roofline and,
  * where arithmetic bounds them, against these measured fused multiply-add
  * rates (the Kerr-Schild push against the FP64 rate, the flat pushes'
- * FP32 work against the FP32 rate).
+ * FP32 work against the FP32 rate), and the current deposition against the
+ * measured rate of scattered atomic additions.
  */
 #ifndef GCB_PEAK_H
 #define GCB_PEAK_H
@@ -28,6 +29,17 @@ enum { GCB_PEAK_FP32 = 0, GCB_PEAK_FP32X2 = 1, GCB_PEAK_FP64 = 2 };
  * kind, NULL tflops); 2 for a CUDA error.
  */
 int gcb_peak_fma(int kind, int iters, void *cuda_stream, double *tflops);
+
+/*
+ * Rate of atomic additions without return to scattered addresses, in G
+ * operations/s: dtype 0 FP32, 1 FP64.  8 blocks of 256 threads per SM each
+ * add `iters` times into a 2^23-element buffer (L2-resident), the 32 lanes
+ * of a warp hitting 32 different 32-byte sectors per instruction; the second
+ * of two launches is timed with CUDA events on cuda_stream.  Allocates and
+ * frees the buffer; changes no device setting.
+ * Returns 0 and writes *gops; 1 for invalid arguments; 2 for a CUDA error.
+ */
+int gcb_peak_red(int dtype, int iters, void *cuda_stream, double *gops);
 
 #ifdef __cplusplus
 }

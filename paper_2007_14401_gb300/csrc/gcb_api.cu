@@ -234,19 +234,23 @@ gcb_status gcb_pos_join(int64_t n, const float *hi, const float *lo, double *x, 
     return launch_check("gcb_pos_join");
 }
 
-// Copy the device counters to `out` and the deposition's skip count to
-// `nskip` (synchronizing the stream) when either is non-NULL.
+// Copy the device counters to `out` and the deposition's to `dst`
+// (synchronizing the stream) when either is non-NULL.
 static gcb_status read_stats(const unsigned long long *stats, cudaStream_t st, gcb_stats *out,
-                             int64_t *nskip = nullptr)
+                             gcb_deposit_stats *dst = nullptr)
 {
-    if (!out && !nskip) return GCB_OK;
+    if (!out && !dst) return GCB_OK;
     unsigned long long h[ST_COUNT];
     if (cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("stats readback: %s", cudaGetErrorString(cudaGetLastError()));
         return GCB_ECUDA;
     }
-    if (nskip) *nskip = (int64_t)h[ST_DEPSKIP];
+    if (dst) {
+        dst->n_skipped = (int64_t)h[ST_DEPSKIP];
+        dst->n_pieces = (int64_t)h[ST_DEPPIECE];
+        dst->n_atomics = (int64_t)h[ST_DEPATOM];
+    }
     if (!out) return GCB_OK;
     out->n_boris = (int64_t)h[ST_BORIS];
     out->n_gca = (int64_t)h[ST_GCA];
@@ -509,7 +513,7 @@ static gcb_status check_current(const gcb_particles *p, const gcb_grid *g, const
 
 static gcb_status push_sr_impl(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
                                const gcb_current *cur, int n_steps, void *cuda_stream, void *ws,
-                               size_t ws_bytes, gcb_stats *out, int64_t *nskip);
+                               size_t ws_bytes, gcb_stats *out, gcb_deposit_stats *dst);
 
 gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
                        int n_steps, void *cuda_stream, void *ws, size_t ws_bytes, gcb_stats *out)
@@ -519,16 +523,16 @@ gcb_status gcb_push_sr(const gcb_particles *p, const gcb_grid *g, const gcb_para
 
 gcb_status gcb_push_deposit_sr(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
                                const gcb_current *cur, int n_steps, void *cuda_stream, void *ws,
-                               size_t ws_bytes, gcb_stats *out, int64_t *n_skipped)
+                               size_t ws_bytes, gcb_stats *out, gcb_deposit_stats *dst)
 {
     g_err[0] = 0;
     if (!cur) { set_error("current NULL"); return GCB_EINVAL; }
-    return push_sr_impl(p, g, prm, cur, n_steps, cuda_stream, ws, ws_bytes, out, n_skipped);
+    return push_sr_impl(p, g, prm, cur, n_steps, cuda_stream, ws, ws_bytes, out, dst);
 }
 
 static gcb_status push_sr_impl(const gcb_particles *p, const gcb_grid *g, const gcb_params *prm,
                                const gcb_current *cur, int n_steps, void *cuda_stream, void *ws,
-                               size_t ws_bytes, gcb_stats *out, int64_t *nskip)
+                               size_t ws_bytes, gcb_stats *out, gcb_deposit_stats *dst)
 {
     g_err[0] = 0;
     gcb_status s = check_problem(p, g, prm);
@@ -578,7 +582,7 @@ static gcb_status push_sr_impl(const gcb_particles *p, const gcb_grid *g, const 
         if (s != GCB_OK) return s;
         step += k;
     }
-    return read_stats(stats, st, out, nskip);
+    return read_stats(stats, st, out, dst);
 }
 
 }  // extern "C"

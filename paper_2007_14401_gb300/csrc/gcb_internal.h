@@ -14,6 +14,8 @@ enum {
     ST_BORIS = 0, ST_GCA, ST_TO_GCA, ST_TO_BORIS, ST_NONCONV, ST_GCAFAIL, ST_NONFINITE,
     ST_SUM_ITER, ST_MAX_ITER, ST_EKIN,
     ST_DEPSKIP,   // particle-steps left out of the current (path too long)
+    ST_DEPPIECE,  // path pieces deposited
+    ST_DEPATOM,   // atomic additions into the current
     ST_COUNT
 };
 constexpr size_t kStatsBytes = 256;

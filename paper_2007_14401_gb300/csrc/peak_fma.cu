@@ -1,7 +1,8 @@
 // peak_fma.cu -- measured FP32 and FP64 fused multiply-add throughput of the
 // GPU, the denominators of the ALU-side roofline fractions the benchmark
 // reports (the push kernels are bound by instruction issue rather than by
-// one pipe, and the Kerr-Schild push by FP64 arithmetic).
+// one pipe, and the Kerr-Schild push by FP64 arithmetic), and the rate of
+// scattered atomic additions (the current deposition's bound).
 //
 // Each thread runs NCH independent FMA chains x = x * a + b for `iters`
 // rounds, so the pipe never waits on a dependency; the grid fills every SM
@@ -51,7 +52,56 @@ __global__ void __launch_bounds__(TPB) k_fma2(int iters, float a, float b, float
     if (s == -12345.0f) sink[threadIdx.x] = s;
 }
 
+// atomic additions without return (RED) to scattered addresses: lane l of a
+// warp adds to element 8 (w 32 + l) + 8 i P (mod n), so that the 32 lanes of
+// one instruction hit 32 different 32-byte sectors and successive rounds
+// walk the buffer (P a prime; n a power of two)
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_red(int iters, T *buf, unsigned mask)
+{
+    const unsigned g = blockIdx.x * TPB + threadIdx.x;
+    for (int i = 0; i < iters; ++i) {
+        const unsigned idx = (8u * g + 8u * 1048573u * (unsigned)i) & mask;
+        atomicAdd(buf + idx, T(1));
+    }
+}
+
 }  // namespace
+
+extern "C" int gcb_peak_red(int dtype, int iters, void *cuda_stream, double *gops)
+{
+    if (!gops || iters < 1 || (dtype != 0 && dtype != 1)) return 1;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 2;
+    const int blocks = nsm * 8;
+    const size_t n = (size_t)1 << 23;           // elements (32 or 64 MB: in L2)
+    const size_t es = dtype == 1 ? 8 : 4;
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, n * es) != cudaSuccess) return 2;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float ms = 0.f;
+    int rc = cudaMemsetAsync(buf, 0, n * es, st) == cudaSuccess ? 0 : 2;
+    for (int rep = 0; rep < 2 && !rc; ++rep) {   // the first launch is untimed
+        cudaEventRecord(e0, st);
+        if (dtype == 1) k_red<double><<<blocks, TPB, 0, st>>>(iters, (double *)buf, (unsigned)(n - 1));
+        else k_red<float><<<blocks, TPB, 0, st>>>(iters, (float *)buf, (unsigned)(n - 1));
+        cudaEventRecord(e1, st);
+    }
+    if (rc || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        rc = 2;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (rc) return rc;
+    *gops = (double)iters * (double)blocks * TPB / (ms * 1e-3) / 1e9;
+    return 0;
+}
 
 extern "C" int gcb_peak_fma(int kind, int iters, void *cuda_stream, double *tflops)
 {

@@ -60,15 +60,17 @@ struct Tile {
 #ifndef GCB_HOIST_HALF
 #define GCB_HOIST_HALF 1
 #endif
-// FP32 3D with current deposition: 256 (the deposition's 3D walk spills at 384)
-#ifndef GCB_MIN_THREADS_F32_3D_DEP
-#define GCB_MIN_THREADS_F32_3D_DEP 256
+// FP32 3D with current deposition and gradient records: 256 (the 3D walk
+// spills 684 B at 384); with gradients from W, 384 as without deposition
+// (measured 14% faster than 256 on the 3D sheet)
+#ifndef GCB_MIN_THREADS_F32_3D_DEP_GRID
+#define GCB_MIN_THREADS_F32_3D_DEP_GRID 256
 #endif
-template <typename R, int ND, bool DEP = false>
+template <typename R, int ND, int GM = 1, bool DEP = false>
 struct MinBlocks {
     static constexpr int n = sizeof(R) == 8
         ? 1
-        : (ND == 3 ? (DEP ? GCB_MIN_THREADS_F32_3D_DEP : GCB_MIN_THREADS_F32_3D)
+        : (ND == 3 ? ((DEP && GM == 2) ? GCB_MIN_THREADS_F32_3D_DEP_GRID : GCB_MIN_THREADS_F32_3D)
                    : GCB_MIN_THREADS_F32_2D) / Tile<R, ND>::n;
 };
 
@@ -207,10 +209,12 @@ __device__ __forceinline__ bool finite_r(R v) { return isfinite(v); }
 // piece's midpoint, and the average of the product of two hats adds the
 // product of the piece's extents (in cells) along those axes over 12.
 // ---------------------------------------------------------------------------
+// returns the number of atomic additions issued
 template <typename R, int ND>
-__device__ __forceinline__ void dep_piece(const PushArgs<R> &a, const int cell[ND], const R p0[ND],
-                                          const R p1[ND], R tau, R Qw, R vz)
+__device__ __forceinline__ int dep_piece(const PushArgs<R> &a, const int cell[ND], const R p0[ND],
+                                         const R p1[ND], R tau, R Qw, R vz)
 {
+    int nat = 0;
     const int nx = a.g.n[0], ny = a.g.n[1];
     int I[2], Jn[2];
     I[0] = cell[0];
@@ -229,11 +233,13 @@ __device__ __forceinline__ void dep_piece(const PushArgs<R> &a, const int cell[N
             const R f = Qw * a.jc[0] * d[0];
             atomicAdd(a.J[0] + r0 + I[0], f * (R(1) - m[1]));
             atomicAdd(a.J[0] + r1 + I[0], f * m[1]);
+            nat += 2;
         }
         if (d[1] != R(0)) {   // J_y at (i, j+1/2) and (i+1, j+1/2)
             const R f = Qw * a.jc[1] * d[1];
             atomicAdd(a.J[1] + r0 + I[0], f * (R(1) - m[0]));
             atomicAdd(a.J[1] + r0 + I[1], f * m[0]);
+            nat += 2;
         }
         if (vz != R(0) && tau > R(0)) {   // J_z at the cell's four nodes
             const R f = Qw * a.jz * vz * tau;
@@ -242,6 +248,7 @@ __device__ __forceinline__ void dep_piece(const PushArgs<R> &a, const int cell[N
             atomicAdd(a.J[2] + r0 + I[1], f * fma(m[0], R(1) - m[1], -cr));
             atomicAdd(a.J[2] + r1 + I[0], f * fma(R(1) - m[0], m[1], -cr));
             atomicAdd(a.J[2] + r1 + I[1], f * fma(m[0], m[1], cr));
+            nat += 4;
         }
     } else {
         const int nz = a.g.n[2];
@@ -269,15 +276,18 @@ __device__ __forceinline__ void dep_piece(const PushArgs<R> &a, const int cell[N
                     else idx = lin(I[ob], Jn[oe], K[0]);
                     atomicAdd(a.J[c] + idx, v);
                 }
+            nat += 4;
         }
     }
+    return nat;
 }
 
 // false: the path is longer than GCB_DEPOSIT_MAX_CELLS cells along an axis
 // and nothing is deposited.  ib, l: cell and offset of x^n; disp = x^{n+1} - x^n.
 template <typename R, int ND>
 __device__ __forceinline__ bool deposit_path(const PushArgs<R> &a, const int ib[ND], const R l[ND],
-                                             const R disp[ND], R Qw, R vz)
+                                             const R disp[ND], R Qw, R vz, unsigned &npc,
+                                             unsigned &nat)
 {
     R s0[ND], ds[ND], p0[ND], tn[ND], td[ND];
     int cell[ND], stp[ND], off[ND];
@@ -315,7 +325,8 @@ __device__ __forceinline__ bool deposit_path(const PushArgs<R> &a, const int ib[
 #pragma unroll
         for (int k = 0; k < ND; ++k)
             p1[k] = fmin(fmax(fma(ds[k], te, s0[k]) - R(off[k]), R(0)), R(1));
-        dep_piece<R, ND>(a, cell, p0, p1, te - t, Qw, vz);
+        nat += dep_piece<R, ND>(a, cell, p0, p1, te - t, Qw, vz);
+        ++npc;
         if (te >= R(1)) break;
 #pragma unroll
         for (int k = 0; k < ND; ++k) {
@@ -339,7 +350,7 @@ __device__ __forceinline__ bool deposit_path(const PushArgs<R> &a, const int ib[
 // test-particle mode); every step's arithmetic is the unfused step's.
 // DEP (unfused only): each advanced particle-step also adds its current to a.J.
 template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false, bool DEP = false>
-__global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND, DEP>::n) k_push_sr(const PushArgs<R> a)
+__global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND, GM, DEP>::n) k_push_sr(const PushArgs<R> a)
 {
     static_assert(!(DEP && FUSE), "deposition runs in unfused launches");
     constexpr int TPB = Tile<R, ND>::n;
@@ -364,7 +375,7 @@ __global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND, DEP>::n) k_pu
     if (tid == 0) s_ek = 0.0;
 
     unsigned nb = 0, ng = 0, tg = 0, tb = 0, nc = 0, gf = 0, nf = 0, si = 0, mi = 0;
-    unsigned nds = 0;   // particle-steps left out of the current (DEP)
+    unsigned nds = 0, npc = 0, nat = 0;   // DEP: skipped paths, pieces, atomics
     double ek = 0.0;
 
     const int64_t ntiles = (a.np + TPB - 1) / TPB;
@@ -648,7 +659,7 @@ __global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND, DEP>::n) k_pu
                         vz = done ? vzg : us[2] / sqrt(R(1) + dot3(us, us) * sp.inv_c2);
                     R Qw = a.dq[(f0 >> GCB_SPECIES_SHIFT) & 3];
                     if (a.w) Qw *= ld_state(a.w + gi);
-                    if (!deposit_path<R, ND>(a, ib, l, disp, Qw, vz)) ++nds;
+                    if (!deposit_path<R, ND>(a, ib, l, disp, Qw, vz, npc, nat)) ++nds;
                 }
                 if (done) ++ng; else ++nb;
                 if (Sprev && !Snew) ++tg;
@@ -713,8 +724,12 @@ __global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND, DEP>::n) k_pu
         if (lane == 0 && v) atomicAdd(&s_acc[k], (unsigned long long)v);
     }
     if constexpr (DEP) {
-        const unsigned v = __reduce_add_sync(0xffffffffu, nds);
-        if (lane == 0 && v) atomicAdd(&a.stats[ST_DEPSKIP], (unsigned long long)v);
+        const unsigned dv[3] = {nds, npc, nat};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const unsigned v = __reduce_add_sync(0xffffffffu, dv[k]);
+            if (lane == 0 && v) atomicAdd(&a.stats[ST_DEPSKIP + k], (unsigned long long)v);
+        }
     }
     unsigned m = __reduce_max_sync(0xffffffffu, vals[8]);
 #pragma unroll

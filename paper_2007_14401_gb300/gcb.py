@@ -74,6 +74,10 @@ class GcbCurrent(C.Structure):
                 ("w", C.c_void_p), ("J", C.c_void_p * 3)]
 
 
+class GcbDepositStats(C.Structure):
+    _fields_ = [("n_skipped", C.c_int64), ("n_pieces", C.c_int64), ("n_atomics", C.c_int64)]
+
+
 DEPOSIT_MAX_CELLS = 64   # GCB_DEPOSIT_MAX_CELLS
 
 
@@ -137,7 +141,7 @@ def load_library(path: str | None = None):
     lib.gcb_push_ks.restype = C.c_int
     lib.gcb_push_deposit_sr.argtypes = [P(GcbParticles), P(GcbGrid), P(GcbParams),
                                         P(GcbCurrent), C.c_int, C.c_void_p, C.c_void_p,
-                                        C.c_size_t, P(GcbStats), P(C.c_int64)]
+                                        C.c_size_t, P(GcbStats), P(GcbDepositStats)]
     lib.gcb_push_deposit_sr.restype = C.c_int
     return lib
 
@@ -221,8 +225,10 @@ class Current:
     J_y at (i, j+1/2, k), J_z at (i, j, k+1/2), in 2D at the node; each at
     its lower node's index).  q: charge of one macro-particle per species;
     w: optional per-particle weights (tensor of n elements).  Pushes add to J;
-    zero() clears it.  n_skipped counts particle-steps left out (paths longer
-    than DEPOSIT_MAX_CELLS cells along an axis)."""
+    zero() clears it.  Counts summed over the pushes that read them (stats
+    on): n_skipped particle-steps left out (paths longer than
+    DEPOSIT_MAX_CELLS cells along an axis), n_pieces path pieces deposited,
+    n_atomics atomic additions into J."""
 
     def __init__(self, grid: Grid, q, precision: str = "mixed", w=None, device="cuda"):
         tdt = torch.float64 if precision == "fp64" else torch.float32
@@ -230,11 +236,11 @@ class Current:
         self.J = torch.zeros((3,) + grid.shape, dtype=tdt, device=device)
         self.q = tuple(float(v) for v in q) + (0.0,) * (4 - len(q))
         self.w = None if w is None else torch.as_tensor(w).to(device, tdt).contiguous()
-        self.n_skipped = 0
+        self.n_skipped = self.n_pieces = self.n_atomics = 0
 
     def zero(self):
         self.J.zero_()
-        self.n_skipped = 0
+        self.n_skipped = self.n_pieces = self.n_atomics = 0
 
     def struct(self) -> GcbCurrent:
         s = GcbCurrent()
@@ -480,14 +486,16 @@ def push(state: State, grid: Grid, params: GcbParams, n_steps: int = 1, stream=N
         _check(rc, "gcb_push_sr")
     else:
         cs = current.struct()
-        nsk = C.c_int64(0)
+        dst = GcbDepositStats()
         rc = _lib.gcb_push_deposit_sr(C.byref(state.s), C.byref(grid.s), C.byref(params),
                                       C.byref(cs), int(n_steps), _stream_ptr(stream),
                                       C.c_void_p(ws.buf.data_ptr()), ws.nbytes,
                                       C.byref(out) if stats else None,
-                                      C.byref(nsk) if stats else None)
+                                      C.byref(dst) if stats else None)
         _check(rc, "gcb_push_deposit_sr")
-        current.n_skipped += int(nsk.value)
+        current.n_skipped += int(dst.n_skipped)
+        current.n_pieces += int(dst.n_pieces)
+        current.n_atomics += int(dst.n_atomics)
     if stats:
         return {k: getattr(out, k) for k, _ in GcbStats._fields_}
     return None

@@ -52,7 +52,8 @@ def test_struct_layout_matches_header(G, tmp_path):
               ("gcb_grid_ks", "dl", G.GcbGridKs), ("gcb_ks_params", "r_out", G.GcbKsParams),
               ("gcb_ks_params", "kick_basis", G.GcbKsParams),
               ("gcb_current", "q", G.GcbCurrent), ("gcb_current", "w", G.GcbCurrent),
-              ("gcb_current", "J", G.GcbCurrent)]
+              ("gcb_current", "J", G.GcbCurrent),
+              ("gcb_deposit_stats", "n_atomics", G.GcbDepositStats)]
     lines = "".join(f'printf("%zu %zu\\n", sizeof({t}), offsetof({t}, {f}));\n'
                     for t, f, _ in fields)
     src = tmp_path / "layout.c"
@@ -128,15 +129,15 @@ def test_binding_fails_loudly_without_the_library():
 
 
 def test_peak_library_exports_its_declared_symbol():
-    """include/gcb_peak.h's entry point is exported by libgcb_peak.so (the
-    benchmark's FMA-rate measurement), and answers invalid arguments without a
-    GPU."""
+    """include/gcb_peak.h's entry points are exported by libgcb_peak.so (the
+    benchmark's FMA-rate and atomic-rate measurements), and answer invalid
+    arguments without a GPU."""
     from paper_2007_14401_gb300 import build
     path = build.build_peak()
     txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "gcb_peak.h")).read(),
                  flags=re.S)
     names = sorted(set(re.findall(r"\b(gcb_[a-z0-9_]+)\s*\(", txt)))
-    assert names == ["gcb_peak_fma"]
+    assert names == ["gcb_peak_fma", "gcb_peak_red"]
     out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True,
                          text=True).stdout
     assert set(names) <= set(re.findall(r" T (gcb_\w+)", out))
@@ -146,3 +147,7 @@ def test_peak_library_exports_its_declared_symbol():
     assert lib.gcb_peak_fma(7, 10, None, C.byref(v)) == 1
     assert lib.gcb_peak_fma(0, 0, None, C.byref(v)) == 1
     assert lib.gcb_peak_fma(0, 10, None, None) == 1
+    lib.gcb_peak_red.argtypes = [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double)]
+    assert lib.gcb_peak_red(2, 10, None, C.byref(v)) == 1
+    assert lib.gcb_peak_red(0, 0, None, C.byref(v)) == 1
+    assert lib.gcb_peak_red(1, 10, None, None) == 1

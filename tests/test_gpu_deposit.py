@@ -102,6 +102,15 @@ def test_one_step_current_matches_oracle(G, precision, pos_mode, workload):
     cur, ocur, ds, ref = deposit_both(G, fields, sub, p, precision, pos_mode, q=(-1.0, 1.0))
     assert_current_parity(cur, ocur, precision)
     assert np.abs(ocur.J[0]).max() > 0 and np.abs(ocur.J[2]).max() > 0
+    # one piece per particle-step plus one per cell face crossed (from the
+    # positions before and the displacement of the step)
+    dx = np.asarray(fields["dx"])[:, None]
+    s0 = sub["x"] / dx
+    s1 = s0 + ref["dxp"] / dx
+    want = sub["flags"].size + int(np.abs(np.floor(s1) - np.floor(s0)).sum())
+    assert abs(cur.n_pieces - want) <= (0 if precision == "fp64" else 1e-3 * want)
+    slots = 8 if len(fields["dx"]) == 2 else 12
+    assert cur.n_pieces <= cur.n_atomics <= slots * cur.n_pieces
 
 
 @pytest.mark.parametrize("force", [1, 2])
