@@ -31,15 +31,15 @@ enum { GCB_PEAK_FP32 = 0, GCB_PEAK_FP32X2 = 1, GCB_PEAK_FP64 = 2 };
 int gcb_peak_fma(int kind, int iters, void *cuda_stream, double *tflops);
 
 /*
- * Rate of atomic additions without return to scattered addresses, in G
- * operations/s: dtype 0 FP32, 1 FP64.  8 blocks of 256 threads per SM each
- * add `iters` times into a 2^23-element buffer (L2-resident), the 32 lanes
- * of a warp hitting 32 different 32-byte sectors per instruction; the second
- * of two launches is timed with CUDA events on cuda_stream.  Allocates and
- * frees the buffer; changes no device setting.
+ * Rate of atomic additions without return, in G operations/s: dtype 0 FP32,
+ * 1 FP64; pattern 0 coalesced (the 32 lanes of a warp add to 32 consecutive
+ * elements), 1 scattered (to 32 different 32-byte sectors).  8 blocks of 256
+ * threads per SM each add `iters` times into a 2^23-element buffer
+ * (L2-resident); the second of two launches is timed with CUDA events on
+ * cuda_stream.  Allocates and frees the buffer; changes no device setting.
  * Returns 0 and writes *gops; 1 for invalid arguments; 2 for a CUDA error.
  */
-int gcb_peak_red(int dtype, int iters, void *cuda_stream, double *gops);
+int gcb_peak_red(int dtype, int pattern, int iters, void *cuda_stream, double *gops);
 
 #ifdef __cplusplus
 }

@@ -52,25 +52,28 @@ __global__ void __launch_bounds__(TPB) k_fma2(int iters, float a, float b, float
     if (s == -12345.0f) sink[threadIdx.x] = s;
 }
 
-// atomic additions without return (RED) to scattered addresses: lane l of a
-// warp adds to element 8 (w 32 + l) + 8 i P (mod n), so that the 32 lanes of
-// one instruction hit 32 different 32-byte sectors and successive rounds
-// walk the buffer (P a prime; n a power of two)
+// atomic additions without return (RED).  stride 1 (coalesced): the lanes
+// of a warp add to 32 consecutive elements; stride 8 (scattered): to 32
+// different 32-byte sectors.  Thread g adds in round i to element
+// stride g + stride 1048573 i (mod n): successive rounds walk the buffer
+// (1048573 a prime; n a power of two).
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_red(int iters, T *buf, unsigned mask)
+__global__ void __launch_bounds__(TPB) k_red(int iters, T *buf, unsigned mask, unsigned stride)
 {
     const unsigned g = blockIdx.x * TPB + threadIdx.x;
     for (int i = 0; i < iters; ++i) {
-        const unsigned idx = (8u * g + 8u * 1048573u * (unsigned)i) & mask;
+        const unsigned idx = (stride * g + stride * 1048573u * (unsigned)i) & mask;
         atomicAdd(buf + idx, T(1));
     }
 }
 
 }  // namespace
 
-extern "C" int gcb_peak_red(int dtype, int iters, void *cuda_stream, double *gops)
+extern "C" int gcb_peak_red(int dtype, int pattern, int iters, void *cuda_stream, double *gops)
 {
-    if (!gops || iters < 1 || (dtype != 0 && dtype != 1)) return 1;
+    if (!gops || iters < 1 || (dtype != 0 && dtype != 1) || (pattern != 0 && pattern != 1))
+        return 1;
+    const unsigned stride = pattern == 0 ? 1u : 8u;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -88,8 +91,10 @@ extern "C" int gcb_peak_red(int dtype, int iters, void *cuda_stream, double *gop
     int rc = cudaMemsetAsync(buf, 0, n * es, st) == cudaSuccess ? 0 : 2;
     for (int rep = 0; rep < 2 && !rc; ++rep) {   // the first launch is untimed
         cudaEventRecord(e0, st);
-        if (dtype == 1) k_red<double><<<blocks, TPB, 0, st>>>(iters, (double *)buf, (unsigned)(n - 1));
-        else k_red<float><<<blocks, TPB, 0, st>>>(iters, (float *)buf, (unsigned)(n - 1));
+        if (dtype == 1)
+            k_red<double><<<blocks, TPB, 0, st>>>(iters, (double *)buf, (unsigned)(n - 1), stride);
+        else
+            k_red<float><<<blocks, TPB, 0, st>>>(iters, (float *)buf, (unsigned)(n - 1), stride);
         cudaEventRecord(e1, st);
     }
     if (rc || cudaEventSynchronize(e1) != cudaSuccess ||

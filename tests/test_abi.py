@@ -147,7 +147,8 @@ def test_peak_library_exports_its_declared_symbol():
     assert lib.gcb_peak_fma(7, 10, None, C.byref(v)) == 1
     assert lib.gcb_peak_fma(0, 0, None, C.byref(v)) == 1
     assert lib.gcb_peak_fma(0, 10, None, None) == 1
-    lib.gcb_peak_red.argtypes = [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double)]
-    assert lib.gcb_peak_red(2, 10, None, C.byref(v)) == 1
-    assert lib.gcb_peak_red(0, 0, None, C.byref(v)) == 1
-    assert lib.gcb_peak_red(1, 10, None, None) == 1
+    lib.gcb_peak_red.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double)]
+    assert lib.gcb_peak_red(2, 0, 10, None, C.byref(v)) == 1
+    assert lib.gcb_peak_red(0, 2, 10, None, C.byref(v)) == 1
+    assert lib.gcb_peak_red(0, 0, 0, None, C.byref(v)) == 1
+    assert lib.gcb_peak_red(1, 1, 10, None, None) == 1
