@@ -300,9 +300,10 @@ typedef struct {
  * cur->J with atomic additions (the order of the additions is not
  * specified, so J's rounding varies from run to run; FP32 J for the mixed
  * path).  Frozen (non-finite) particles deposit nothing.  Unfused launches
- * only: prm->fuse_steps > 1 or prm->drift_frame != GCB_FRAME_SIMPLE is
- * GCB_EUNSUPPORTED.  dst (host, optional): when non-NULL the call
- * synchronizes `stream` and fills it (counts over all the call's steps).
+ * only: prm->fuse_steps > 1, prm->drift_frame != GCB_FRAME_SIMPLE or a grid
+ * of 2^31 nodes or more is GCB_EUNSUPPORTED.  dst (host, optional): when
+ * non-NULL the call synchronizes `stream` and fills it (counts over all the
+ * call's steps).
  * Other arguments, checks and errors as gcb_push_sr; GCB_EINVAL for a NULL,
  * misaligned or unreachable J or w, a dtype other than the particles'
  * mom_dtype, or a non-finite charge.

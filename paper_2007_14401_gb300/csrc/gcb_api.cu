@@ -507,7 +507,10 @@ static gcb_status check_current(const gcb_particles *p, const gcb_grid *g, const
         set_error("deposition: unfused steps (fuse_steps <= 1) in the simplified drift frame");
         return GCB_EUNSUPPORTED;
     }
-    (void)g;
+    if (g->n[0] * g->n[1] * g->n[2] >= ((int64_t)1 << 31)) {
+        set_error("deposition: the grid must have fewer than 2^31 nodes");
+        return GCB_EUNSUPPORTED;
+    }
     return GCB_OK;
 }
 

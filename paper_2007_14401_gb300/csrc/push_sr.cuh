@@ -228,7 +228,8 @@ __device__ __forceinline__ int dep_piece(const PushArgs<R> &a, const int cell[ND
         m[k] = R(0.5) * (p0[k] + p1[k]);
     }
     if constexpr (ND == 2) {
-        const int64_t r0 = (int64_t)Jn[0] * nx, r1 = (int64_t)Jn[1] * nx;
+        // 32-bit indices (the deposition is limited to grids of < 2^31 nodes)
+        const int r0 = Jn[0] * nx, r1 = Jn[1] * nx;
         if (d[0] != R(0)) {   // J_x at (i+1/2, j) and (i+1/2, j+1)
             const R f = Qw * a.jc[0] * d[0];
             atomicAdd(a.J[0] + r0 + I[0], f * (R(1) - m[1]));
@@ -255,7 +256,7 @@ __device__ __forceinline__ int dep_piece(const PushArgs<R> &a, const int cell[ND
         int K[2];
         K[0] = cell[2];
         K[1] = cell[2] + 1 == nz ? 0 : cell[2] + 1;
-        auto lin = [&](int i, int j, int k) { return ((int64_t)k * ny + j) * nx + i; };
+        auto lin = [&](int i, int j, int k) { return (k * ny + j) * nx + i; };
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (d[c] == R(0)) continue;
@@ -270,7 +271,7 @@ __device__ __forceinline__ int dep_piece(const PushArgs<R> &a, const int cell[ND
                     const R wb = ob ? m[b] : R(1) - m[b];
                     const R we = oe ? m[e] : R(1) - m[e];
                     const R v = f * fma(wb, we, (ob == oe) ? cr : -cr);
-                    int64_t idx;
+                    int idx;
                     if (c == 0) idx = lin(I[0], Jn[ob], K[oe]);
                     else if (c == 1) idx = lin(I[oe], Jn[0], K[ob]);
                     else idx = lin(I[ob], Jn[oe], K[0]);
