@@ -189,48 +189,71 @@ def test_long_paths_nonfinite_and_empty(G):
     assert bool((c0.J == 2.5).all()) and c0.n_skipped == 0
 
 
-def test_full_size_continuity_and_total(G):
-    """The benchmark's 2D workload (2^24 particles, 2048 x 1024 nodes), mixed
-    path, one step with deposition: (rho^{n+1} - rho^n)/dt + div J = 0 with
-    the cloud-in-cell charge of the positions before and after (FP64 on the
-    device), and sum J_a V = sum q w dxp_a/dt over the particles."""
+@pytest.mark.parametrize("workload", ["recon2d", "sheet3d"])
+def test_full_size_continuity_and_total(G, workload):
+    """The benchmark's workloads at full size (2D: 2^24 particles, 2048 x 1024
+    nodes; 3D: 2^26 particles, 256^3 nodes), mixed path, one step with
+    deposition in the benchmark's sorted order: (rho^{n+1} - rho^n)/dt +
+    div J = 0 with the cloud-in-cell charge of the positions before and after
+    (FP64 on the device), and sum J_a V = sum q w dxp_a/dt over the
+    particles."""
     import torch
-    fields, st, p = inputs.reconnection_2d(seed=1)
+    if workload == "recon2d":
+        fields, st, p = inputs.reconnection_2d(seed=1)
+        tile = (1, 1)
+    else:
+        fields, st, p = inputs.current_sheet_3d(seed=2)
+        tile = (1, 1, 1)
     grid = G.Grid(fields, dtype="f32")
+    nd = grid.ndim
     ds = G.State.from_numpy(st, precision="mixed", pos_mode="pair")
+    G.sort(ds, grid, G.make_params(p, sort_every=1, sort_tile=tile))
     x0 = torch.as_tensor(ds.to_numpy()["x"]).cuda()
+    sp = ds.flags.to(torch.int64) >> 6
+    q = torch.where(sp == 0, -1.0, 1.0).double()
     cur = G.Current(grid, (-1.0, 1.0), precision="mixed")
     s = G.push(ds, grid, G.make_params(p), 1, current=cur)
     x1 = torch.as_tensor(ds.to_numpy()["x"]).cuda()
-    sp = torch.as_tensor(st["flags"].astype(np.int64) >> 6).cuda()
-    q = torch.where(sp == 0, -1.0, 1.0).double()
-    nx, ny = grid.n[0], grid.n[1]
+    n = grid.n[:nd]
     dt = p["dt"]
-    r0, r1 = cic_rho_torch(x0, q, nx, ny), cic_rho_torch(x1, q, nx, ny)
+    r0, r1 = cic_rho_torch(x0, q, n), cic_rho_torch(x1, q, n)
+    del x0, x1
     J = cur.J.double()
-    div = (J[0] - torch.roll(J[0], 1, dims=1)) + (J[1] - torch.roll(J[1], 1, dims=0))
+    div = torch.zeros_like(r0)
+    for a in range(nd):
+        div += J[a] - torch.roll(J[a], 1, dims=nd - 1 - a)
     res = (r1 - r0) / dt + div
-    scale = max(float(J[:2].abs().max()), float(r0.abs().max()) / dt)
+    scale = max(float(J[:nd].abs().max()), float(r0.abs().max()) / dt)
     assert float(res.abs().max()) < 1e-4 * scale, (float(res.abs().max()), scale)
     dxp = ds.dxp.double()
-    for a in range(2):
+    for a in range(nd):
         tot = float((q * dxp[a]).sum()) / dt
         tot_abs = float((q * dxp[a]).abs().sum()) / dt
         assert abs(float(J[a].sum()) - tot) <= 1e-5 * tot_abs
     assert s["n_nonfinite"] == 0 and cur.n_skipped == 0
 
 
-def cic_rho_torch(x, q, nx, ny):
+def cic_rho_torch(x, q, n):
+    """Cloud-in-cell charge at the nodes (unit cells, periodic), FP64."""
     import torch
-    i0 = torch.floor(x[0]).long()
-    j0 = torch.floor(x[1]).long()
-    fx, fy = x[0] - i0, x[1] - j0
-    rho = torch.zeros(ny * nx, dtype=torch.float64, device=x.device)
-    for oi, wx in ((0, 1 - fx), (1, fx)):
-        for oj, wy in ((0, 1 - fy), (1, fy)):
-            idx = ((j0 + oj) % ny) * nx + (i0 + oi) % nx
-            rho.index_add_(0, idx, q * wx * wy)
-    return rho.view(ny, nx)
+    nd = len(n)
+    base = [torch.floor(x[a]).long() for a in range(nd)]
+    frac = [x[a] - base[a] for a in range(nd)]
+    size = 1
+    for v in n:
+        size *= v
+    rho = torch.zeros(size, dtype=torch.float64, device=x.device)
+    for o in range(1 << nd):
+        w = q.clone()
+        idx = torch.zeros_like(base[0])
+        stride = 1
+        for a in range(nd):
+            off = (o >> a) & 1
+            w = w * (frac[a] if off else 1 - frac[a])
+            idx += ((base[a] + off) % n[a]) * stride
+            stride *= n[a]
+        rho.index_add_(0, idx, w)
+    return rho.view(*reversed(n))
 
 
 def test_refused_options(G):
