@@ -93,7 +93,8 @@ class Params(C.Structure):
                 ("f_E", C.c_double), ("dl", C.c_double), ("qm", C.c_double * 4),
                 ("curvature", C.c_int), ("mu_mode", C.c_int), ("grad_mode", C.c_int),
                 ("force", C.c_int), ("max_iter", C.c_int), ("fixed_iters", C.c_int),
-                ("tol", C.c_double), ("frame", C.c_int), ("gyro_phase", C.c_int)]
+                ("tol", C.c_double), ("frame", C.c_int), ("gyro_phase", C.c_int),
+                ("mirror", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -183,10 +184,11 @@ def _load():
 
 def make_params(*, c=1.0, dt, f_rho=0.4, f_E=1.0, dl=1.0, qm=(-1.0, 1.0, 0.0, 0.0),
                 curvature=1, mu_mode=MU_CONSERVE, grad_mode=GRAD_DW, force=FORCE_NONE,
-                max_iter=16, fixed_iters=0, tol=1e-7, frame=0, gyro_phase=0) -> Params:
+                max_iter=16, fixed_iters=0, tol=1e-7, frame=0, gyro_phase=0,
+                mirror=0) -> Params:
     q = list(qm) + [0.0] * (4 - len(qm))
     return Params(c, dt, f_rho, f_E, dl, (C.c_double * 4)(*q), curvature, mu_mode,
-                  grad_mode, force, max_iter, fixed_iters, tol, frame, gyro_phase)
+                  grad_mode, force, max_iter, fixed_iters, tol, frame, gyro_phase, mirror)
 
 
 class OracleField:

@@ -165,6 +165,7 @@ typedef struct {
     double db[3][3];   /* d_i b_j */
     double bgb[3];     /* (b . grad) b */
     double vgb[3];     /* (v_E . grad) b */
+    double gB[3];      /* grad |B|: d_i |B| = b_j d_i B_j (lab-frame b) */
     int ok;            /* B > 0 and v_E < c */
 } point_t;
 
@@ -237,6 +238,7 @@ static void eval_point(const orc_field *f, const orc_params *p, const double R[3
     for (int i = 0; i < 3; ++i) {
         double bdB = P->b[0] * P->dB[i][0] + P->b[1] * P->dB[i][1] +
                      P->b[2] * P->dB[i][2];
+        P->gB[i] = bdB;
         for (int j = 0; j < 3; ++j)
             P->db[i][j] = (P->dB[i][j] - P->b[j] * bdB) / P->Bmag;
     }
@@ -349,6 +351,39 @@ static void boris_step(const double E[3], const double B[3], double qm,
 }
 
 /* ---------------------------------------------------------------------- */
+/* Mirror terms (option `mirror`).  Sec. 2.2 names the grad-B ("mirror")    */
+/* drift and the mirror force of the guiding-center expansion and discards  */
+/* them, giving no formula.  Reading: the standard relativistic forms of    */
+/* the expansion the paper cites (Vandervoort 1960, Northrop 1963), in the   */
+/* notation of Eq. (curvdrift): the grad-B term (mu/(m Gamma)) grad(B/kappa) */
+/* joins the bracket of v_c,                                                */
+/*   v_gB = (m c kappa^2/(q B)) b x [ (mu/(m Gamma)) grad(B/kappa) ],         */
+/* and the mirror force -(mu/(m Gamma)) b . grad(B/kappa) joins du_par/dt.  */
+/* The records carry no grad E, so grad(B/kappa) is taken as grad(B)/kappa  */
+/* (grad kappa is second order in E/B); mu is mu/m as stored.  In the       */
+/* discrete step the drift is evaluated like v_c (at each fixed-point       */
+/* iterate, with its Gamma), and the force explicitly at (x^n,              */
+/* u_par^{n-1/2}), with Gamma(R^n, u_par^{n-1/2}).  The conversions at      */
+/* R^{n-1/2} and R^{n+1/2} keep the paper's drift set (v_E + v_c).          */
+/* ---------------------------------------------------------------------- */
+static void v_gradB(const point_t *P, const orc_params *p, double qm, double mu, double Gam,
+                    double vg[3])
+{
+    double a[3], bxa[3];
+    for (int k = 0; k < 3; ++k) a[k] = mu / Gam * P->gB[k] / P->kappa;
+    cross3(P->b, a, bxa);
+    double pref = p->c * P->kappa * P->kappa / (qm * P->Bmag);
+    for (int k = 0; k < 3; ++k) vg[k] = pref * bxa[k];
+}
+
+static double mirror_force(const point_t *P, const orc_params *p, double upar, double mu,
+                           double uperp)
+{
+    double G0 = gamma_gca(P, p, upar, mu, uperp);
+    return -mu / G0 * dot3(P->b, P->gB) / P->kappa;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Full -> GC conversion (Sec. 3.1): at R^{n-1/2},                         */
 /* u = u_par b + (v_E + v_c(R, u_par)) Gamma + u_perp,g, with u_par = u.b   */
 /* and Gamma taken equal to the Lorentz factor of the full u.  Then         */
@@ -454,15 +489,17 @@ static int upar_kick(const point_t *P, const orc_params *p, double qm,
                      orc_detail *d)
 {
     double dt = p->dt, c2 = p->c * p->c;
+    /* mirror force (option), explicit at (x^n, u_par^{n-1/2}) */
+    double fm = p->mirror ? dt * mirror_force(P, p, upar, mu, uperp) : 0.0;
     if (!p->curvature) {
-        *upar_new = upar + qm * dt * P->Epar;
+        *upar_new = upar + qm * dt * P->Epar + fm;
         return 1;
     }
     double a = dot3(P->vE, P->bgb);
     double g = dot3(P->vE, P->vgb);
     double D = 1.0 - 0.5 * dt * a;
     double G0 = gamma_gca(P, p, upar, mu, uperp);
-    double upr = upar * (1.0 + 0.5 * dt * a) + qm * dt * P->Epar + 0.5 * dt * G0 * g;
+    double upr = upar * (1.0 + 0.5 * dt * a) + qm * dt * P->Epar + 0.5 * dt * G0 * g + fm;
     double k1 = 0.25 * dt * dt * g * g - c2 * D * D / (P->kappa * P->kappa);
     double k2 = upr * dt * g;
     double k3 = upr * upr + (c2 + perp_sq(P, p, mu, uperp)) * D * D;
@@ -480,14 +517,16 @@ static int upar_kick(const point_t *P, const orc_params *p, double qm,
 }
 
 /* GC velocity dR/dt = u_par b / Gamma + v_E + v_c at a point (Eq. dRdt),   */
-/* Gamma and v_c evaluated with the given u_par (Eq. dRdtcase2disc).        */
+/* Gamma and v_c evaluated with the given u_par (Eq. dRdtcase2disc); with   */
+/* the mirror option, + v_gB.                                               */
 static void gc_velocity(const point_t *P, const orc_params *p, double qm,
                         double upar, double mu, double uperp, double V[3])
 {
     double G = gamma_gca(P, p, upar, mu, uperp);
-    double vc[3];
+    double vc[3], vg[3] = {0.0, 0.0, 0.0};
     v_curv(P, p, qm, upar, G, vc);
-    for (int k = 0; k < 3; ++k) V[k] = upar * P->b[k] / G + P->vE[k] + vc[k];
+    if (p->mirror) v_gradB(P, p, qm, mu, G, vg);
+    for (int k = 0; k < 3; ++k) V[k] = upar * P->b[k] / G + P->vE[k] + vc[k] + vg[k];
 }
 
 /* ---------------------------------------------------------------------- */

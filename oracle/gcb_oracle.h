@@ -70,6 +70,8 @@ typedef struct {
     int frame;           /* ORC_FRAME_SIMPLE (b, v_E = cExB/B^2) or ORC_FRAME_BT */
     int gyro_phase;      /* 0: gyration direction kept (Sec. 3.1); 1: advanced by
                             the gyro-frequency over the step */
+    int mirror;          /* 0: the paper's reduced GCA; 1: with the grad-B drift
+                            and the mirror force it discards (Sec. 2.2) */
 } orc_params;
 
 typedef struct {

@@ -472,7 +472,7 @@ int orcg_push_jac(long n, double *x, double *u, double *dxp, unsigned char *flag
                   double *jac)
 {
     if (nm < 0 || nm > NM_MAX || n < 0 || nx < 1 || ny < 1 || p->frame != ORC_FRAME_SIMPLE ||
-        p->gyro_phase != 0)
+        p->gyro_phase != 0 || p->mirror != 0)
         return 1;
     ModeField f{{nx, ny}, {dx, dy}, base, pat, nm, amps};
 #ifdef _OPENMP

@@ -20,7 +20,8 @@ def oracle_params(p, **over):
                          grad_mode=q.get("grad_mode", 0), force=q.get("force", 0),
                          max_iter=q.get("gca_max_iter", 16),
                          fixed_iters=q.get("gca_fixed_iters", 0), tol=q.get("gca_tol", 1e-7),
-                         frame=q.get("drift_frame", 0), gyro_phase=q.get("gyro_phase", 0))
+                         frame=q.get("drift_frame", 0), gyro_phase=q.get("gyro_phase", 0),
+                         mirror=q.get("mirror", 0))
 
 
 def copy_state(st):

@@ -184,6 +184,36 @@ def test_deposit_pins_catch_planted_mistake(name, old, new, tmp_path):
     assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
 
 
+# mistakes in the mirror terms (option mirror)
+MUTANTS_MIRROR = [
+    ("mirror_drift_sign", "for (int k = 0; k < 3; ++k) vg[k] = pref * bxa[k];",
+     "for (int k = 0; k < 3; ++k) vg[k] = -pref * bxa[k];"),
+    ("mirror_drift_kappa_dropped",
+     "for (int k = 0; k < 3; ++k) a[k] = mu / Gam * P->gB[k] / P->kappa;",
+     "for (int k = 0; k < 3; ++k) a[k] = mu / Gam * P->gB[k];"),
+    ("mirror_drift_gamma_dropped",
+     "for (int k = 0; k < 3; ++k) a[k] = mu / Gam * P->gB[k] / P->kappa;",
+     "for (int k = 0; k < 3; ++k) a[k] = mu * P->gB[k] / P->kappa;"),
+    ("mirror_force_sign", "return -mu / G0 * dot3(P->b, P->gB) / P->kappa;",
+     "return mu / G0 * dot3(P->b, P->gB) / P->kappa;"),
+    ("mirror_force_gamma_dropped", "return -mu / G0 * dot3(P->b, P->gB) / P->kappa;",
+     "return -mu * dot3(P->b, P->gB) / P->kappa;"),
+    ("mirror_force_not_in_flat_scheme", "*upar_new = upar + qm * dt * P->Epar + fm;",
+     "*upar_new = upar + qm * dt * P->Epar;"),
+    ("mirror_gradB_is_gradBz", "P->gB[i] = bdB;", "P->gB[i] = P->dB[i][2] + P->dB[i][0];"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS_MIRROR, ids=[c[0] for c in MUTANTS_MIRROR])
+def test_mirror_pins_catch_planted_mistake(name, old, new, tmp_path):
+    lib = _build_mutant(str(tmp_path), SRC, old, new)
+    env = dict(os.environ, GCB_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_mirror_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+
+
 # mistakes in the dual-number gradient oracle: its arithmetic on derivatives
 # and the seeding of the directions
 SRC_GRAD = os.path.join(ROOT, "oracle", "gcb_oracle_grad.cpp")
