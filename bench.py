@@ -323,6 +323,37 @@ def pic_deposit(G, multi, ds, grid, p, sort_every, tile, ws, step, w, args, barr
     return out
 
 
+def option_costs(G, multi, ds, grid, p, sort_every, tile, ws, step, args, barrier, stream):
+    """ms per step of the push with each method option on (the exact drift
+    frame, the evolved gyration phase, the mirror terms) against the plain
+    push, each timed over the same number of steps from a sort step."""
+    import torch
+    K = max(8, args.steps // 4)
+    out = {}
+    for name, over in (("plain", {}), ("drift_frame_bt", {"drift_frame": 1}),
+                       ("gyro_phase_evolve", {"gyro_phase": 1}), ("mirror_terms", {"mirror": 1})):
+        gp = G.make_params(p, sort_every=sort_every, sort_tile=tile, **over)
+        k0 = step[0] + (-step[0]) % max(1, sort_every)
+        gp.step_index = k0
+        G.push(ds, grid, gp, 1, workspace=ws, stats=False)          # warm-up
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(K):
+            gp.step_index = k0 + 1 + k
+            G.push(ds, grid, gp, 1, workspace=ws, stats=False)
+        e1.record(stream)
+        barrier()
+        step[0] = k0 + 1 + K
+        _, ms, _ = multi.whole_job_rate(ds.n, K, e0.elapsed_time(e1), device="cuda")
+        out[name] = ms / K
+    base = out["plain"]
+    return {"ms_per_step": out, "vs_plain": {k: v / base for k, v in out.items()},
+            "steps": K, "method": "each option timed over the same number of steps of the "
+                                  "evolving state, from a sort step, with CUDA events"}
+
+
 def workload_config(w, n_total, ngpu, sort_every, sort_tile):
     cfg = {"workload": w["desc"].format(n=n_total), "particles": n_total,
            "particles_per_gpu": n_total // ngpu, "steps_per_call": 1,
@@ -600,6 +631,8 @@ def main():
                     help="skip the adjoint / forward cost ratio of the default line")
     ap.add_argument("--no-deposit", action="store_true",
                     help="skip the PiC step with current deposition")
+    ap.add_argument("--no-options", action="store_true",
+                    help="skip the cost of the method options (exact frame, phase, mirror)")
     ap.add_argument("--e2e-chunks", type=int, default=8,
                     help="particle chunks streamed through the GPU in the end-to-end timing")
     ap.add_argument("--sort-every", type=int, default=None)
@@ -750,6 +783,13 @@ def main():
         pic = pic_deposit(G, multi, ds, grid, p, sort_every, tile, ws, step, w, args, barrier,
                           stream, n)
 
+    # what the method options cost on this workload (flat pushes with
+    # FP32-pair positions or FP64: where every option has kernels)
+    opts = None
+    if not ks and not args.no_options:
+        opts = option_costs(G, multi, ds, grid, p, sort_every, tile, ws, step, args, barrier,
+                            stream)
+
     fp64 = None
     if not args.no_fp64 and rank == 0 and w["fp64_b"] is not None:
         n64 = min(n, 1 << 22)
@@ -829,7 +869,8 @@ def main():
                          "ms_push_kernel": avg_launch},
                 "clocks": clocks,
                 "branch_mix": mix,
-                "fp64": fp64, "test_particle_mode": tpm, "pic_deposit": pic}
+                "fp64": fp64, "test_particle_mode": tpm, "pic_deposit": pic,
+                "option_costs": opts}
         if not args.no_adjoint and args.workload == "reconnection2d":
             line["adjoint_vs_forward"] = adjoint_vs_forward(G)
         if not args.no_cpu_baseline:

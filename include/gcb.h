@@ -50,6 +50,7 @@ enum { GCB_FORCE_NONE = 0, GCB_FORCE_BORIS = 1, GCB_FORCE_GCA = 2 };
 enum { GCB_MU_CONSERVE = 0, GCB_UPERP_CONSERVE = 1 };
 enum { GCB_FRAME_SIMPLE = 0, GCB_FRAME_BT = 1 };
 enum { GCB_PHASE_KEEP = 0, GCB_PHASE_EVOLVE = 1 };
+enum { GCB_MIRROR_OFF = 0, GCB_MIRROR_ON = 1 };
 
 /* Per-particle flag byte. */
 enum {
@@ -162,6 +163,18 @@ typedef struct {
                                 Gamma) at R^{n+1/2} (the extra equation Sec. 3.1
                                 says could be added).  gcb_push_sr only; the
                                 covariant push and the adjoint refuse it. */
+    int32_t mirror;          /* GCB_MIRROR_OFF (0): the paper's reduced GCA, which
+                                drops the grad-B drift and the mirror force
+                                (Sec. 2.2); GCB_MIRROR_ON: with them, in the
+                                relativistic forms of the expansion the paper cites:
+                                (c kappa mu/((q/m) B Gamma)) b x grad B added to
+                                the guiding-center velocity and the force
+                                -(mu/Gamma) b.grad(B)/kappa to du_par/dt, explicit
+                                at (x^n, u_par^{n-1/2}) (mu as mu/m; grad kappa
+                                neglected: the records carry no grad E).
+                                gcb_push_sr only, unfused, simplified frame; the
+                                deposition, the covariant push and the adjoint
+                                refuse it (GCB_EUNSUPPORTED). */
 } gcb_params;
 
 /* Counters of one gcb_push_sr call, summed over its steps. */

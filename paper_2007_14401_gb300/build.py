@@ -22,13 +22,15 @@ PEAK_LIB = os.path.join(OUT_DIR, "libgcb_peak.so")
 PEAK_SRC = "peak_fma.cu"
 
 SOURCES = ["gcb_api.cu", "sort_sr.cu", "gcb_noalloc.cu", "gcb_ks.cu", "adjoint_sr.cu",
-           "push_sr_f64.cu", "push_sr_f32.cu", "push_dep_f64.cu", "push_dep_f32.cu"]
+           "push_sr_f64.cu", "push_sr_f32.cu", "push_dep_f64.cu", "push_dep_f32.cu",
+           "push_mir_f64.cu", "push_mir_f32.cu"]
 # The mixed-precision push and the adjoint unit use approximate FP32 division
 # and square root (about 2 ulp) and flush FP32 denormals: the flags act on
 # single precision only, so the FP64 kernels in the adjoint unit keep IEEE
 # operations, as does the FP64 push.  The adjoint's FP32 replay of a step then
 # uses the same arithmetic as the FP32 push it retraces.
 EXTRA = {"push_sr_f32.cu": ["-use_fast_math"], "push_dep_f32.cu": ["-use_fast_math"],
+         "push_mir_f32.cu": ["-use_fast_math"],
          "adjoint_sr.cu": ["-use_fast_math"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

@@ -301,6 +301,16 @@ static gcb_status check_problem(const gcb_particles *p, const gcb_grid *g, const
         set_error("drift_frame GCB_FRAME_BT runs one step per launch (fuse_steps <= 1)");
         return GCB_EUNSUPPORTED;
     }
+    if (prm->mirror != GCB_MIRROR_OFF && prm->mirror != GCB_MIRROR_ON) {
+        set_error("mirror must be GCB_MIRROR_OFF or GCB_MIRROR_ON");
+        return GCB_EINVAL;
+    }
+    if (prm->mirror == GCB_MIRROR_ON &&
+        (prm->fuse_steps > 1 || prm->drift_frame != GCB_FRAME_SIMPLE)) {
+        set_error("the mirror terms run one step per launch (fuse_steps <= 1) in the "
+                  "simplified drift frame");
+        return GCB_EUNSUPPORTED;
+    }
     if (prm->sort_every < 0 || prm->sort_tile[0] < 0 || prm->sort_tile[1] < 0 ||
         prm->sort_tile[2] < 0 || prm->step_index < 0) {
         set_error("sort_every, sort_tile and step_index must be >= 0");
@@ -435,9 +445,10 @@ gcb_status gcb_push_ks(const gcb_particles *p, const gcb_grid_ks *gk, const gcb_
         return GCB_EUNSUPPORTED;
     }
     if (prm->c != 1.0) { set_error("the covariant scheme uses c = 1"); return GCB_EINVAL; }
-    if (prm->drift_frame != GCB_FRAME_SIMPLE || prm->gyro_phase != GCB_PHASE_KEEP) {
-        set_error("the covariant scheme uses the simplified drift frame and keeps the "
-                  "gyration direction");
+    if (prm->drift_frame != GCB_FRAME_SIMPLE || prm->gyro_phase != GCB_PHASE_KEEP ||
+        prm->mirror != GCB_MIRROR_OFF) {
+        set_error("the covariant scheme uses the simplified drift frame, keeps the "
+                  "gyration direction and has no mirror terms");
         return GCB_EUNSUPPORTED;
     }
     if (!(prm->dt > 0) || !(prm->f_rho > 0) || !(prm->f_E > 0)) { set_error("dt, f_rho, f_E must be > 0"); return GCB_EINVAL; }
@@ -503,8 +514,10 @@ static gcb_status check_current(const gcb_particles *p, const gcb_grid *g, const
         set_error("per-particle weights are not permuted by sorting: sort_every must be 0");
         return GCB_EUNSUPPORTED;
     }
-    if (prm->fuse_steps > 1 || prm->drift_frame != GCB_FRAME_SIMPLE) {
-        set_error("deposition: unfused steps (fuse_steps <= 1) in the simplified drift frame");
+    if (prm->fuse_steps > 1 || prm->drift_frame != GCB_FRAME_SIMPLE ||
+        prm->mirror != GCB_MIRROR_OFF) {
+        set_error("deposition: unfused steps (fuse_steps <= 1) in the simplified drift frame, "
+                  "without mirror terms");
         return GCB_EUNSUPPORTED;
     }
     if (g->n[0] * g->n[1] * g->n[2] >= ((int64_t)1 << 31)) {
@@ -579,6 +592,9 @@ static gcb_status push_sr_impl(const gcb_particles *p, const gcb_grid *g, const 
         if (cur)
             s = fp64 ? push_dep_step_f64(p, in, g, prm, cur, st, stats)
                      : push_dep_step_f32(p, in, g, prm, cur, st, stats);
+        else if (prm->mirror == GCB_MIRROR_ON)
+            s = fp64 ? push_mir_step_f64(p, in, g, prm, st, stats)
+                     : push_mir_step_f32(p, in, g, prm, st, stats);
         else
             s = fp64 ? push_step_f64(p, in, g, prm, st, stats, k)
                      : push_step_f32(p, in, g, prm, st, stats, k);
@@ -803,9 +819,10 @@ static gcb_status check_adjoint(const gcb_particles *p, const gcb_grid *g, const
         set_error("the adjoint supports 2D grids with gradient records (grad_mode GRID)");
         return GCB_EUNSUPPORTED;
     }
-    if (prm->drift_frame != GCB_FRAME_SIMPLE || prm->gyro_phase != GCB_PHASE_KEEP) {
+    if (prm->drift_frame != GCB_FRAME_SIMPLE || prm->gyro_phase != GCB_PHASE_KEEP ||
+        prm->mirror != GCB_MIRROR_OFF) {
         set_error("the adjoint differentiates the simplified drift frame with the gyration "
-                  "direction kept only");
+                  "direction kept and without mirror terms only");
         return GCB_EUNSUPPORTED;
     }
     if (n_steps < 1 || ckpt_every < 1) { set_error("n_steps and ckpt_every must be >= 1"); return GCB_EINVAL; }

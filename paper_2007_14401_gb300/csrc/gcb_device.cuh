@@ -379,6 +379,7 @@ template <typename R>
 struct Frame {
     R Bmag, ib, b[3], vE[3], kappa, Epar;
     R bgb[3], vgb[3];
+    R gB[3];      // grad |B| (mirror terms only)
     bool ok;
 };
 
@@ -457,7 +458,8 @@ __device__ __forceinline__ void bt_frame(const T E[3], const T B[3], T B2, T c, 
 // one: b*, the exact v_E and kappa from it, E_par = E.b*; the gradient terms
 // are (b*.grad)b and (v_E.grad)b with grad b that of the lab-frame b = B/B
 // (projected), the records carrying no grad E.
-template <typename R, int ND, bool GRADS, bool PROJ = true, bool BT = false>
+// MIR = true also forms grad |B|: d_i |B| = b_j d_i B_j (the mirror terms).
+template <typename R, int ND, bool GRADS, bool PROJ = true, bool BT = false, bool MIR = false>
 __device__ __forceinline__ void make_frame(const FieldPt<R, ND> &F, R c, R inv_c2, Frame<R> &f)
 {
     if constexpr (BT) {
@@ -552,6 +554,11 @@ __device__ __forceinline__ void make_frame(const FieldPt<R, ND> &F, R c, R inv_c
                 f.vgb[j] = y[j] * ib;
             }
         }
+        if constexpr (MIR) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                f.gB[i] = i < ND ? dot3(f.b, F.dB[i]) : R(0);
+        }
     }
 }
 
@@ -627,13 +634,23 @@ __device__ __forceinline__ void vcurv_ig(const Frame<R> &f, const StepPar<R> &s,
     for (int k = 0; k < 3; ++k) vc[k] = pref * x[k];
 }
 
-template <typename R>
+// MIR = true adds the grad-B drift (the mirror option): the term
+// (mu/(m Gamma)) grad(B)/kappa in the bracket of v_c, i.e.
+// v_gB = cq kappa mu/(Gamma B) b x grad B (mu as mu/m).
+template <typename R, bool MIR = false>
 __device__ __forceinline__ void gc_vel_ig(const Frame<R> &f, const StepPar<R> &s, R cq, R upar, R mu,
                                           R uperp, R V[3])
 {
     R iG = R(1) / gamma_gc(f, s, upar, mu, uperp);
     R vc[3];
     vcurv_ig(f, s, cq, upar, iG, vc);
+    if constexpr (MIR) {
+        R x[3];
+        cross3(f.b, f.gB, x);
+        const R pg = cq * f.kappa * mu * iG * f.ib;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) vc[k] = fma(pg, x[k], vc[k]);
+    }
     R ig = upar * iG;
 #pragma unroll
     for (int k = 0; k < 3; ++k) V[k] = fma(ig, f.b[k], f.vE[k] + vc[k]);
@@ -727,7 +744,10 @@ using StepRecs = std::conditional_t<HasCellCache<Gth>::value, CellRecs<ND, GM>, 
 // the cell of x^n when the caller gathered there through them).  Fh: the
 // fields at R^{n-1/2} = x^n - dxp/2 when the caller has gathered them already
 // (the same gather the step would make), else null.
-template <typename R, int ND, int GM, typename Gth, bool BT = false>
+// MIR = true: with the mirror terms (grad-B drift in the guiding-center
+// velocity, mirror force -(mu/Gamma) b.grad(B)/kappa explicit at
+// (x^n, u_par^{n-1/2}) in the u_par update).
+template <typename R, int ND, int GM, typename Gth, bool BT = false, bool MIR = false>
 __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, const int ib[ND],
                                            const R ln[ND], const R dxp[ND],
                                            const FieldPt<R, ND> &F0, R u[3], R disp[ND],
@@ -743,7 +763,7 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
     const R cq = s.c / s.qm;
     FieldPt<R, ND> F;
     Frame<R> f0, f;
-    make_frame<R, ND, GR, false, BT>(F0, s.c, s.inv_c2, f0);
+    make_frame<R, ND, GR, false, BT, MIR>(F0, s.c, s.inv_c2, f0);
 
     // conversion at R^{n-1/2} = x^n - dxp/2 (Sec. 3.1)
     R pt[ND];
@@ -775,14 +795,18 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
 
     // u_par update at R^n (Sec. 2.2.1 / Eqs. dupardtcase2discsol, duparprimedtcase2discsol)
     R upn;
+    R fm = R(0);   // dt times the mirror force (MIR)
+    if constexpr (MIR)
+        fm = -s.dt * mu * dot3(f0.b, f0.gB) / (gamma_gc(f0, s, upar, mu, uperp) * f0.kappa);
     if (!s.curvature) {
-        upn = fma(s.qm * s.dt, f0.Epar, upar);
+        upn = fma(s.qm * s.dt, f0.Epar, upar) + fm;
     } else {
         R a = dot3(f0.vE, f0.bgb);
         R gg = dot3(f0.vE, f0.vgb);
         R D = fma(-s.half_dt, a, R(1));
         R G0 = gamma_gc(f0, s, upar, mu, uperp);
         R upr = fma(upar, fma(s.half_dt, a, R(1)), fma(s.qm * s.dt, f0.Epar, s.half_dt * G0 * gg));
+        if constexpr (MIR) upr += fm;
         R c2 = s.c * s.c;
         R kap2 = f0.kappa * f0.kappa;
         R k1 = R(0.25) * s.dt * s.dt * gg * gg - c2 * D * D / kap2;
@@ -802,7 +826,7 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
     // fixed point on Eq. (dRdtcase2disc): R^{k+1} = R^n + dt/2 (V^n + V^k),
     // iterated on the displacement R^{k+1} - R^n from R^0 = R^n.
     R Vn[3];
-    gc_vel_ig(f0, s, cq, upn, mu, uperp, Vn);
+    gc_vel_ig<R, MIR>(f0, s, cq, upn, mu, uperp, Vn);
     R dk[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) dk[d] = R(0);
@@ -831,9 +855,9 @@ __device__ __forceinline__ bool gca_step_c(const Gth &gth, const StepPar<R> &s, 
 #pragma unroll
         for (int d = 0; d < ND; ++d) pt[d] = ln[d] + dk[d];
         gat(pt, F);
-        make_frame<R, ND, GR, false, BT>(F, s.c, s.inv_c2, f);
+        make_frame<R, ND, GR, false, BT, MIR>(F, s.c, s.inv_c2, f);
         okall = okall && f.ok;   // a bad frame fails the step after the loop
-        gc_vel_ig(f, s, cq, upn, mu, uperp, V);
+        gc_vel_ig<R, MIR>(f, s, cq, upn, mu, uperp, V);
     }
     if (!okall) return false;
 

@@ -32,6 +32,11 @@ gcb_status push_step_f64(const gcb_particles *p, const gcb_particles *in, const 
 gcb_status push_step_f32(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
                          const gcb_params *prm, cudaStream_t st, unsigned long long *stats,
                          int nsteps = 1);
+// One unfused step with the mirror terms (push_mir_*.cu).
+gcb_status push_mir_step_f64(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
+                             const gcb_params *prm, cudaStream_t st, unsigned long long *stats);
+gcb_status push_mir_step_f32(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
+                             const gcb_params *prm, cudaStream_t st, unsigned long long *stats);
 // One unfused step that also adds the step's current to cur->J (push_dep_*.cu).
 gcb_status push_dep_step_f64(const gcb_particles *p, const gcb_particles *in, const gcb_grid *g,
                              const gcb_params *prm, const gcb_current *cur, cudaStream_t st,

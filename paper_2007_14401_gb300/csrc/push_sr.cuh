@@ -350,7 +350,9 @@ __device__ __forceinline__ bool deposit_path(const PushArgs<R> &a, const int ib[
 // its shared-memory slots between the steps and written once at the end (the
 // test-particle mode); every step's arithmetic is the unfused step's.
 // DEP (unfused only): each advanced particle-step also adds its current to a.J.
-template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false, bool DEP = false>
+// MIR (unfused only): the guiding-center step with the mirror terms.
+template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false, bool DEP = false,
+          bool MIR = false>
 __global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND, GM, DEP>::n) k_push_sr(const PushArgs<R> a)
 {
     static_assert(!(DEP && FUSE), "deposition runs in unfused launches");
@@ -591,7 +593,7 @@ __global__ void __launch_bounds__(Tile<R, ND>::n, MinBlocks<R, ND, GM, DEP>::n) 
             bool done = false;
             R vzg = R(0);   // out-of-plane guiding-center velocity of the step (2D DEP)
             if (isg) {
-                done = gca_step_c<R, ND, GM, Gth, BT>(Gth{a.g}, sp, ib, l, ds, F, us, disp, it,
+                done = gca_step_c<R, ND, GM, Gth, BT, MIR>(Gth{a.g}, sp, ib, l, ds, F, us, disp, it,
                                                       ncv, cr, (HOIST && uni) ? &Fh : nullptr,
                                                       (DEP && ND == 2) ? &vzg : nullptr);
                 if (!done) {
@@ -802,7 +804,8 @@ static void fill_args(PushArgs<R> &a, const gcb_particles *p, const gcb_particle
     a.stats = stats;
 }
 
-template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false, bool DEP = false>
+template <typename R, int ND, int PM, int GM, bool FUSE, bool BT = false, bool DEP = false,
+          bool MIR = false>
 static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
 {
     static int grid_cache[64] = {0};
@@ -815,7 +818,7 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     if (grid == 0) {
         int nsm = 0, occ = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM, FUSE, BT, DEP>,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_sr<R, ND, PM, GM, FUSE, BT, DEP, MIR>,
                                                           Tile<R, ND>::n, 0) !=
                 cudaSuccess) {
             set_error("occupancy query failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -828,7 +831,7 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     int64_t ntiles = (a.np + TPB - 1) / TPB;
     if (ntiles == 0) return GCB_OK;
     int nb = (int)(ntiles < grid ? ntiles : grid);
-    k_push_sr<R, ND, PM, GM, FUSE, BT, DEP><<<nb, TPB, 0, st>>>(a);
+    k_push_sr<R, ND, PM, GM, FUSE, BT, DEP, MIR><<<nb, TPB, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));
@@ -837,16 +840,16 @@ static gcb_status launch_push(const PushArgs<R> &a, cudaStream_t st)
     return GCB_OK;
 }
 
-template <typename R, int PM, bool FUSE, bool BT = false, bool DEP = false>
+template <typename R, int PM, bool FUSE, bool BT = false, bool DEP = false, bool MIR = false>
 static gcb_status dispatch_dims(const PushArgs<R> &a, const gcb_grid *g, const gcb_params *prm,
                                 cudaStream_t st)
 {
     const bool grid_grad = prm->grad_mode == GCB_GRAD_GRID;
     if (g->ndim == 2)
-        return grid_grad ? launch_push<R, 2, PM, 2, FUSE, BT, DEP>(a, st)
-                         : launch_push<R, 2, PM, 1, FUSE, BT, DEP>(a, st);
-    return grid_grad ? launch_push<R, 3, PM, 2, FUSE, BT, DEP>(a, st)
-                     : launch_push<R, 3, PM, 1, FUSE, BT, DEP>(a, st);
+        return grid_grad ? launch_push<R, 2, PM, 2, FUSE, BT, DEP, MIR>(a, st)
+                         : launch_push<R, 2, PM, 1, FUSE, BT, DEP, MIR>(a, st);
+    return grid_grad ? launch_push<R, 3, PM, 2, FUSE, BT, DEP, MIR>(a, st)
+                     : launch_push<R, 3, PM, 1, FUSE, BT, DEP, MIR>(a, st);
 }
 
 // Which (arithmetic, position) pairs carry kernels of the exact drift frame:
@@ -871,6 +874,18 @@ static gcb_status dispatch_push(const gcb_particles *p, const gcb_particles *in,
     if (nsteps <= 1) return dispatch_dims<R, PM, false>(a, g, prm, st);
     a.nsteps = nsteps;
     return dispatch_dims<R, PM, true>(a, g, prm, st);
+}
+
+// One unfused step with the mirror terms (simplified drift frame, no
+// deposition; checked by the caller).
+template <typename R, int PM>
+static gcb_status dispatch_push_mir(const gcb_particles *p, const gcb_particles *in,
+                                    const gcb_grid *g, const gcb_params *prm, cudaStream_t st,
+                                    unsigned long long *stats)
+{
+    PushArgs<R> a;
+    fill_args<R>(a, p, in, g, prm, stats);
+    return dispatch_dims<R, PM, false, false, false, true>(a, g, prm, st);
 }
 
 // One unfused step with current deposition into cur (simplified drift frame;

@@ -21,6 +21,7 @@ FORCE_NONE, FORCE_BORIS, FORCE_GCA = 0, 1, 2
 MU_CONSERVE, UPERP_CONSERVE = 0, 1
 FRAME_SIMPLE, FRAME_BT = 0, 1
 PHASE_KEEP, PHASE_EVOLVE = 0, 1
+MIRROR_OFF, MIRROR_ON = 0, 1
 FLAG_S, FLAG_SPREV, FLAG_NONCONV, FLAG_GCAFAIL, FLAG_NONFINITE, FLAG_EXITED = 1, 2, 4, 8, 16, 32
 SPECIES_SHIFT = 6
 STATUS = {0: "GCB_OK", 1: "GCB_EINVAL", 2: "GCB_ECUDA", 3: "GCB_EUNSUPPORTED", 4: "GCB_ENOMEM"}
@@ -47,7 +48,7 @@ class GcbParams(C.Structure):
                 ("gca_fixed_iters", C.c_int32), ("gca_tol", C.c_double),
                 ("sort_every", C.c_int32), ("sort_tile", C.c_int32 * 3),
                 ("step_index", C.c_int64), ("fuse_steps", C.c_int32),
-                ("drift_frame", C.c_int32), ("gyro_phase", C.c_int32)]
+                ("drift_frame", C.c_int32), ("gyro_phase", C.c_int32), ("mirror", C.c_int32)]
 
 
 class GcbStats(C.Structure):
@@ -443,7 +444,7 @@ def make_params(p: dict, **over) -> GcbParams:
                      float(q.get("gca_tol", 1e-7)), int(q.get("sort_every", 0)),
                      (C.c_int32 * 3)(*tile[:3]), int(q.get("step_index", 0)),
                      int(q.get("fuse_steps", 0)), int(q.get("drift_frame", 0)),
-                     int(q.get("gyro_phase", 0)))
+                     int(q.get("gyro_phase", 0)), int(q.get("mirror", 0)))
 
 
 def _work_device(state):
