@@ -177,11 +177,16 @@ typedef struct {
                                 refuse it (GCB_EUNSUPPORTED). */
 } gcb_params;
 
-/* Counters of one gcb_push_sr call, summed over its steps. */
+/* Counters of one push call (gcb_push_sr, gcb_push_ks, ...), summed over its
+ * steps. */
 typedef struct {
     int64_t n_boris, n_gca;          /* particle-steps per branch */
     int64_t n_to_gca, n_to_boris;    /* switches S: 1 -> 0 and 0 -> 1 */
-    int64_t n_nonconv, n_gcafail, n_nonfinite;
+    int64_t n_nonconv, n_gcafail;    /* steps with GCB_FLAG_NONCONV / GCB_FLAG_GCAFAIL */
+    int64_t n_nonfinite;             /* particle-steps not advanced: a non-finite
+                                        state (GCB_FLAG_NONFINITE), and in the
+                                        covariant push also a particle frozen after
+                                        leaving [r_in, r_out] (GCB_FLAG_EXITED) */
     int64_t sum_iter, max_iter;      /* fixed-point iterations */
     double sum_ekin;                 /* sum of (Gamma - 1) m c^2 / m after each step */
 } gcb_stats;
