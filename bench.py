@@ -196,9 +196,7 @@ def coupling_report(G, multi, ds, grid, gp, ws, ks, snap, step_first, steps, fie
            "to_gca": tot["n_to_gca"], "to_boris": tot["n_to_boris"],
            "mean_iter": tot["sum_iter"] / max(1, tot["n_gca"]), "max_iter": tot["max_iter"],
            "nonconv": tot["n_nonconv"], "gcafail": tot["n_gcafail"],
-           # particle-steps not advanced: non-finite states, and in the
-           # covariant push particles frozen after leaving [r_in, r_out]
-           ("frozen_exited_or_nonfinite" if ks else "nonfinite"): tot["n_nonfinite"]}
+           "nonfinite": tot["n_nonfinite"], "exited": tot["n_exited"]}
     if not ks:
         x = snap[0].double().cpu().numpy()
         if ds.x_lo is not None:

@@ -183,12 +183,13 @@ typedef struct {
     int64_t n_boris, n_gca;          /* particle-steps per branch */
     int64_t n_to_gca, n_to_boris;    /* switches S: 1 -> 0 and 0 -> 1 */
     int64_t n_nonconv, n_gcafail;    /* steps with GCB_FLAG_NONCONV / GCB_FLAG_GCAFAIL */
-    int64_t n_nonfinite;             /* particle-steps not advanced: a non-finite
-                                        state (GCB_FLAG_NONFINITE), and in the
-                                        covariant push also a particle frozen after
-                                        leaving [r_in, r_out] (GCB_FLAG_EXITED) */
+    int64_t n_nonfinite;             /* particle-steps not advanced: non-finite state
+                                        (GCB_FLAG_NONFINITE) */
     int64_t sum_iter, max_iter;      /* fixed-point iterations */
     double sum_ekin;                 /* sum of (Gamma - 1) m c^2 / m after each step */
+    int64_t n_exited;                /* particle-steps not advanced because the
+                                        particle had left [r_in, r_out] before the
+                                        step (GCB_FLAG_EXITED; covariant push only) */
 } gcb_stats;
 
 /* Library version (major*10000 + minor*100 + patch). */

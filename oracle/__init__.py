@@ -101,7 +101,7 @@ class Stats(C.Structure):
     _fields_ = [("n_boris", C.c_long), ("n_gca", C.c_long), ("n_to_gca", C.c_long),
                 ("n_to_boris", C.c_long), ("n_nonconv", C.c_long), ("n_gcafail", C.c_long),
                 ("n_nonfinite", C.c_long), ("sum_iter", C.c_long), ("max_iter", C.c_long),
-                ("sum_ekin", C.c_double)]
+                ("sum_ekin", C.c_double), ("n_exited", C.c_long)]
 
 
 class Detail(C.Structure):

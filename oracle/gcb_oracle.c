@@ -372,7 +372,7 @@ static void v_gradB(const point_t *P, const orc_params *p, double qm, double mu,
     double a[3], bxa[3];
     for (int k = 0; k < 3; ++k) a[k] = mu / Gam * P->gB[k] / P->kappa;
     cross3(P->b, a, bxa);
-    double pref = p->c * P->kappa * P->kappa / (qm * P->Bmag);
+    double pref = p->c * P->kappa * P->kappa / (P->Bmag * qm);   /* as in v_c */
     for (int k = 0; k < 3; ++k) vg[k] = pref * bxa[k];
 }
 

@@ -79,6 +79,7 @@ typedef struct {
     long n_nonconv, n_gcafail, n_nonfinite, sum_iter;
     long max_iter;
     double sum_ekin;     /* sum of (Gamma - 1) over particles and steps */
+    long n_exited;       /* covariant push: steps not taken after leaving [r_in, r_out] */
 } orc_stats;
 
 /* Kerr-Schild field on the axisymmetric node grid (log r, theta):

@@ -700,20 +700,25 @@ int orc_push_ks(long n, double *const x[3], double *const u[3], unsigned char *f
     (void)nthreads;
 #endif
     for (int s = 0; s < n_steps; ++s) {
-        long nb = 0, ng = 0, tg = 0, tb = 0, nc = 0, gf = 0, nf = 0, si = 0, mi = 0;
+        long nb = 0, ng = 0, tg = 0, tb = 0, nc = 0, gf = 0, nf = 0, ne = 0, si = 0, mi = 0;
         double ek = 0.0;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 64) \
-    reduction(+ : nb, ng, tg, tb, nc, gf, nf, si, ek) reduction(max : mi)
+    reduction(+ : nb, ng, tg, tb, nc, gf, nf, ne, si, ek) reduction(max : mi)
 #endif
         for (long i = 0; i < n; ++i) {
             double xi[3] = {x[0][i], x[1][i], x[2][i]}, ui[3] = {u[0][i], u[1][i], u[2][i]};
             unsigned char fl = flags[i];
+            const unsigned char fl0 = fl;
             orc_detail d;
             orc_ks_step_one(f, kp, p, dl, xi, ui, &fl, &d);
             for (int k = 0; k < 3; ++k) { x[k][i] = xi[k]; u[k][i] = ui[k]; }
             flags[i] = fl;
-            if (d.branch < 0) { ++nf; continue; }
+            if (d.branch < 0) {
+                /* already outside [r_in, r_out]: exited; otherwise non-finite */
+                if ((fl0 & ORC_FLAG_EXITED) && !(fl0 & ORC_FLAG_NONFINITE)) ++ne; else ++nf;
+                continue;
+            }
             if (d.branch == 1) ++nb; else ++ng;
             int sp = (fl & ORC_FLAG_SPREV) ? 1 : 0, sn = (fl & ORC_FLAG_S) ? 1 : 0;
             if (sp && !sn) ++tg;
@@ -731,6 +736,7 @@ int orc_push_ks(long n, double *const x[3], double *const u[3], unsigned char *f
         }
         acc.n_boris += nb; acc.n_gca += ng; acc.n_to_gca += tg; acc.n_to_boris += tb;
         acc.n_nonconv += nc; acc.n_gcafail += gf; acc.n_nonfinite += nf;
+        acc.n_exited += ne;
         acc.sum_iter += si;
         if (mi > acc.max_iter) acc.max_iter = mi;
         acc.sum_ekin += ek;

@@ -264,6 +264,7 @@ static gcb_status read_stats(const unsigned long long *stats, cudaStream_t st, g
     double e;
     memcpy(&e, &h[ST_EKIN], sizeof(e));
     out->sum_ekin = e;
+    out->n_exited = (int64_t)h[ST_EXITED];
     return GCB_OK;
 }
 

@@ -16,6 +16,7 @@ enum {
     ST_DEPSKIP,   // particle-steps left out of the current (path too long)
     ST_DEPPIECE,  // path pieces deposited
     ST_DEPATOM,   // atomic additions into the current
+    ST_EXITED,    // covariant push: particle-steps frozen after leaving [r_in, r_out]
     ST_COUNT
 };
 constexpr size_t kStatsBytes = 256;

@@ -609,6 +609,7 @@ __global__ void __launch_bounds__(TPB, 3) k_push_ks(const KsGrid<FT> g, const Ar
     if (tid < ST_COUNT) s_acc[tid] = 0ull;
     if (tid == 0) s_ek = 0.0;
     unsigned nb = 0, ng = 0, tg = 0, tb = 0, nc = 0, gf = 0, nf = 0, si = 0, mi = 0;
+    unsigned ne = 0;   // frozen after leaving [r_in, r_out]
     double ek = 0.0;
     const double PI = 3.141592653589793;
 
@@ -630,6 +631,7 @@ __global__ void __launch_bounds__(TPB, 3) k_push_ks(const KsGrid<FT> g, const Ar
                 us[k] = a.uin[k][i];
                 fin = fin && isfinite(xs[k]) && isfinite(us[k]);
             }
+            const uint8_t fl_in = fl;
             if (!fin && !(fl & GCB_FLAG_NONFINITE)) { fl |= GCB_FLAG_NONFINITE; }
             if (fin && !(fl & (GCB_FLAG_NONFINITE | GCB_FLAG_EXITED))) {
                 // switch (Sec. 3, 4.2): Gamma/(|q/m| B) against the cell size of
@@ -658,6 +660,8 @@ __global__ void __launch_bounds__(TPB, 3) k_push_ks(const KsGrid<FT> g, const Ar
                 if (a.c.force == GCB_FORCE_BORIS) S = 1;
                 if (a.c.force == GCB_FORCE_GCA) S = 0;
                 cls = S;
+            } else if ((fl_in & GCB_FLAG_EXITED) && !(fl_in & GCB_FLAG_NONFINITE)) {
+                ++ne;
             } else {
                 ++nf;
             }
@@ -748,6 +752,10 @@ __global__ void __launch_bounds__(TPB, 3) k_push_ks(const KsGrid<FT> g, const Ar
     for (int k = 0; k < 8; ++k) {
         unsigned v = __reduce_add_sync(0xffffffffu, vals[k]);
         if (lane == 0 && v) atomicAdd(&s_acc[k], (unsigned long long)v);
+    }
+    {
+        const unsigned v = __reduce_add_sync(0xffffffffu, ne);
+        if (lane == 0 && v) atomicAdd(&a.stats[ST_EXITED], (unsigned long long)v);
     }
     unsigned mx = __reduce_max_sync(0xffffffffu, vals[8]);
 #pragma unroll

@@ -55,7 +55,7 @@ class GcbStats(C.Structure):
     _fields_ = [("n_boris", C.c_int64), ("n_gca", C.c_int64), ("n_to_gca", C.c_int64),
                 ("n_to_boris", C.c_int64), ("n_nonconv", C.c_int64), ("n_gcafail", C.c_int64),
                 ("n_nonfinite", C.c_int64), ("sum_iter", C.c_int64), ("max_iter", C.c_int64),
-                ("sum_ekin", C.c_double)]
+                ("sum_ekin", C.c_double), ("n_exited", C.c_int64)]
 
 
 class GcbGridKs(C.Structure):

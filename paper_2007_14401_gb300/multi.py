@@ -50,7 +50,7 @@ def sum_over_ranks(x: torch.Tensor) -> torch.Tensor:
 
 # gcb_stats fields summed over ranks (the rest: max_iter, a maximum)
 STATS_SUM = ("n_boris", "n_gca", "n_to_gca", "n_to_boris", "n_nonconv", "n_gcafail",
-             "n_nonfinite", "sum_iter", "sum_ekin")
+             "n_nonfinite", "sum_iter", "sum_ekin", "n_exited")
 
 
 def reduce_stats(stats: dict, device="cpu") -> dict:

@@ -48,7 +48,7 @@ def test_struct_layout_matches_header(G, tmp_path):
               ("gcb_params", "gca_tol", G.GcbParams), ("gcb_params", "step_index", G.GcbParams),
               ("gcb_params", "fuse_steps", G.GcbParams), ("gcb_params", "drift_frame", G.GcbParams),
               ("gcb_params", "gyro_phase", G.GcbParams), ("gcb_params", "mirror", G.GcbParams),
-              ("gcb_stats", "sum_ekin", G.GcbStats),
+              ("gcb_stats", "sum_ekin", G.GcbStats), ("gcb_stats", "n_exited", G.GcbStats),
               ("gcb_grid_ks", "dl", G.GcbGridKs), ("gcb_ks_params", "r_out", G.GcbKsParams),
               ("gcb_ks_params", "kick_basis", G.GcbKsParams),
               ("gcb_current", "q", G.GcbCurrent), ("gcb_current", "w", G.GcbCurrent),

@@ -79,7 +79,8 @@ def assert_permutation(ds):
 
 
 def counted(stats, n, steps):
-    return stats["n_boris"] + stats["n_gca"] + stats["n_nonfinite"] == n * steps
+    return (stats["n_boris"] + stats["n_gca"] + stats["n_nonfinite"] + stats["n_exited"]
+            == n * steps)
 
 
 SWITCH_BITS = O.FLAG_S | O.FLAG_SPREV

@@ -88,7 +88,7 @@ def test_fp64_one_step(G, wald, qm, force):
     assert np.all(dx <= 1e-12 * np.maximum(np.abs(ref["x"][:, same]), 1.0))
     un = np.linalg.norm(ref["u"][:, same], axis=0) + 1.0
     assert np.all(np.abs(got["u"] - ref["u"])[:, same] <= 1e-12 * un)
-    for k in ("n_boris", "n_gca", "n_gcafail", "n_nonfinite", "sum_iter", "max_iter"):
+    for k in ("n_boris", "n_gca", "n_gcafail", "n_nonfinite", "n_exited", "sum_iter", "max_iter"):
         assert gs[k] == os_[k], k
     if force == 0 and qm == -30.0:
         assert gs["n_boris"] > 0 and gs["n_gca"] > 0
@@ -128,7 +128,10 @@ def test_exits_and_frozen(G, wald):
     assert np.array_equal(got["flags"] & (G.FLAG_EXITED | G.FLAG_NONFINITE),
                           ref["flags"] & (O.FLAG_EXITED | O.FLAG_NONFINITE))
     assert np.all(got["flags"][:5] & G.FLAG_EXITED)
-    assert gs["n_nonfinite"] == os_["n_nonfinite"]
+    assert gs["n_nonfinite"] == os_["n_nonfinite"] and gs["n_exited"] == os_["n_exited"]
+    # the non-finite particle is not advanced in any of the 3 steps; the five
+    # falling in leave at the first step and are frozen for the other two
+    assert os_["n_nonfinite"] == 3 and os_["n_exited"] >= 10
 
 
 @pytest.mark.parametrize("force", [1, 0])
@@ -148,7 +151,7 @@ def test_global_basis_one_step(G, wald, force):
     assert np.all(dx <= 1e-12 * np.maximum(np.abs(ref["x"][:, same]), 1.0))
     un = np.linalg.norm(ref["u"][:, same], axis=0) + 1.0
     assert np.all(np.abs(got["u"] - ref["u"])[:, same] <= 1e-12 * un)
-    for k in ("n_boris", "n_gca", "n_gcafail", "n_nonfinite", "sum_iter", "max_iter"):
+    for k in ("n_boris", "n_gca", "n_gcafail", "n_nonfinite", "n_exited", "sum_iter", "max_iter"):
         assert gs[k] == os_[k], k
     assert gs["n_boris"] > 0
 

@@ -111,7 +111,8 @@ def test_stats_reduced_over_rank_shards_equal_one_process(orc):
 def test_reduce_stats_single_process_is_identity():
     from paper_2007_14401_gb300 import multi
     s = {"n_boris": 3, "n_gca": 5, "n_to_gca": 1, "n_to_boris": 0, "n_nonconv": 0,
-         "n_gcafail": 0, "n_nonfinite": 0, "sum_iter": 15, "max_iter": 4, "sum_ekin": 0.25}
+         "n_gcafail": 0, "n_nonfinite": 0, "sum_iter": 15, "max_iter": 4, "sum_ekin": 0.25,
+         "n_exited": 2}
     assert multi.reduce_stats(s) == s
 
 
