@@ -42,15 +42,15 @@ MUTANTS = [
     ("gather_weights_swapped", "w[d] = od ? t[d] : 1.0 - t[d];",
      "w[d] = od ? 1.0 - t[d] : t[d];"),
     ("upar_curv_accel_dropped",
-     "+ qm * dt * P->Epar + 0.5 * dt * G0 * g;", "+ qm * dt * P->Epar;"),
+     "+ qm * dt * P->Epar + 0.5 * dt * G0 * g + fm;", "+ qm * dt * P->Epar + fm;"),
     ("upar_Epar_dropped",
-     "+ qm * dt * P->Epar + 0.5 * dt * G0 * g;", "+ 0.5 * dt * G0 * g;"),
+     "+ qm * dt * P->Epar + 0.5 * dt * G0 * g + fm;", "+ 0.5 * dt * G0 * g + fm;"),
     ("k3_D_dropped", "double k3 = upr * upr + (c2 + perp_sq(P, p, mu, uperp)) * D * D;",
      "double k3 = upr * upr + (c2 + perp_sq(P, p, mu, uperp));"),
     ("upar_new_sign", "*upar_new = (upr + 0.5 * dt * G1 * g) / D;",
      "*upar_new = (upr - 0.5 * dt * G1 * g) / D;"),
-    ("zero_curv_Epar_sign", "*upar_new = upar + qm * dt * P->Epar;",
-     "*upar_new = upar - qm * dt * P->Epar;"),
+    ("zero_curv_Epar_sign", "*upar_new = upar + qm * dt * P->Epar + fm;",
+     "*upar_new = upar - qm * dt * P->Epar + fm;"),
     ("decompose_point_sign", "Rh[k] = xn[k] - 0.5 * dxp[k];", "Rh[k] = xn[k] + 0.5 * dxp[k];"),
     ("reconstruct_at_end", "Rp[k] = 0.5 * (Rk[k] + xn[k]);", "Rp[k] = Rk[k];"),
     ("fixed_point_explicit", "xn[k] + 0.5 * p->dt * (Vn[k] + Vk[k])",
