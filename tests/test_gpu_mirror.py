@@ -67,6 +67,18 @@ def test_fp64_mirror_terms_match_oracle_3d(G):
     assert frac > 0.999 and gs["n_gca"] > 1000
 
 
+def test_fp64_mirror_terms_match_oracle_gradient_records(G):
+    """The reconnection field with gradient records (grad_mode GRID): grad |B|
+    from the records' d_i B_j."""
+    fields, st, p = inputs.reconnection_2d(nx=64, ny=32, n_particles=4096 + 37,
+                                           omega_dt_max=50.0, seed=36)
+    p = dict(p, gca_fixed_iters=5, mirror=1)
+    m = switch_margins(oracle_field(fields), oracle_params(p), st)
+    got, ref, gs, os_, _ = run_both(G, fields, st, p)
+    frac = assert_fp64_parity(got, ref, m, (64.0, 32.0), (1.0, 1.0))
+    assert frac > 0.999 and gs["n_gca"] > 1000
+
+
 def bottle_grid(B0=1.0, L=12.0, n=(16, 16, 64)):
     """B_z = B0 (1 + s^2/L^2), B_x = -B0 x' s/L^2, B_y = -B0 y' s/L^2 about the
     axis x' = y' = 0 (x' = x - 8, y' = y - 8, s = z - 32), sampled on nodes."""
