@@ -263,6 +263,38 @@ __global__ void k_gather_copy(const GatherArgs a)
     }
 }
 
+// The same gather for a layout fixed at compile time: N4 arrays of 4-byte
+// elements, N8 of 8-byte elements, the flags and optionally the ids, with no
+// per-element branch on the element size (the read-only loads of one
+// particle are free to be in flight together).
+struct GatherFixedArgs {
+    int64_t n;
+    const uint32_t *s4[12];
+    uint32_t *d4[12];
+    const unsigned long long *s8[9];
+    unsigned long long *d8[9];
+    const uint8_t *sf;
+    uint8_t *df;
+    const unsigned long long *sp;   // ids or NULL
+    unsigned long long *dp;
+    const int32_t *inv;
+};
+
+template <int N4, int N8>
+__global__ void k_gather_fixed(const GatherFixedArgs a)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a.inv[j];
+#pragma unroll
+        for (int k = 0; k < N4; ++k) a.d4[k][j] = __ldg(a.s4[k] + i);
+#pragma unroll
+        for (int k = 0; k < N8; ++k) a.d8[k][j] = __ldg(a.s8[k] + i);
+        a.df[j] = __ldg(a.sf + i);
+        if (a.sp) a.dp[j] = __ldg(a.sp + i);
+    }
+}
+
 // Element-wise permutation of up to 16 arrays: dst[j] = src[idx[j]]
 // (gather) or dst[idx[j]] = src[j] (scatter).
 struct PermArgs {
@@ -345,7 +377,42 @@ gcb_status sort_into_workspace(const gcb_particles *p, const gcb_grid *g, const 
     }
     out.narr = ga.na;
     ga.inv = inv;
-    k_gather_copy<<<blocks_for(p->n, 256), 256, 0, st>>>(ga);
+    // the layouts of the pushes' states get a gather without size branches
+    GatherFixedArgs fa;
+    int n4 = 0, n8 = 0;
+    bool fixed = true;
+    fa.n = p->n;
+    fa.inv = inv;
+    fa.sf = nullptr;
+    fa.df = nullptr;
+    fa.sp = nullptr;
+    fa.dp = nullptr;
+    for (int k = 0; k < ga.na && fixed; ++k) {
+        if (!ga.src[k]) continue;
+        if (ga.es[k] == 4 && n4 < 12) {
+            fa.s4[n4] = (const uint32_t *)ga.src[k];
+            fa.d4[n4++] = (uint32_t *)ga.dst[k];
+        } else if (ga.es[k] == 8 && k == ga.na - 1) {   // the ids (last array)
+            fa.sp = (const unsigned long long *)ga.src[k];
+            fa.dp = (unsigned long long *)ga.dst[k];
+        } else if (ga.es[k] == 8 && n8 < 9) {
+            fa.s8[n8] = (const unsigned long long *)ga.src[k];
+            fa.d8[n8++] = (unsigned long long *)ga.dst[k];
+        } else if (ga.es[k] == 1 && !fa.sf) {
+            fa.sf = (const uint8_t *)ga.src[k];
+            fa.df = (uint8_t *)ga.dst[k];
+        } else {
+            fixed = false;
+        }
+    }
+    fixed = fixed && fa.sf;
+    // (the 2D mixed state with FP32-pair positions: a step with a sort measured
+    // 1.57 against 1.71 ms at 2^24 particles; the 3D one, 12 arrays, measured
+    // slower than the generic gather, its registers halving the resident
+    // threads)
+    const int nb = blocks_for(p->n, 256);
+    if (fixed && n4 == 9 && n8 == 0) k_gather_fixed<9, 0><<<nb, 256, 0, st>>>(fa);
+    else k_gather_copy<<<nb, 256, 0, st>>>(ga);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("sort kernels: %s", cudaGetErrorString(e));
