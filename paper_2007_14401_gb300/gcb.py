@@ -502,6 +502,44 @@ def push(state: State, grid: Grid, params: GcbParams, n_steps: int = 1, stream=N
     return None
 
 
+class StepGraph:
+    """n_steps pushes of one state captured in a CUDA graph, replayed with
+    one launch of the graph: for small problems, whose steps are short
+    enough that issuing them one by one from the host leaves the GPU idle.
+
+    The capture records the calls as they are made now: step p.step_index +
+    k for k < n_steps (so the sort schedule of those indices), the state's,
+    grid's, workspace's and current's device addresses, and no statistics
+    (a call with statistics synchronizes, which a capture cannot).  Each
+    replay advances the state by the same n_steps, with the same step
+    indices; with sorting, make n_steps a multiple of params.sort_every.
+    Push the state once without the graph before capturing (the first call
+    of each kernel sizes its grid).  With ``current``, each step adds its
+    current to current.J (zero it between replays as a PiC loop would)."""
+
+    def __init__(self, state: State, grid: Grid, params: GcbParams, n_steps: int,
+                 workspace: Workspace, current: Current | None = None):
+        if n_steps < 1:
+            raise ValueError("n_steps must be >= 1")
+        self.n_steps = int(n_steps)
+        self.graph = torch.cuda.CUDAGraph()
+        first = int(params.step_index)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.graph, stream=side):
+                for k in range(self.n_steps):
+                    params.step_index = first + k
+                    push(state, grid, params, 1, workspace=workspace, stats=False,
+                         current=current)
+        params.step_index = first
+        torch.cuda.current_stream().wait_stream(side)
+
+    def replay(self):
+        """Run the captured steps on the current stream (asynchronous)."""
+        self.graph.replay()
+
+
 # --------------------------------------------------------------------------
 # adjoint
 # --------------------------------------------------------------------------
