@@ -209,13 +209,23 @@ __device__ __forceinline__ bool finite_r(R v) { return isfinite(v); }
 // piece's midpoint, and the average of the product of two hats adds the
 // product of the piece's extents (in cells) along those axes over 12.
 // ---------------------------------------------------------------------------
+// Per particle-step: the current's arrays and grid sizes, and the factors
+// Q w dx_a/(dt V) (per cell of displacement along a) and, in 2D,
+// Q w v_z/V (per unit step fraction), formed once for all the pieces.
+template <typename R>
+struct DepCtx {
+    R *J[3];
+    R f[3];
+    int n[3];
+};
+
 // returns the number of atomic additions issued
 template <typename R, int ND>
-__device__ __forceinline__ int dep_piece(const PushArgs<R> &a, const int cell[ND], const R p0[ND],
-                                         const R p1[ND], R tau, R Qw, R vz)
+__device__ __forceinline__ int dep_piece(const DepCtx<R> &q, const int cell[ND], const R p0[ND],
+                                         const R p1[ND], R tau)
 {
     int nat = 0;
-    const int nx = a.g.n[0], ny = a.g.n[1];
+    const int nx = q.n[0], ny = q.n[1];
     int I[2], Jn[2];
     I[0] = cell[0];
     I[1] = cell[0] + 1 == nx ? 0 : cell[0] + 1;
@@ -230,29 +240,31 @@ __device__ __forceinline__ int dep_piece(const PushArgs<R> &a, const int cell[ND
     if constexpr (ND == 2) {
         // 32-bit indices (the deposition is limited to grids of < 2^31 nodes)
         const int r0 = Jn[0] * nx, r1 = Jn[1] * nx;
+        const int i00 = r0 + I[0], i10 = r0 + I[1], i01 = r1 + I[0], i11 = r1 + I[1];
         if (d[0] != R(0)) {   // J_x at (i+1/2, j) and (i+1/2, j+1)
-            const R f = Qw * a.jc[0] * d[0];
-            atomicAdd(a.J[0] + r0 + I[0], f * (R(1) - m[1]));
-            atomicAdd(a.J[0] + r1 + I[0], f * m[1]);
+            const R f = q.f[0] * d[0];
+            atomicAdd(q.J[0] + i00, f * (R(1) - m[1]));
+            atomicAdd(q.J[0] + i01, f * m[1]);
             nat += 2;
         }
         if (d[1] != R(0)) {   // J_y at (i, j+1/2) and (i+1, j+1/2)
-            const R f = Qw * a.jc[1] * d[1];
-            atomicAdd(a.J[1] + r0 + I[0], f * (R(1) - m[0]));
-            atomicAdd(a.J[1] + r0 + I[1], f * m[0]);
+            const R f = q.f[1] * d[1];
+            atomicAdd(q.J[1] + i00, f * (R(1) - m[0]));
+            atomicAdd(q.J[1] + i10, f * m[0]);
             nat += 2;
         }
-        if (vz != R(0) && tau > R(0)) {   // J_z at the cell's four nodes
-            const R f = Qw * a.jz * vz * tau;
+        if (q.f[2] != R(0) && tau > R(0)) {   // J_z at the cell's four nodes
+            const R f = q.f[2] * tau;
             const R cr = d[0] * d[1] * R(1.0 / 12.0);
-            atomicAdd(a.J[2] + r0 + I[0], f * fma(R(1) - m[0], R(1) - m[1], cr));
-            atomicAdd(a.J[2] + r0 + I[1], f * fma(m[0], R(1) - m[1], -cr));
-            atomicAdd(a.J[2] + r1 + I[0], f * fma(R(1) - m[0], m[1], -cr));
-            atomicAdd(a.J[2] + r1 + I[1], f * fma(m[0], m[1], cr));
+            const R w0 = R(1) - m[0], w1 = R(1) - m[1];
+            atomicAdd(q.J[2] + i00, f * fma(w0, w1, cr));
+            atomicAdd(q.J[2] + i10, f * fma(m[0], w1, -cr));
+            atomicAdd(q.J[2] + i01, f * fma(w0, m[1], -cr));
+            atomicAdd(q.J[2] + i11, f * fma(m[0], m[1], cr));
             nat += 4;
         }
     } else {
-        const int nz = a.g.n[2];
+        const int nz = q.n[2];
         int K[2];
         K[0] = cell[2];
         K[1] = cell[2] + 1 == nz ? 0 : cell[2] + 1;
@@ -262,7 +274,7 @@ __device__ __forceinline__ int dep_piece(const PushArgs<R> &a, const int cell[ND
             if (d[c] == R(0)) continue;
             // the other two axes in cyclic order, b then e
             const int b = c == 2 ? 0 : c + 1, e = c == 0 ? 2 : c - 1;
-            const R f = Qw * a.jc[c] * d[c];
+            const R f = q.f[c] * d[c];
             const R cr = d[b] * d[e] * R(1.0 / 12.0);
 #pragma unroll
             for (int oe = 0; oe < 2; ++oe)
@@ -275,7 +287,7 @@ __device__ __forceinline__ int dep_piece(const PushArgs<R> &a, const int cell[ND
                     if (c == 0) idx = lin(I[0], Jn[ob], K[oe]);
                     else if (c == 1) idx = lin(I[oe], Jn[0], K[ob]);
                     else idx = lin(I[ob], Jn[oe], K[0]);
-                    atomicAdd(a.J[c] + idx, v);
+                    atomicAdd(q.J[c] + idx, v);
                 }
             nat += 4;
         }
@@ -290,8 +302,18 @@ __device__ __forceinline__ bool deposit_path(const PushArgs<R> &a, const int ib[
                                              const R disp[ND], R Qw, R vz, unsigned &npc,
                                              unsigned &nat)
 {
-    R s0[ND], ds[ND], p0[ND], tn[ND], td[ND];
-    int cell[ND], stp[ND], off[ND];
+    DepCtx<R> q;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        q.J[k] = a.J[k];
+        q.n[k] = a.g.n[k];
+    }
+    q.f[0] = Qw * a.jc[0];
+    q.f[1] = Qw * a.jc[1];
+    q.f[2] = ND == 2 ? Qw * a.jz * vz : Qw * a.jc[2];
+    // off: the current cell's offset from the cell of x^n (held in R)
+    R s0[ND], ds[ND], p0[ND], tn[ND], td[ND], off[ND];
+    int cell[ND], stp[ND];
 #pragma unroll
     for (int k = 0; k < ND; ++k) {
         ds[k] = disp[k] * a.g.inv_dx[k];
@@ -299,7 +321,7 @@ __device__ __forceinline__ bool deposit_path(const PushArgs<R> &a, const int ib[
         s0[k] = fmin(fmax(l[k] * a.g.inv_dx[k], R(0)), R(1));
         p0[k] = s0[k];
         cell[k] = ib[k];
-        off[k] = 0;
+        off[k] = R(0);
         if (ds[k] > R(0)) {
             stp[k] = 1;
             td[k] = R(1) / ds[k];
@@ -325,16 +347,16 @@ __device__ __forceinline__ bool deposit_path(const PushArgs<R> &a, const int ib[
         R p1[ND];
 #pragma unroll
         for (int k = 0; k < ND; ++k)
-            p1[k] = fmin(fmax(fma(ds[k], te, s0[k]) - R(off[k]), R(0)), R(1));
-        nat += dep_piece<R, ND>(a, cell, p0, p1, te - t, Qw, vz);
+            p1[k] = fmin(fmax(fma(ds[k], te, s0[k]) - off[k], R(0)), R(1));
+        nat += dep_piece<R, ND>(q, cell, p0, p1, te - t);
         ++npc;
         if (te >= R(1)) break;
 #pragma unroll
         for (int k = 0; k < ND; ++k) {
             if (stp[k] != 0 && tn[k] <= te) {   // enters the next cell along k
                 int c = cell[k] + stp[k];
-                cell[k] = c < 0 ? a.g.n[k] - 1 : (c == a.g.n[k] ? 0 : c);
-                off[k] += stp[k];
+                cell[k] = c < 0 ? q.n[k] - 1 : (c == q.n[k] ? 0 : c);
+                off[k] += R(stp[k]);
                 tn[k] += td[k];
                 p1[k] = stp[k] > 0 ? R(0) : R(1);
             }
