@@ -152,6 +152,27 @@ def test_weights_and_changing_fields(G, precision, pos_mode):
     assert_current_parity(cur, ocur, precision)
 
 
+def test_several_steps_in_one_call_and_host_state(G):
+    """Three steps in one call add the three steps' currents (against the
+    oracle's three steps); a state left in pinned host memory deposits the
+    same current as the same state on the device."""
+    import torch
+    fields, st, p = recon(n=2048 + 5, seed=27)
+    p = dict(p, gca_fixed_iters=5, force=1)
+    cur, ocur, ds, ref = deposit_both(G, fields, st, p, "fp64", "f64", q=(-1.0, 1.0), n_steps=3)
+    assert_current_parity(cur, ocur, "fp64")
+    grid = G.Grid(fields, dtype="f64")
+    J = []
+    for device in ("cuda", "pinned"):
+        s = G.State.from_numpy(st, precision="fp64", pos_mode="f64", device=device)
+        c = G.Current(grid, (-1.0, 1.0), precision="fp64")
+        G.push(s, grid, G.make_params(p), 2, current=c)
+        torch.cuda.synchronize()
+        J.append(c.J.cpu().numpy())
+    scale = np.abs(J[0]).max()
+    assert scale > 0 and np.abs(J[0] - J[1]).max() <= 1e-12 * scale
+
+
 def test_sorting_does_not_change_the_current(G):
     fields, st, p = recon(seed=25)
     p = dict(p, gca_fixed_iters=5)
