@@ -154,8 +154,9 @@ typedef struct {
                                 (and kappa from it) in place of b and v_E, and
                                 E_par = E.b*, with the gradients of b taken for
                                 those of b* (the records carry no grad E).
-                                GCB_FRAME_BT: gcb_push_sr only, unfused, FP64 or
-                                FP32-pair positions; elsewhere GCB_EUNSUPPORTED. */
+                                GCB_FRAME_BT: gcb_push_sr and gcb_push_deposit_sr,
+                                unfused, FP64 or FP32-pair positions, without the
+                                mirror terms; elsewhere GCB_EUNSUPPORTED. */
     int32_t gyro_phase;      /* GCB_PHASE_KEEP (0): the reconstruction keeps the
                                 gyration direction of the decomposition (Sec. 3.1);
                                 GCB_PHASE_EVOLVE: it turns that direction about b
@@ -172,9 +173,9 @@ typedef struct {
                                 -(mu/Gamma) b.grad(B)/kappa to du_par/dt, explicit
                                 at (x^n, u_par^{n-1/2}) (mu as mu/m; grad kappa
                                 neglected: the records carry no grad E).
-                                gcb_push_sr only, unfused, simplified frame; the
-                                deposition, the covariant push and the adjoint
-                                refuse it (GCB_EUNSUPPORTED). */
+                                gcb_push_sr and gcb_push_deposit_sr, unfused,
+                                simplified frame; the covariant push and the
+                                adjoint refuse it (GCB_EUNSUPPORTED). */
 } gcb_params;
 
 /* Counters of one push call (gcb_push_sr, gcb_push_ks, ...), summed over its
@@ -318,9 +319,10 @@ typedef struct {
  * gcb_push_sr that also deposits every advanced particle-step's current into
  * cur->J with atomic additions (the order of the additions is not
  * specified, so J's rounding varies from run to run; FP32 J for the mixed
- * path).  Frozen (non-finite) particles deposit nothing.  Unfused launches
- * only: prm->fuse_steps > 1, prm->drift_frame != GCB_FRAME_SIMPLE or a grid
- * of 2^31 nodes or more is GCB_EUNSUPPORTED.  dst (host, optional): when
+ * path).  Frozen (non-finite) particles deposit nothing.  The step is that
+ * of gcb_push_sr with the same options (drift frame, mirror terms, gyration
+ * phase).  Unfused launches only: prm->fuse_steps > 1 or a grid of 2^31
+ * nodes or more is GCB_EUNSUPPORTED.  dst (host, optional): when
  * non-NULL the call synchronizes `stream` and fills it (counts over all the
  * call's steps).
  * Other arguments, checks and errors as gcb_push_sr; GCB_EINVAL for a NULL,

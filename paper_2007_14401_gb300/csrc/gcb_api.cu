@@ -515,10 +515,8 @@ static gcb_status check_current(const gcb_particles *p, const gcb_grid *g, const
         set_error("per-particle weights are not permuted by sorting: sort_every must be 0");
         return GCB_EUNSUPPORTED;
     }
-    if (prm->fuse_steps > 1 || prm->drift_frame != GCB_FRAME_SIMPLE ||
-        prm->mirror != GCB_MIRROR_OFF) {
-        set_error("deposition: unfused steps (fuse_steps <= 1) in the simplified drift frame, "
-                  "without mirror terms");
+    if (prm->fuse_steps > 1) {
+        set_error("deposition: unfused steps only (fuse_steps <= 1)");
         return GCB_EUNSUPPORTED;
     }
     if (g->n[0] * g->n[1] * g->n[2] >= ((int64_t)1 << 31)) {

@@ -1005,8 +1005,9 @@ static gcb_status dispatch_push_mir(const gcb_particles *p, const gcb_particles 
     return dispatch_dims<R, PM, false, false, false, true>(a, g, prm, st);
 }
 
-// One unfused step with current deposition into cur (simplified drift frame;
-// checked by the caller).
+// One unfused step with current deposition into cur, in the simplified or
+// the exact drift frame, with or without the mirror terms (not both; checked
+// by the caller).
 template <typename R, int PM>
 static gcb_status dispatch_push_dep(const gcb_particles *p, const gcb_particles *in,
                                     const gcb_grid *g, const gcb_params *prm,
@@ -1024,6 +1025,12 @@ static gcb_status dispatch_push_dep(const gcb_particles *p, const gcb_particles 
     a.jz = (R)(1.0 / V);
     a.w = static_cast<const R *>(cur->w);
     for (int k = 0; k < 4; ++k) a.dq[k] = (R)cur->q[k];
+    if (prm->mirror == GCB_MIRROR_ON) return dispatch_dims<R, PM, false, false, true, true>(a, g, prm, st);
+    if (prm->drift_frame == GCB_FRAME_BT) {
+        if constexpr (BtInstantiated<R, PM>::value) return dispatch_dims<R, PM, false, true, true>(a, g, prm, st);
+        set_error("drift_frame GCB_FRAME_BT needs FP64 or FP32-pair positions");
+        return GCB_EUNSUPPORTED;
+    }
     return dispatch_dims<R, PM, false, false, true>(a, g, prm, st);
 }
 

@@ -11,10 +11,13 @@ per-particle displacements carry FP32 rounding).  Cases: 2D reconnection
 and 3D current sheet in both precisions (several tiles and a ragged tail),
 forced branches, two species with charges and weights, sorting, fields that
 change between steps (grid.update), paths longer than the cap, non-finite
-particles, an empty state.  At the full 2D size of the benchmark: the
+particles, an empty state, the step's options (the mirror terms, the exact
+drift frame).  At the full 2D size of the benchmark: the
 discrete continuity equation with the cloud-in-cell charge of the positions
 before and after the step, and the total current against the particles' own
-displacements.  Options the deposition does not carry are refused.
+displacements.  Option combinations the push does not carry (fused steps,
+the mirror terms in the exact frame, the exact frame with FP64 positions on
+the mixed path) are refused.
 """
 import numpy as np
 import pytest
@@ -173,6 +176,32 @@ def test_several_steps_in_one_call_and_host_state(G):
     assert scale > 0 and np.abs(J[0] - J[1]).max() <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("option", ["mirror", "exact_frame"])
+@pytest.mark.parametrize("precision,pos_mode", [("fp64", "f64"), ("mixed", "pair")])
+def test_current_with_step_options(G, option, precision, pos_mode):
+    """The deposition follows the step with its options: the mirror terms
+    (reconnection field) and the exact drift frame (Harris sheet with a guide
+    field and E.B != 0); either changes the oracle's current by percents."""
+    if option == "mirror":
+        fields, st, p = recon(seed=28)
+        over = dict(mirror=1)
+    else:
+        fields, st, p = inputs.harris_2d(n_per_species=2048, seed=29, Bg=0.3, Ez=0.08)
+        over = dict(drift_frame=O.FRAME_BT)
+    p = dict(p, gca_fixed_iters=5, **over)
+    idx = agreeing_subset(G, fields, st, p, precision, pos_mode,
+                          1e-12 if precision == "fp64" else 1e-4)
+    assert idx.size > 0.95 * st["flags"].size
+    sub = inputs.subset(st, idx)
+    cur, ocur, _, _ = deposit_both(G, fields, sub, p, precision, pos_mode, q=(-1.0, 1.0))
+    assert_current_parity(cur, ocur, precision)
+    plain = O.Current(cur.J.shape[1:], q=(-1.0, 1.0))
+    O.push_sr({k: v.copy() for k, v in sub.items()}, oracle_field(fields),
+              oracle_params(dict(p, mirror=0, drift_frame=O.FRAME_SIMPLE)), 1, current=plain)
+    J0, J1 = np.array(ocur.J), np.array(plain.J)
+    assert np.abs(J0 - J1).max() > 1e-2 * np.abs(J0).max()
+
+
 def test_sorting_does_not_change_the_current(G):
     fields, st, p = recon(seed=25)
     p = dict(p, gca_fixed_iters=5)
@@ -286,7 +315,10 @@ def test_refused_options(G):
     with pytest.raises(G.GcbError, match="UNSUPPORTED"):
         G.push(ds, grid, G.make_params(p, fuse_steps=4), 4, current=cur)
     with pytest.raises(G.GcbError, match="UNSUPPORTED"):
-        G.push(ds, grid, G.make_params(p, drift_frame=1), 1, current=cur)
+        G.push(ds, grid, G.make_params(p, drift_frame=1, mirror=1), 1, current=cur)
+    f64 = G.State.from_numpy(st, precision="mixed", pos_mode="f64")
+    with pytest.raises(G.GcbError, match="UNSUPPORTED"):
+        G.push(f64, grid, G.make_params(p, drift_frame=1), 1, current=cur)
     wc = G.Current(grid, (-1.0, 1.0), precision="mixed", w=np.ones(ds.n))
     with pytest.raises(G.GcbError, match="UNSUPPORTED"):
         G.push(ds, grid, G.make_params(p, sort_every=1), 1, current=wc)

@@ -139,9 +139,6 @@ def test_paths_without_the_mirror_terms_refuse_them(G):
         G.push(ds, grid, G.make_params(p, mirror=1, fuse_steps=4), 4)
     with pytest.raises(G.GcbError, match="UNSUPPORTED"):
         G.push(ds, grid, G.make_params(p, mirror=1, drift_frame=1), 1)
-    cur = G.Current(grid, (-1.0, 1.0), precision="mixed")
-    with pytest.raises(G.GcbError, match="UNSUPPORTED"):
-        G.push(ds, grid, G.make_params(p, mirror=1), 1, current=cur)
     lam = torch.zeros((7, ds.n), dtype=torch.float32, device="cuda")
     with pytest.raises(G.GcbError, match="UNSUPPORTED"):
         G.adjoint(ds, grid, G.make_params(p, mirror=1, gca_fixed_iters=4), 2, lam)
