@@ -51,6 +51,29 @@ def test_host_state_equals_device_state(G, precision, pos_mode, gdt):
     assert sa["sum_ekin"] == pytest.approx(sb["sum_ekin"], rel=1e-12)
 
 
+@pytest.mark.parametrize("n", [1, 31, 33, 4096 + 7])
+@pytest.mark.parametrize("pos_mode", ["pair", "f64"])
+def test_small_and_ragged_states_without_sorting(G, n, pos_mode):
+    """Without sorting the push reads the caller's arrays: a device state
+    through the shared-memory copies of the 2D mixed kernels' next tile, a
+    host state with plain loads.  The two give the same state bit for bit,
+    for one particle, a ragged single tile, a ragged second tile and many
+    tiles per block."""
+    fields, st, p = inputs.reconnection_2d(nx=64, ny=32, n_particles=n, seed=15)
+    grid = G.Grid(fields, dtype="f32")
+    gp = G.make_params(p)
+    out = []
+    for device in ("cuda", "pinned"):
+        ds = G.State.from_numpy(st, precision="mixed", pos_mode=pos_mode, device=device)
+        ws = G.Workspace(ds, grid, gp, device="cuda")
+        for k in range(3):
+            gp.step_index = k
+            G.push(ds, grid, gp, 1, workspace=ws)
+        out.append(ds.to_numpy())
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
 def test_host_state_covariant(G):
     fields, st, p = inputs.kerr_wald(nr=64, nth=48, n_particles=3000, seed=13)
     grid = G.KsGrid(fields, p["a"], p["r_in"], p["r_out"], dtype="f32")
