@@ -80,8 +80,8 @@ WORKLOADS = {
         fma_pipe=0.288,
         # DRAM bytes (read + write) of one push launch at 2^24 particles, from
         # an ncu capture of this kernel (1 pass: dram__bytes_read.sum +
-        # dram__bytes_write.sum = 721.97 MB + 560.67 MB)
-        traffic_b=1282.64e6),
+        # dram__bytes_write.sum = 722.01 MB + 560.56 MB)
+        traffic_b=1282.57e6),
     "harris2d_fp64": dict(
         gen=_gen_harris, n=16384, precision="fp64", grid="f64", sort_every=0, tile=(1, 1),
         state_b=57, field_b=128 * 128 * 48, fp64_b=None,
