@@ -1,9 +1,11 @@
 // push_sr.cuh -- one coupled step (Sec. 3.1) over all particles, one kernel.
 //
 // Each block walks tiles of TPB consecutive particles (persistent grid):
-//   phase 1  every thread loads one particle (coalesced SoA loads), gathers
-//            E, B at x^n, evaluates the switch S and stages the particle in
-//            shared memory;
+//   phase 1  every thread loads one particle (coalesced SoA loads; the
+//            unfused FP32 2D kernels take it from shared memory, where
+//            asynchronous copies issued during the previous tile put it),
+//            gathers E, B at x^n, evaluates the switch S and stages the
+//            particle in shared memory;
 //   compact  a warp ballot per branch plus a block prefix over the per-warp
 //            counts orders the tile's slots as [GCA ..., Boris ..., frozen],
 //            so all warps but one run a single branch and GCA lanes run the
